@@ -1,0 +1,370 @@
+"""Pins of the FP64 CPU oracle to facts fixed by the paper and by mathematics.
+
+Each test checks the oracle against something other than itself: hand
+closed forms (tests/golden), library routines (scipy rotations, numpy,
+Python's stable sort), invariances that follow from Eq. 1-3, and central
+finite differences of the oracle's own forward for every gradient.
+"""
+import copy
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy.spatial.transform import Rotation
+
+import oracle
+from paper_2403_11577_gb300 import scenes
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "closed_forms.json")
+
+
+def _single_scene(Xs, scales, logit_o, rgb, quats=None):
+    n = len(Xs)
+    q = np.tile([1.0, 0, 0, 0], (n, 1)) if quats is None else np.asarray(quats, float)
+    return scenes.Scene(np.asarray(Xs, np.float64), q, np.log(np.asarray(scales, float)),
+                        np.asarray(logit_o, float), np.asarray(rgb, float),
+                        np.array([0.0]), np.zeros((1, 3)), np.array([[1.0, 0, 0, 0]]))
+
+
+CAM = scenes.Camera(64, 48, 60.0, 60.0, 32.0, 24.0)
+FRAME = scenes.Frame(CAM, 0.0)
+BG = (0.1, 0.2, 0.3)
+
+
+def test_single_gaussian_closed_form():
+    """Isotropic Gaussian on the optical axis: EWA covariance, conic, peak
+    alpha = min(0.99, opacity), C = alpha c + (1 - alpha) bg (Eq. 2-3, Eq. 5)."""
+    g = json.load(open(GOLDEN))["single_isotropic_on_axis"]
+    sc = _single_scene([[0, 0, 2]], [[0.1] * 3], [0.0], [[0.8, 0.4, 0.2]])
+    opts = oracle.Opts(bg=BG)
+    pr = oracle.project(sc, CAM, np.eye(3), np.zeros(3), opts)
+    assert pr["cov"][0, 0] == pytest.approx(g["cov_xx"], rel=1e-12)
+    assert pr["conic"][0, 0] == pytest.approx(g["conic_a"], rel=1e-12)
+    assert abs(pr["conic"][0, 1]) < 1e-15
+    np.testing.assert_allclose(pr["mean"][0], g["mean"], atol=1e-12)
+    rgb, T, last, flags = oracle.render(sc, FRAME, np.zeros(6), 0.0, opts, pixels=[[32, 24], [33, 24]])
+    np.testing.assert_allclose(rgb[0], g["rgb_at_mean"], atol=1e-12)
+    assert T[0] == pytest.approx(g["T_at_mean"], abs=1e-12)
+    assert T[1] == pytest.approx(1 - g["alpha_at_33_24"], abs=1e-12)
+    np.testing.assert_allclose(rgb[1], g["rgb_at_33_24"], atol=1e-12)
+    assert list(last) == [0, 0] and list(flags) == [0, 0]
+
+
+def test_peak_alpha_clamp():
+    """A nearly opaque Gaussian is clamped to alpha_max = 0.99 at its peak."""
+    sc = _single_scene([[0, 0, 2]], [[0.1] * 3], [8.0], [[1.0, 1.0, 1.0]])
+    rgb, T, _, _ = oracle.render(sc, FRAME, np.zeros(6), 0.0, oracle.Opts(), pixels=[[32, 24]])
+    assert T[0] == pytest.approx(0.01, abs=1e-12)
+    np.testing.assert_allclose(rgb[0], [0.99] * 3, atol=1e-12)
+
+
+def test_two_gaussians_depth_order():
+    """Front-to-back compositing of two depth-ordered splats (Eq. 5); the
+    farther Gaussian is first in memory."""
+    g = json.load(open(GOLDEN))["two_gaussians_on_axis"]
+    sc = _single_scene([[0, 0, 3], [0, 0, 2]], [[0.1] * 3] * 2, [0.0, math.log(3.0)],
+                       [[1, 0, 0], [0, 0, 1]])
+    rgb, T, last, _ = oracle.render(sc, FRAME, np.zeros(6), 0.0, oracle.Opts(bg=BG), pixels=[[32, 24]])
+    np.testing.assert_allclose(rgb[0], g["rgb_at_mean"], atol=1e-12)
+    assert T[0] == pytest.approx(g["T_at_mean"], abs=1e-12)
+    assert last[0] == 0  # the farther one is composited last
+
+
+def test_early_termination_closed_form():
+    """Compositing stops before a Gaussian would bring T below t_min."""
+    g = json.load(open(GOLDEN))["stacked_opaque_on_axis"]
+    cols = [[1, 0, 0], [0, 1, 0], [0, 0, 1], [1, 1, 0], [0, 1, 1]]
+    sc = _single_scene([[0, 0, z] for z in (2, 3, 4, 5, 6)], [[0.1] * 3] * 5,
+                       [math.log(19.0)] * 5, cols)
+    rgb, T, last, flags = oracle.render(sc, FRAME, np.zeros(6), 0.0, oracle.Opts(bg=BG), pixels=[[32, 24]])
+    np.testing.assert_allclose(rgb[0], g["rgb_at_mean"], atol=1e-12)
+    assert T[0] == pytest.approx(g["T_at_mean"], rel=1e-12)
+    assert last[0] == g["last"] and flags[0] == 0
+
+
+def test_opacity_zero_gives_background():
+    p = scenes.tiny_problem()
+    sc = copy.deepcopy(p.scenes[0])
+    sc.logit_opacity = np.full(sc.n, -60.0)
+    rgb, T, last, _ = oracle.render(sc, p.frames[0], p.ext[0], 0.0, oracle.Opts(bg=BG))
+    assert np.all(T == 1.0) and np.all(last == -1)
+    assert np.all(rgb == np.array(BG))
+
+
+def test_transmittance_monotone_and_colour_linear():
+    p = scenes.tiny_problem()
+    sc, fr = p.scenes[0], p.frames[0]
+    opts = oracle.Opts(t_min=0.0)
+    R, t = oracle.frame_pose(sc, p.ext[0], 0.0, fr.timestamp)
+    depth = oracle.project(sc, fr.camera, R, t, opts)["depth"]
+    order = np.argsort(depth, kind="stable")
+    prev = np.ones(fr.camera.width * fr.camera.height)
+    for k in range(8, sc.n + 1, 8):
+        sub = copy.deepcopy(sc)
+        sub.logit_opacity = sc.logit_opacity.astype(np.float64).copy()
+        sub.logit_opacity[order[k:]] = -60.0
+        T = oracle.render(sub, fr, p.ext[0], 0.0, opts)[1]
+        assert np.all(T <= prev + 1e-15) and np.all(T > 0) and np.all(T <= 1)
+        prev = T
+    # colour linearity with bg = 0: C(a c1 + b c2) = a C(c1) + b C(c2)
+    rng = np.random.default_rng(3)
+    c1, c2 = rng.uniform(size=(sc.n, 3)), rng.uniform(size=(sc.n, 3))
+    s1, s2, s3 = (copy.deepcopy(sc) for _ in range(3))
+    s1.rgb, s2.rgb, s3.rgb = c1, c2, 0.3 * c1 + 1.7 * c2
+    r1 = oracle.render(s1, fr, p.ext[0], 0.0)[0]
+    r2 = oracle.render(s2, fr, p.ext[0], 0.0)[0]
+    r3 = oracle.render(s3, fr, p.ext[0], 0.0)[0]
+    np.testing.assert_allclose(r3, 0.3 * r1 + 1.7 * r2, atol=1e-12)
+
+
+def test_trajectory_closed_form():
+    """Lerp + SLERP between keyframes (Sec. III-A): constant velocity and
+    constant yaw rate give p(tau), R(tau) and dR/dtau in closed form."""
+    yaw = math.radians(60.0)
+    sc = _single_scene([[0, 0, 5]], [[0.1] * 3], [0.0], [[1, 1, 1]])
+    sc.traj_t = np.array([0.0, 1.0, 3.0])
+    sc.traj_p = np.array([[0, 0, 0], [1, 2, 3], [1, 2, 3]], float)
+    sc.traj_q = np.array([[1, 0, 0, 0], [math.cos(yaw / 2), 0, 0, math.sin(yaw / 2)],
+                          [math.cos(yaw / 2), 0, 0, math.sin(yaw / 2)]])
+    for tau in [0.0, 0.25, 0.5, 0.999]:
+        R, p, dR, dp = oracle.lidar_pose(sc, tau)
+        Rz = Rotation.from_rotvec([0, 0, yaw * tau]).as_matrix()
+        np.testing.assert_allclose(p, np.array([1, 2, 3]) * tau, atol=1e-12)
+        np.testing.assert_allclose(R, Rz, atol=1e-12)
+        np.testing.assert_allclose(dp, [1, 2, 3], atol=1e-12)
+        W = np.array([[0, -yaw, 0], [yaw, 0, 0], [0, 0, 0]])
+        np.testing.assert_allclose(dR, Rz @ W, atol=1e-10)
+    # keyframes are reproduced exactly and the next segment starts at t_1
+    R, p, dR, dp = oracle.lidar_pose(sc, 1.0)
+    np.testing.assert_allclose(p, [1, 2, 3], atol=1e-12)
+    np.testing.assert_allclose(R, Rotation.from_rotvec([0, 0, yaw]).as_matrix(), atol=1e-12)
+    np.testing.assert_allclose(dp, 0, atol=1e-12)
+    np.testing.assert_allclose(dR, 0, atol=1e-12)
+    # outside the keyframes the end segment is extended linearly
+    R, p, _, _ = oracle.lidar_pose(sc, -0.5)
+    np.testing.assert_allclose(p, np.array([1, 2, 3]) * -0.5, atol=1e-12)
+    np.testing.assert_allclose(R, Rotation.from_rotvec([0, 0, -yaw / 2]).as_matrix(), atol=1e-12)
+
+
+def test_slerp_shortest_arc():
+    """q and -q are the same rotation; SLERP takes the shorter arc."""
+    sc = _single_scene([[0, 0, 5]], [[0.1] * 3], [0.0], [[1, 1, 1]])
+    a = math.radians(40.0)
+    sc.traj_t = np.array([0.0, 1.0])
+    sc.traj_p = np.zeros((2, 3))
+    sc.traj_q = np.array([[1, 0, 0, 0], [-math.cos(a / 2), 0, -math.sin(a / 2), 0]])
+    R, _, _, _ = oracle.lidar_pose(sc, 0.5)
+    np.testing.assert_allclose(R, Rotation.from_rotvec([0, a / 2, 0]).as_matrix(), atol=1e-12)
+
+
+def test_frame_pose_matches_library_composition():
+    """Eq. 1: T^n = T_L(t + delta) * L_T_i; X^n = (T^n)^-1 X (Eq. 2) --
+    against scipy's rotation-vector exponential and numpy's inverse."""
+    p = scenes.tiny_problem()
+    sc = p.scenes[0]
+    ext = np.array([0.3, -0.2, 0.5, 0.4, -0.1, 0.2])
+    for delta in [0.0, 0.07, -0.13]:
+        R_wL, p_wL, _, _ = oracle.lidar_pose(sc, 0.4 + delta)
+        Re = Rotation.from_rotvec(ext[:3]).as_matrix()
+        T = np.eye(4)
+        T[:3, :3] = R_wL @ Re
+        T[:3, 3] = R_wL @ ext[3:] + p_wL
+        Tinv = np.linalg.inv(T)
+        R_cw, t_cw = oracle.frame_pose(sc, ext, delta, 0.4)
+        np.testing.assert_allclose(R_cw, Tinv[:3, :3], atol=1e-12)
+        np.testing.assert_allclose(t_cw, Tinv[:3, 3], atol=1e-12)
+
+
+def test_rotated_anisotropic_projection():
+    """Eq. 3 and EWA: the oracle's 2D covariance equals J Sigma_c J^T + lp I
+    with Sigma_c built from the quaternion product q_c = q_cw * q (scipy) and
+    J the finite-difference Jacobian of the pinhole map."""
+    rng = np.random.default_rng(11)
+    n = 16
+    X = np.stack([rng.uniform(-1, 1, n), rng.uniform(-1, 1, n), rng.uniform(3, 8, n)], 1)
+    q = rng.normal(size=(n, 4))
+    ls = np.log(rng.uniform(0.05, 0.5, (n, 3)))
+    sc = scenes.Scene(X, q, ls, np.zeros(n), np.ones((n, 3)), np.array([0.0]), np.zeros((1, 3)),
+                      np.array([[1.0, 0, 0, 0]]))
+    Rcw = Rotation.from_rotvec([0.1, -0.2, 0.05]).as_matrix()
+    tcw = np.array([0.2, -0.1, 0.3])
+    cam = scenes.Camera(640, 480, 500.0, 480.0, 320.0, 240.0)
+    pr = oracle.project(sc, cam, Rcw, tcw, oracle.Opts())
+    rcw = Rotation.from_matrix(Rcw)
+    for g in range(n):
+        qg = Rotation.from_quat(np.r_[q[g, 1:], q[g, 0]])  # scipy is (x, y, z, w)
+        Rc = (rcw * qg).as_matrix()
+        Sc = Rc @ np.diag(np.exp(2 * ls[g])) @ Rc.T
+        pc = Rcw @ X[g] + tcw
+
+        def pin(v):
+            return np.array([cam.fx * v[0] / v[2] + cam.cx, cam.fy * v[1] / v[2] + cam.cy])
+        Jfd = np.zeros((2, 3))
+        for k in range(3):
+            e = np.zeros(3)
+            e[k] = 1e-6
+            Jfd[:, k] = (pin(pc + e) - pin(pc - e)) / 2e-6
+        cov = Jfd @ Sc @ Jfd.T + 0.3 * np.eye(2)
+        np.testing.assert_allclose(pr["cov"][g], [cov[0, 0], cov[0, 1], cov[1, 1]], rtol=1e-6)
+        np.testing.assert_allclose(pr["conic"][g], np.linalg.inv(cov)[[0, 0, 1], [0, 1, 1]], rtol=1e-6)
+        np.testing.assert_allclose(pr["mean"][g], pin(pc), rtol=1e-12)
+        assert pr["depth"][g] == pytest.approx(pc[2], rel=1e-12)
+
+
+def test_rigid_motion_invariance():
+    """Moving the points, the Gaussian orientations and the LiDAR trajectory
+    by one rigid motion leaves every image unchanged (Eq. 1-3)."""
+    p = scenes.tiny_problem()
+    sc, fr = p.scenes[0], p.frames[0]
+    ext = np.array([0.05, 0.02, -0.03, 0.1, 0.0, -0.05])
+    M = Rotation.from_rotvec([0.4, -0.7, 0.2])
+    t0 = np.array([3.0, -2.0, 1.5])
+    sc2 = copy.deepcopy(sc)
+    sc2.X = M.apply(sc.X.astype(np.float64)) + t0
+    qg = Rotation.from_quat(np.c_[sc.quat[:, 1:], sc.quat[:, 0]].astype(np.float64))
+    qq = (M * qg).as_quat()
+    sc2.quat = np.c_[qq[:, 3], qq[:, :3]]
+    sc2.traj_p = M.apply(sc.traj_p) + t0
+    tq = (M * Rotation.from_quat(np.c_[sc.traj_q[:, 1:], sc.traj_q[:, 0]])).as_quat()
+    sc2.traj_q = np.c_[tq[:, 3], tq[:, :3]]
+    a = oracle.render(sc, fr, ext, 0.01)
+    b = oracle.render(sc2, fr, ext, 0.01)
+    np.testing.assert_allclose(a[0], b[0], atol=1e-10)
+    np.testing.assert_array_equal(a[2], b[2])
+
+
+def test_stationary_trajectory_has_zero_time_gradient():
+    p = scenes.tiny_problem()
+    sc = copy.deepcopy(p.scenes[0])
+    sc.traj_p = np.zeros((2, 3))
+    sc.traj_q = np.array([[1.0, 0, 0, 0], [1.0, 0, 0, 0]])
+    W = np.random.default_rng(0).normal(size=(64 * 48, 3))
+    g = oracle.backward(sc, p.frames[0], p.ext[0], 0.0, W)
+    assert g["delta"][0] == 0.0
+    assert np.any(g["ext"] != 0)
+
+
+def _fd_check(opts, seed, opacity_shift=0.0):
+    p = scenes.tiny_problem()
+    sc, fr = p.scenes[0], p.frames[0]
+    sc.logit_opacity = sc.logit_opacity.astype(np.float64) + opacity_shift
+    ext = p.ext_target[0]  # a non-identity extrinsic
+    delta = 0.013
+    W = np.random.default_rng(seed).normal(size=(64 * 48, 3))
+    # pixels on a discontinuity (alpha skip/clamp, T stop) get no weight
+    W[oracle.render(sc, fr, ext, delta, opts)[3] != 0] = 0.0
+
+    def L(scene, e, d):
+        rgb, _, _, flags = oracle.render(scene, fr, e, d, opts)
+        return float((rgb * W).sum()), flags
+
+    L0, flags = L(sc, ext, delta)
+    G = oracle.backward(sc, fr, ext, delta, W, opts)
+    errs = {}
+    for k in range(6):
+        h = 1e-6
+        e1, e2 = ext.copy(), ext.copy()
+        e1[k] += h
+        e2[k] -= h
+        fd = (L(sc, e1, delta)[0] - L(sc, e2, delta)[0]) / (2 * h)
+        errs["ext%d" % k] = abs(fd - G["ext"][k]) / max(abs(G["ext"][k]), 1e-3)
+    fd = (L(sc, ext, delta + 1e-6)[0] - L(sc, ext, delta - 1e-6)[0]) / 2e-6
+    errs["delta"] = abs(fd - G["delta"][0]) / max(abs(G["delta"][0]), 1e-3)
+    for name in ["quat", "log_scale", "logit_opacity", "rgb"]:
+        ga = G[name].ravel()
+        scale = np.abs(ga).max()
+        for i in np.argsort(-np.abs(ga))[:12]:
+            s1, s2 = copy.deepcopy(sc), copy.deepcopy(sc)
+            a1 = getattr(s1, name).astype(np.float64)
+            a2 = getattr(s2, name).astype(np.float64)
+            h = 1e-6 * max(1.0, abs(a1.ravel()[i]))
+            a1.ravel()[i] += h
+            a2.ravel()[i] -= h
+            setattr(s1, name, a1)
+            setattr(s2, name, a2)
+            fd = (L(s1, ext, delta)[0] - L(s2, ext, delta)[0]) / (2 * h)
+            errs["%s%d" % (name, i)] = abs(fd - ga[i]) / scale
+    return errs, flags[W[:, 0] != 0]
+
+
+@pytest.mark.parametrize("mode", ["smooth", "default", "opaque_bg"])
+def test_gradients_match_finite_differences(mode):
+    """Every oracle gradient (Gaussian parameters, extrinsic, time offset)
+    against FP64 central differences of the oracle's forward.  'opaque_bg'
+    raises the opacities so that compositing terminates early at many pixels
+    and uses a non-zero background."""
+    if mode == "smooth":
+        errs, flags = _fd_check(oracle.SMOOTH, 7)
+    elif mode == "default":
+        errs, flags = _fd_check(oracle.Opts(), 7)
+    else:
+        errs, flags = _fd_check(oracle.Opts(bg=(0.2, 0.5, 0.8)), 8, opacity_shift=5.0)
+    assert np.all(flags == 0)
+    worst = max(errs, key=errs.get)
+    assert errs[worst] < 1e-6, (worst, errs[worst])
+
+
+def test_bin_sort_matches_python_stable_sort():
+    """Tile binning + depth order against Python's stable sort of the
+    emitted (key, value) pairs."""
+    tiles = [(5, 3), (2, 4), (7, 1)]
+    npf = [40, 25, 30]
+    rect, depth = scenes.random_splat_records(9, tiles, npf, tie_fraction=0.5, max_extent_tiles=4)
+    keys, vals, ranges = oracle.bin_sort(tiles, npf, rect, depth)
+    pairs = []
+    rec = 0
+    tile_off = 0
+    for (tx, ty), n in zip(tiles, npf):
+        for g in range(n):
+            x0, y0, x1, y1 = rect[rec + g]
+            bits = int(np.frombuffer(depth[rec + g].tobytes(), np.uint32)[0])
+            for yy in range(y0, y1 + 1):
+                for xx in range(x0, x1 + 1):
+                    pairs.append(((tile_off + yy * tx + xx) << 32 | bits, g))
+        rec += n
+        tile_off += tx * ty
+    pairs.sort(key=lambda kv: kv[0])  # stable: equal keys keep emission order
+    assert len(pairs) == len(keys)
+    assert [k for k, _ in pairs] == [int(k) for k in keys]
+    assert [v for _, v in pairs] == [int(v) for v in vals]
+    for t in range(tile_off):
+        idx = [i for i, (k, _) in enumerate(pairs) if k >> 32 == t]
+        if idx:
+            assert tuple(ranges[t]) == (idx[0], idx[-1] + 1)
+        else:
+            assert tuple(ranges[t]) == (0, 0)
+    assert sum(1 for i in range(1, len(pairs)) if pairs[i][0] == pairs[i - 1][0]) > 0
+
+
+def test_l1_matches_numpy():
+    rng = np.random.default_rng(1)
+    a, b = rng.uniform(size=(7, 5, 3)), rng.uniform(size=(7, 5, 3))
+    b[0, 0, 0] = a[0, 0, 0]
+    loss, grad = oracle.l1(a, b)
+    assert loss == pytest.approx(np.abs(a - b).mean(), rel=1e-14)
+    np.testing.assert_array_equal(grad, np.sign(a - b) / a.size)
+
+
+def test_ambiguity_flag_alpha_threshold():
+    """A pixel where some alpha sits on the 1/255 skip threshold is flagged."""
+    # o = 0.5; choose the pixel offset dx so that 0.5 exp(-dx^2 conic / 2) = 1/255
+    sc = _single_scene([[0, 0, 2]], [[0.1] * 3], [0.0], [[1, 1, 1]])
+    conic = 1 / 9.3
+    dx = math.sqrt(2 * math.log(0.5 * 255) / conic)
+    cam = scenes.Camera(64, 48, 60.0, 60.0, 32.0 - (dx - round(dx)), 24.0)
+    fr = scenes.Frame(cam, 0.0)
+    _, _, _, flags = oracle.render(sc, fr, np.zeros(6), 0.0, oracle.Opts(), pixels=[[32 + round(dx), 24], [32, 24]])
+    assert flags[0] & oracle.FLAG_ALPHA_EDGE and flags[1] == 0
+
+
+def test_scale_clamp():
+    """scale_max clamps the axis scales (voxel-size bound, Sec. III-D1)."""
+    p = scenes.tiny_problem()
+    sc = p.scenes[0]
+    sc2 = copy.deepcopy(sc)
+    sc2.log_scale = np.minimum(sc.log_scale.astype(np.float64), math.log(0.2))
+    a = oracle.render(sc, p.frames[0], p.ext[0], 0.0, oracle.Opts(scale_max=0.2))
+    b = oracle.render(sc2, p.frames[0], p.ext[0], 0.0, oracle.Opts())
+    np.testing.assert_allclose(a[0], b[0], atol=1e-12)
