@@ -1,0 +1,287 @@
+/*
+ * gs3dcalib.h -- C ABI of libgs3dcalib.so: differentiable tile-based 3D
+ * Gaussian splatting for LiDAR-camera spatiotemporal calibration
+ * (3DGS-Calib, arXiv 2403.11577), hand-written CUDA for sm_103a (GB300).
+ *
+ * The path, in the paper's terms:
+ *   pose     Eq. 1      T^n = T_L(t^n + delta_i) * L_T^i       gs_pose_compose
+ *   project  Eq. 2-3    X^n = (T^n)^-1 X,  r^n = (R^n)^-1 r,
+ *                       EWA projection of each Gaussian           gs_project
+ *   bin/sort Eq. 5 (Phi) tile binning + depth order               gs_bin_sort
+ *   render   Eq. 5 (Phi) front-to-back alpha compositing          gs_render_fwd
+ *   loss     Eq. 4      L1 term of L_photo                        gs_loss_l1
+ *   backward Sec. III-B "gradients are backpropagated to both the Gaussian
+ *                       parameters, and the calibration parameters through
+ *                       the input pose"                           gs_render_bwd,
+ *                                                                 gs_pose_grad
+ *
+ * Conventions (all entry points):
+ *   - Pointers named *_dev, and every tensor argument unless stated, are
+ *     DEVICE pointers owned by the caller.  The library never allocates or
+ *     frees device memory; scratch lives in one caller-allocated workspace
+ *     of gs_workspace_size() bytes (256-byte aligned).
+ *   - Every call enqueues work on `stream` (a cudaStream_t; NULL = legacy
+ *     default stream) and returns without synchronising, except
+ *     gs_batch_init and gs_read_stats, which are synchronous.  The
+ *     asynchronous calls can be captured into a CUDA graph.
+ *   - Layouts are row-major and contiguous; float is IEEE binary32, double
+ *     binary64.  Quaternions are Hamilton (w, x, y, z).  An extrinsic is the
+ *     camera-to-LiDAR transform L_T^i = [Exp(omega) | t] stored as
+ *     (omega_x, omega_y, omega_z, t_x, t_y, t_z), omega a rotation vector.
+ *   - Return value: GS_OK, or a host-detected error (nothing was enqueued
+ *     for GS_ERR_INVALID_ARG; GS_ERR_CUDA means a launch failed).  Errors
+ *     found on the device (pair-buffer overflow, non-finite values) set
+ *     bits of a status word in the workspace; read it with gs_read_stats.
+ *   - Per-(frame, Gaussian) "records": frame f owns records
+ *     [record_offset, record_offset + gauss_count); record r of frame f is
+ *     Gaussian gauss_offset + (r - record_offset).
+ */
+#ifndef GS3DCALIB_H
+#define GS3DCALIB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t gs_status;
+enum {
+    GS_OK = 0,
+    GS_ERR_INVALID_ARG = 1,
+    GS_ERR_CAPACITY = 2,
+    GS_ERR_CUDA = 3,
+    GS_ERR_UNSUPPORTED = 4
+};
+
+/* bits of the device status word */
+enum {
+    GS_DEV_PAIR_OVERFLOW = 1u,  /* more tile-Gaussian pairs than pair_capacity:
+                                   the batch was rendered with no Gaussians */
+    GS_DEV_NONFINITE = 2u       /* a non-finite projected value was culled */
+};
+
+/* One camera frame n_i (Sec. III-A notation table). */
+typedef struct {
+    int32_t width, height;      /* image size in pixels */
+    float fx, fy, cx, cy;       /* pinhole intrinsics; pixel (u,v) is the
+                                   image point (u,v) of fx*x/z + cx */
+    int32_t camera_id;          /* camera i: index into ext[] and delta[] */
+    int32_t traj_id;            /* LiDAR trajectory (scene) of the frame */
+    int32_t gauss_offset;       /* first Gaussian of the frame's scene */
+    int32_t gauss_count;        /* Gaussians in the scene (G) */
+    double timestamp;           /* t^{n_i}, seconds, camera clock */
+    /* written by gs_batch_init: */
+    int64_t record_offset;      /* first per-(frame, Gaussian) record */
+    int64_t pixel_offset;       /* first pixel in the image outputs */
+    int32_t tile_offset;        /* first global tile id */
+    int32_t tiles_x, tiles_y;   /* tiles covering the image */
+    int32_t reserved;
+} gs_frame;
+
+/* Renderer settings.  The paper defers the renderer to 3DGS
+ * [kerbl20233d] and EWA [zwicker2001ewa]; these are that renderer's
+ * choices, exposed as parameters. */
+typedef struct {
+    float near_z;     /* cull centres with camera depth <= near_z, metres
+                         ("remove the points behind the camera", Sec. III-C) */
+    float lowpass;    /* EWA screen-space filter variance added to the 2D
+                         covariance diagonal, px^2 (0.3) */
+    float alpha_min;  /* skip a Gaussian whose alpha is below this (1/255) */
+    float alpha_max;  /* clamp alpha to at most this (0.99) */
+    float t_min;      /* stop before transmittance would drop below (1e-4) */
+    float scale_max;  /* clamp each axis scale to at most this, metres;
+                         +inf = off (voxel-size bound, Sec. III-D1) */
+    float bg[3];      /* background colour */
+    int32_t tile;     /* tile edge in pixels: 8, 16 or 32 */
+    int32_t batch;    /* Gaussians staged in shared memory per round:
+                         64, 128 or 256 */
+    int32_t reserved;
+} gs_opts;
+
+/* A batch of frames planned by gs_batch_init. */
+typedef struct {
+    const gs_frame *frames_dev; /* device copy of the frame table */
+    int32_t num_frames;         /* F */
+    int32_t num_cameras;        /* entries of ext[] / delta[] */
+    int32_t num_trajs;          /* entries of traj_offset[] minus one */
+    int32_t num_gaussians;      /* rows of the Gaussian parameter arrays */
+    int32_t tile;               /* tile edge the plan was made for */
+    int32_t num_tiles;          /* total tiles over all frames */
+    int64_t num_records;        /* total per-(frame, Gaussian) records */
+    int64_t num_pixels;         /* total pixels over all frames */
+    int64_t pair_capacity;      /* tile-Gaussian pairs the workspace holds */
+} gs_batch;
+
+/* Counters kept in the workspace (gs_read_stats). */
+typedef struct {
+    uint32_t status;            /* GS_DEV_* bits, sticky until gs_reset_status */
+    uint32_t reserved;
+    uint64_t num_pairs;         /* tile-Gaussian pairs of the last gs_bin_sort */
+    uint64_t eval_fwd;          /* (pixel, pair) evaluations, last gs_render_fwd */
+    uint64_t eval_bwd;          /* (pixel, pair) evaluations, last gs_render_bwd */
+} gs_stats;
+
+/* ------------------------------------------------------------ planning -- */
+
+/* Version string of the library. */
+const char *gs_version(void);
+
+/* sizeof(gs_frame), sizeof(gs_opts), sizeof(gs_batch), sizeof(gs_stats)
+ * written to out[0..n) so that bindings can check their struct mirrors.
+ * Returns the number of sizes written. */
+int32_t gs_struct_sizes(size_t *out, int32_t n);
+
+/* Plan a batch (host, synchronous).  frames_host[F] is read and its
+ * gs_batch_init-written fields are filled; the completed table is copied
+ * to frames_dev (caller-allocated device memory of F * sizeof(gs_frame)
+ * bytes) with cudaMemcpy.  tile must be 8, 16 or 32.  Frames are checked:
+ * positive sizes, camera_id < num_cameras, traj_id < num_trajs, Gaussian
+ * range inside [0, num_gaussians), tiles_x and tiles_y < 65536.
+ * Errors: GS_ERR_INVALID_ARG, GS_ERR_CUDA (copy failed). */
+gs_status gs_batch_init(gs_frame *frames_host, int32_t num_frames, int32_t num_gaussians,
+                        int32_t num_cameras, int32_t num_trajs, int32_t tile,
+                        int64_t pair_capacity, gs_frame *frames_dev, gs_batch *out);
+
+/* Workspace bytes needed by a batch (host).  0 on invalid input. */
+size_t gs_workspace_size(const gs_batch *batch);
+
+/* Byte offsets of the workspace regions (host), for tests and tools that
+ * read intermediate buffers:  [0] stats, [1] pose32 (float[F][16]: R_cw
+ * row-major 9, camera centre hi 3, camera centre lo 3, pad), [2] pose64
+ * (double[F][32]), [3] rect (uint32[R][2]: x0 | y0 << 16, x1 | y1 << 16,
+ * inclusive tile coordinates, empty as x0 > x1), [4] depth (float[R]),
+ * [5] splat (float4[R][2]), [6] grad2d (float4[R][3]), [7] keys
+ * (uint64[pair_capacity]), [8] vals (uint32[pair_capacity]), [9] ranges
+ * (uint32[T][2]: [start, end) of each tile in keys/vals).  Returns the
+ * number of offsets written (<= max_entries). */
+int32_t gs_workspace_offsets(const gs_batch *batch, size_t *offsets, int32_t max_entries);
+
+/* Read the counters (synchronises `stream`). */
+gs_status gs_read_stats(const gs_batch *batch, const void *ws_dev, void *stream, gs_stats *out);
+
+/* Clear the device status bits (async). */
+gs_status gs_reset_status(const gs_batch *batch, void *ws_dev, void *stream);
+
+/* Kernel timing hook.  After this call, every launch of the selected
+ * kernel is bracketed by cudaEventRecordWithFlags(start/stop, stream,
+ * cudaEventRecordExternal) on the kernel's own stream, so the events also
+ * become event-record nodes when the launch is captured into a CUDA graph.
+ * kernel: GS_PROF_NONE (0) disables the hook; GS_PROF_PROJECT,
+ * GS_PROF_BIN_SORT (the whole binning and sorting sequence),
+ * GS_PROF_RENDER_FWD, GS_PROF_RENDER_BWD (the compositing backward only),
+ * GS_PROF_PROJECT_BWD.  The events are cudaEvent_t handles owned by the
+ * caller (created with timing enabled).  Process-wide setting; not thread
+ * safe.  Errors: GS_ERR_INVALID_ARG for an unknown kernel or NULL events. */
+enum {
+    GS_PROF_NONE = 0,
+    GS_PROF_PROJECT = 1,
+    GS_PROF_BIN_SORT = 2,
+    GS_PROF_RENDER_FWD = 3,
+    GS_PROF_RENDER_BWD = 4,
+    GS_PROF_PROJECT_BWD = 5
+};
+gs_status gs_profile_events(int32_t kernel, void *start_event, void *stop_event);
+
+/* ----------------------------------------------------------- hot path -- */
+
+/* Eq. 1 (Sec. III-A): camera pose of every frame.  The LiDAR trajectory
+ * T_L(t) interpolates keyframes linearly in position and by SLERP in
+ * orientation; the segment [t_k, t_{k+1}) holding tau = t^{n_i} + delta_i is
+ * used (the end segments extend linearly beyond the keyframes).
+ *   traj_t[K]        keyframe times (double), increasing within a trajectory
+ *   traj_pose[K][7]  keyframe LiDAR-to-world pose (p_x,p_y,p_z, q_w,q_x,q_y,q_z)
+ *   traj_offset[num_trajs+1]  trajectory j owns keyframes
+ *                    [traj_offset[j], traj_offset[j+1]) (int32, >= 1 each)
+ *   ext[C][6]        camera-to-LiDAR extrinsic per camera (double)
+ *   delta[C]         time offset per camera, seconds (double)
+ * Writes the world-to-camera pose of each frame (and the camera-frame
+ * velocity twist used by the time-offset gradient) to the workspace. */
+gs_status gs_pose_compose(const gs_batch *batch, const double *traj_t, const double *traj_pose,
+                          const int32_t *traj_offset, const double *ext, const double *delta,
+                          void *ws_dev, void *stream);
+
+/* Eq. 2-3 and the EWA projection of Phi (Eq. 5): for every (frame,
+ * Gaussian) record, the camera-frame centre X^n = (T^n)^-1 X, the
+ * camera-frame covariance R^n^-1 Sigma R^n^-T, the 2D mean, the conic
+ * (inverse of J Sigma_c J^T + lowpass I), the opacity, and the rectangle of
+ * tiles where alpha can reach alpha_min.  Gaussians with depth <= near_z
+ * or opacity < alpha_min are culled (empty rectangle).
+ *   X[N][3]        centres, world frame (float; fixed LiDAR points, Sec. III-B)
+ *   quat[N][4]     rotation r, any non-zero norm (normalised inside)
+ *   log_scale[N][3] s = exp(log_scale), clamped to scale_max
+ *   logit_opacity[N] alpha = sigmoid(logit_opacity)
+ * Reads the poses written by gs_pose_compose. */
+gs_status gs_project(const gs_batch *batch, const float *X, const float *quat,
+                     const float *log_scale, const float *logit_opacity, const gs_opts *opts,
+                     void *ws_dev, void *stream);
+
+/* Tile binning and depth ordering for Phi (Eq. 5): every record emits one
+ * pair per tile of its rectangle, key = (global tile << 32) | float bits of
+ * the depth, value = Gaussian index within its scene; the pairs are sorted
+ * by key with a stable LSD radix sort (equal keys keep record order), and
+ * each tile's [start, end) range is found.  If the pairs exceed
+ * pair_capacity, GS_DEV_PAIR_OVERFLOW is set and the batch is treated as
+ * having no pairs. */
+gs_status gs_bin_sort(const gs_batch *batch, const gs_opts *opts, void *ws_dev, void *stream);
+
+/* Phi (Eq. 5): front-to-back alpha compositing per pixel over its tile's
+ * depth-ordered Gaussians: alpha = min(alpha_max, opacity * exp(power)),
+ * power = -1/2 d^T conic d, skip alpha < alpha_min, stop before T would fall
+ * below t_min; C = sum c alpha T + T_final bg.
+ *   colors[N][3]      view-independent colour c (float, used as is)
+ *   out_rgb[P][3]     rendered colour, P = num_pixels, frame f at
+ *                     pixel_offset, row-major (float)
+ *   out_T[P]          final transmittance (float)
+ *   out_last[P]       one past the position, within the tile's sorted
+ *                     range, of the last composited Gaussian; 0 if none
+ *                     (int32) -- the backward's starting point */
+gs_status gs_render_fwd(const gs_batch *batch, const float *colors, const gs_opts *opts,
+                        void *ws_dev, float *out_rgb, float *out_T, int32_t *out_last,
+                        void *stream);
+
+/* L1 term of L_photo (Eq. 4): loss = mean |rgb - target| over n values and
+ * grad = sign(rgb - target) / n (0 where equal) * scale.
+ *   out_loss[1] (double) is overwritten; grad may alias nothing.
+ *   ws_dev: a workspace of this batch (uses its reduction scratch). */
+gs_status gs_loss_l1(const gs_batch *batch, const float *rgb, const float *target, int64_t n,
+                     float scale, double *out_loss, float *out_grad, void *ws_dev, void *stream);
+
+/* Backward of Phi and of the projection (Sec. III-B): walks each pixel's
+ * composited Gaussians in reverse order, recovering transmittance by
+ * division instead of storing it, reduces per-pixel gradients warp-first,
+ * accumulates per-record 2D gradients, then carries them through the EWA
+ * projection and Eq. 2-3 to the Gaussian parameters and to a per-frame
+ * camera twist (kept in the workspace for gs_pose_grad).
+ *   dL_drgb[P][3]  gradient of the loss w.r.t. out_rgb
+ *   out_T, out_last: as written by gs_render_fwd for the same inputs
+ *   d_quat[N][4], d_log_scale[N][3], d_logit_opacity[N], d_colors[N][3]:
+ *                  gradients of all N Gaussians; added to the arrays if
+ *                  accumulate != 0, written over them if accumulate == 0.
+ * gs_project zeroes the per-record accumulators this call consumes, so each
+ * gs_render_bwd needs its own preceding gs_project. */
+gs_status gs_render_bwd(const gs_batch *batch, const float *X, const float *quat,
+                        const float *log_scale, const float *logit_opacity, const float *colors,
+                        const gs_opts *opts, void *ws_dev, const float *out_T,
+                        const int32_t *out_last, const float *dL_drgb, float *d_quat,
+                        float *d_log_scale, float *d_logit_opacity, float *d_colors,
+                        int32_t accumulate, void *stream);
+
+/* Gradient w.r.t. the calibration parameters "through the input pose"
+ * (Sec. III-B, Eq. 1): sums the per-frame camera twists of gs_render_bwd
+ * per camera and maps them to
+ *   d_ext[C][6]   dL/d(omega, t) of the extrinsic (double)
+ *   d_delta[C]    dL/d delta (double)
+ *   d_xi[C][6]    optional (NULL to skip): dL/dxi for the right
+ *                 perturbation L_T^i <- L_T^i Exp(xi), xi = (rho, phi)
+ *   ext[C][6]     the extrinsic used by gs_pose_compose
+ *   accumulate    0: outputs are written; otherwise added to. */
+gs_status gs_pose_grad(const gs_batch *batch, const double *ext, void *ws_dev, double *d_ext,
+                       double *d_delta, double *d_xi, int32_t accumulate, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GS3DCALIB_H */

@@ -1,0 +1,389 @@
+// Tile binning and depth ordering for Phi (Eq. 5).
+//
+// 1. k_pair_count: tiles per record, summed per block of kEmitItems records.
+// 2. k_pair_scan:  exclusive scan of the block sums; total pairs P; if P
+//    exceeds the capacity the overflow bit is set and P is taken as 0.
+// 3. k_pair_emit:  each block re-derives its records' counts, scans them in
+//    shared memory and writes its pairs cooperatively (every thread strides
+//    over the block's output range and finds its record by binary search),
+//    key = (global tile << 32) | float bits of the depth, value = Gaussian
+//    index within its scene.  Records are emitted in order, so for equal
+//    keys the emission order is ascending value.
+// 4. LSD radix sort, 8-bit digits over the key bits that can be non-zero,
+//    each pass: k_radix_hist (per-block digit counts) -> k_radix_scan (one
+//    exclusive scan of the digit-major count matrix) -> k_radix_scatter
+//    (stable: per-warp ranking with match_any in index order, per-tile
+//    prefix over warps, staging in shared memory by digit, then coalesced
+//    writes).  Each block owns one contiguous chunk of the input, so the
+//    order of equal digits is preserved across blocks.
+// 5. k_tile_ranges: [start, end) of every tile in the sorted pairs.
+// No kernel waits on another block; there are no spin loops.
+#include "common.cuh"
+
+namespace gs {
+
+namespace {
+
+__device__ __forceinline__ uint32_t rect_count(uint2 rc) {
+    uint32_t x0 = rc.x & 0xffffu, y0 = rc.x >> 16, x1 = rc.y & 0xffffu, y1 = rc.y >> 16;
+    if (x0 > x1 || y0 > y1) return 0u;
+    return (x1 - x0 + 1u) * (y1 - y0 + 1u);
+}
+
+template <int NT>
+__device__ __forceinline__ unsigned long long block_sum_u64(unsigned long long v, unsigned long long *sh) {
+    for (int s = 16; s > 0; s >>= 1) v += __shfl_xor_sync(0xffffffffu, v, s);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+    __syncthreads();
+    unsigned long long t = 0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < NT / 32; w++) t += sh[w];
+    return t;  // valid in thread 0
+}
+
+__global__ void __launch_bounds__(kEmitThreads)
+k_pair_count(const uint2 *__restrict__ rect, long long R, unsigned long long *__restrict__ sums) {
+    __shared__ unsigned long long sh[kEmitThreads / 32];
+    const long long base = (long long)blockIdx.x * kEmitItems;
+    unsigned long long c = 0;
+    for (int i = threadIdx.x; i < kEmitItems; i += kEmitThreads) {
+        long long r = base + i;
+        if (r < R) c += rect_count(rect[r]);
+    }
+    unsigned long long t = block_sum_u64<kEmitThreads>(c, sh);
+    if (threadIdx.x == 0) sums[blockIdx.x] = t;
+}
+
+// Exclusive scan of n u64 values in place by one block of 1024 threads.
+__device__ void block_exclusive_scan_u64(unsigned long long *a, long long n, unsigned long long *total) {
+    __shared__ unsigned long long part[1024];
+    const int T = blockDim.x;
+    const long long per = (n + T - 1) / T;
+    const long long lo = min((long long)threadIdx.x * per, n), hi = min(lo + per, n);
+    unsigned long long s = 0;
+    for (long long i = lo; i < hi; i++) s += a[i];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int off = 1; off < T; off <<= 1) {
+        unsigned long long v = threadIdx.x >= off ? part[threadIdx.x - off] : 0ull;
+        __syncthreads();
+        part[threadIdx.x] += v;
+        __syncthreads();
+    }
+    unsigned long long run = part[threadIdx.x] - s;  // exclusive prefix of this thread's segment
+    for (long long i = lo; i < hi; i++) {
+        unsigned long long x = a[i];
+        a[i] = run;
+        run += x;
+    }
+    if (threadIdx.x == T - 1) *total = part[T - 1];
+}
+
+__global__ void __launch_bounds__(1024)
+k_pair_scan(unsigned long long *__restrict__ sums, int nb, long long capacity, Stats *__restrict__ stats) {
+    __shared__ unsigned long long total;
+    block_exclusive_scan_u64(sums, nb, &total);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        stats->raw_pairs = total;
+        if (total > (unsigned long long)capacity) {
+            stats->num_pairs = 0;
+            atomicOr(&stats->status, (unsigned)GS_DEV_PAIR_OVERFLOW);
+        } else {
+            stats->num_pairs = total;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kEmitThreads)
+k_pair_emit(const gs_frame *__restrict__ frames, int F, const uint2 *__restrict__ rect,
+            const float *__restrict__ depth, long long R, const unsigned long long *__restrict__ sums,
+            const Stats *__restrict__ stats, unsigned long long *__restrict__ keys, uint32_t *__restrict__ vals) {
+    __shared__ unsigned long long off[kEmitItems + 1];
+    __shared__ uint32_t s_tile0[kEmitItems];   // global tile of the rect's first tile
+    __shared__ uint32_t s_w[kEmitItems];       // rect width in tiles
+    __shared__ uint32_t s_stride[kEmitItems];  // tiles_x of the frame
+    __shared__ uint32_t s_bits[kEmitItems];
+    __shared__ uint32_t s_val[kEmitItems];
+    __shared__ unsigned long long wsum[kEmitThreads / 32];
+    if (stats->num_pairs == 0) return;  // nothing to emit, or overflow
+    const long long base = (long long)blockIdx.x * kEmitItems;
+    constexpr int PER = kEmitItems / kEmitThreads;
+    // counts of this thread's PER consecutive records
+    unsigned long long c[PER];
+    unsigned long long mine = 0;
+    for (int j = 0; j < PER; j++) {
+        const int i = threadIdx.x * PER + j;
+        const long long r = base + i;
+        c[j] = 0;
+        if (r < R) {
+            uint2 rc = rect[r];
+            c[j] = rect_count(rc);
+            if (c[j]) {
+                const int f = frame_of_record(frames, F, r);
+                const gs_frame &fr = frames[f];
+                const uint32_t x0 = rc.x & 0xffffu, y0 = rc.x >> 16, x1 = rc.y & 0xffffu;
+                s_tile0[i] = (uint32_t)fr.tile_offset + y0 * (uint32_t)fr.tiles_x + x0;
+                s_w[i] = x1 - x0 + 1u;
+                s_stride[i] = (uint32_t)fr.tiles_x;
+                s_bits[i] = __float_as_uint(depth[r]);
+                s_val[i] = (uint32_t)(r - fr.record_offset);
+            }
+        }
+        mine += c[j];
+    }
+    // block exclusive scan of the per-thread totals (warp shuffles + warp sums)
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned long long incl = mine;
+    for (int s = 1; s < 32; s <<= 1) {
+        unsigned long long v = __shfl_up_sync(0xffffffffu, incl, s);
+        if (lane >= s) incl += v;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    unsigned long long wpre = 0;
+    for (int w = 0; w < warp; w++) wpre += wsum[w];
+    unsigned long long run = wpre + incl - mine;
+    for (int j = 0; j < PER; j++) {
+        off[threadIdx.x * PER + j] = run;
+        run += c[j];
+    }
+    if (threadIdx.x == kEmitThreads - 1) off[kEmitItems] = run;
+    __syncthreads();
+    const unsigned long long total = off[kEmitItems];
+    const unsigned long long gbase = sums[blockIdx.x];
+    for (unsigned long long o = threadIdx.x; o < total; o += kEmitThreads) {
+        // record i with off[i] <= o < off[i+1] (records with 0 pairs are skipped)
+        int lo = 0, hi = kEmitItems - 1;
+        while (lo < hi) {
+            int mid = (lo + hi + 1) >> 1;
+            if (off[mid] <= o) lo = mid; else hi = mid - 1;
+        }
+        const uint32_t k = (uint32_t)(o - off[lo]);
+        const uint32_t w = s_w[lo];
+        const uint32_t tile = s_tile0[lo] + (k / w) * s_stride[lo] + (k % w);
+        keys[gbase + o] = ((unsigned long long)tile << 32) | s_bits[lo];
+        vals[gbase + o] = s_val[lo];
+    }
+}
+
+// ------------------------------------------------------------ radix sort
+
+struct Chunk { long long lo, hi; };
+
+__device__ __forceinline__ Chunk sort_chunk(unsigned long long P, int nb, int b) {
+    const long long tiles = (long long)((P + kSortTile - 1) / kSortTile);
+    const long long per = (tiles + nb - 1) / nb;
+    long long lo = min((long long)b * per * kSortTile, (long long)P);
+    long long hi = min(lo + per * kSortTile, (long long)P);
+    return {lo, hi};
+}
+
+__global__ void __launch_bounds__(kSortThreads)
+k_radix_hist(const unsigned long long *__restrict__ keys, const Stats *__restrict__ stats, int shift,
+             int nb, uint32_t *__restrict__ hist) {
+    __shared__ uint32_t h[kSortThreads / 32][kRadix];
+    const int warp = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < (kSortThreads / 32) * kRadix; i += kSortThreads) (&h[0][0])[i] = 0;
+    __syncthreads();
+    const Chunk c = sort_chunk(stats->num_pairs, nb, blockIdx.x);
+    for (long long i = c.lo + threadIdx.x; i < c.hi; i += kSortThreads)
+        atomicAdd(&h[warp][(uint32_t)(keys[i] >> shift) & (kRadix - 1)], 1u);
+    __syncthreads();
+    for (int d = threadIdx.x; d < kRadix; d += kSortThreads) {
+        uint32_t s = 0;
+        for (int w = 0; w < kSortThreads / 32; w++) s += h[w][d];
+        hist[(size_t)d * nb + blockIdx.x] = s;
+    }
+}
+
+// Exclusive scan of the digit-major matrix hist[d * nb + b] (u32; the total
+// fits: it is at most the pair capacity, checked on the host to be < 2^32).
+__global__ void __launch_bounds__(1024) k_radix_scan(uint32_t *__restrict__ hist, int n) {
+    __shared__ uint32_t part[1024];
+    const int T = blockDim.x;
+    const int per = (n + T - 1) / T;
+    const int lo = min((int)threadIdx.x * per, n), hi = min(lo + per, n);
+    uint32_t s = 0;
+    for (int i = lo; i < hi; i++) s += hist[i];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int off = 1; off < T; off <<= 1) {
+        uint32_t v = threadIdx.x >= off ? part[threadIdx.x - off] : 0u;
+        __syncthreads();
+        part[threadIdx.x] += v;
+        __syncthreads();
+    }
+    uint32_t run = part[threadIdx.x] - s;
+    for (int i = lo; i < hi; i++) {
+        uint32_t x = hist[i];
+        hist[i] = run;
+        run += x;
+    }
+}
+
+constexpr int kWarps = kSortThreads / 32;
+
+struct ScatterSmem {
+    unsigned long long skey[kSortTile];
+    uint32_t sval[kSortTile];
+    uint32_t wcnt[kWarps][kRadix];   // per-warp digit counts, then exclusive prefix over warps
+    uint32_t tcnt[kRadix];           // digit counts of the tile
+    uint32_t tstart[kRadix];         // exclusive scan of tcnt
+    uint32_t run[kRadix];            // next global position of each digit
+    uint32_t wtot[kRadix / 32];
+};
+
+__global__ void __launch_bounds__(kSortThreads)
+k_radix_scatter(const unsigned long long *__restrict__ kin, const uint32_t *__restrict__ vin,
+                unsigned long long *__restrict__ kout, uint32_t *__restrict__ vout,
+                const Stats *__restrict__ stats, int shift, int nb, const uint32_t *__restrict__ hist) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    ScatterSmem &S = *reinterpret_cast<ScatterSmem *>(smem_raw);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const Chunk c = sort_chunk(stats->num_pairs, nb, blockIdx.x);
+    for (int d = threadIdx.x; d < kRadix; d += kSortThreads) S.run[d] = hist[(size_t)d * nb + blockIdx.x];
+    const uint32_t lt_mask = (1u << lane) - 1u;
+    for (long long t0 = c.lo; t0 < c.hi; t0 += kSortTile) {
+        for (int i = lane; i < kRadix; i += 32) S.wcnt[warp][i] = 0;
+        __syncwarp();
+        unsigned long long k[kSortItems];
+        uint32_t v[kSortItems], dg[kSortItems], rk[kSortItems];
+        // warp w owns items [w*32*ITEMS, (w+1)*32*ITEMS) of the tile, in index order
+#pragma unroll
+        for (int r = 0; r < kSortItems; r++) {
+            const long long idx = t0 + (long long)warp * 32 * kSortItems + r * 32 + lane;
+            const bool valid = idx < c.hi;
+            k[r] = valid ? kin[idx] : 0ull;
+            v[r] = valid ? vin[idx] : 0u;
+            const uint32_t d = (uint32_t)(k[r] >> shift) & (kRadix - 1);
+            dg[r] = valid ? d : kRadix;  // kRadix marks an empty slot
+            const uint32_t key = valid ? d : (uint32_t)(kRadix + lane);
+            const uint32_t peers = __match_any_sync(0xffffffffu, key);
+            const uint32_t before = (uint32_t)__popc(peers & lt_mask);
+            uint32_t base = valid ? S.wcnt[warp][d] : 0u;
+            __syncwarp();
+            if (valid && before == 0) S.wcnt[warp][d] = base + (uint32_t)__popc(peers);
+            __syncwarp();
+            rk[r] = base + before;
+        }
+        __syncthreads();
+        // per digit: exclusive prefix over warps and the tile count
+        for (int d = threadIdx.x; d < kRadix; d += kSortThreads) {
+            uint32_t s = 0;
+            for (int w = 0; w < kWarps; w++) {
+                uint32_t x = S.wcnt[w][d];
+                S.wcnt[w][d] = s;
+                s += x;
+            }
+            S.tcnt[d] = s;
+        }
+        __syncthreads();
+        // exclusive scan of tcnt over the 256 digits (8 warps of 32)
+        if (threadIdx.x < kRadix) {
+            const uint32_t x = S.tcnt[threadIdx.x];
+            uint32_t incl = x;
+            for (int s = 1; s < 32; s <<= 1) {
+                uint32_t y = __shfl_up_sync(0xffffffffu, incl, s);
+                if (lane >= s) incl += y;
+            }
+            if (lane == 31) S.wtot[warp] = incl;
+            S.tstart[threadIdx.x] = incl - x;
+        }
+        __syncthreads();
+        if (threadIdx.x < kRadix) {
+            uint32_t pre = 0;
+            for (int w = 0; w < warp; w++) pre += S.wtot[w];
+            S.tstart[threadIdx.x] += pre;
+        }
+        __syncthreads();
+        // stage by digit
+#pragma unroll
+        for (int r = 0; r < kSortItems; r++) {
+            if (dg[r] < kRadix) {
+                const uint32_t pos = S.tstart[dg[r]] + S.wcnt[warp][dg[r]] + rk[r];
+                S.skey[pos] = k[r];
+                S.sval[pos] = v[r];
+            }
+        }
+        __syncthreads();
+        const int n = (int)min((long long)kSortTile, c.hi - t0);
+        for (int i = threadIdx.x; i < n; i += kSortThreads) {
+            const unsigned long long key = S.skey[i];
+            const uint32_t d = (uint32_t)(key >> shift) & (kRadix - 1);
+            const uint32_t pos = S.run[d] + (uint32_t)i - S.tstart[d];
+            kout[pos] = key;
+            vout[pos] = S.sval[i];
+        }
+        __syncthreads();
+        for (int d = threadIdx.x; d < kRadix; d += kSortThreads) S.run[d] += S.tcnt[d];
+        __syncthreads();
+    }
+}
+
+__global__ void k_tile_ranges(const unsigned long long *__restrict__ keys, const Stats *__restrict__ stats,
+                              uint2 *__restrict__ ranges) {
+    const long long P = (long long)stats->num_pairs;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < P;
+         i += (long long)gridDim.x * blockDim.x) {
+        const uint32_t t = (uint32_t)(keys[i] >> 32);
+        if (i == 0 || (uint32_t)(keys[i - 1] >> 32) != t) ranges[t].x = (uint32_t)i;
+        if (i == P - 1 || (uint32_t)(keys[i + 1] >> 32) != t) ranges[t].y = (uint32_t)(i + 1);
+    }
+}
+
+}  // namespace
+
+int radix_passes(int num_tiles) {
+    int tb = 0;
+    while ((1ll << tb) < (long long)num_tiles) tb++;
+    return (32 + tb + kRadixBits - 1) / kRadixBits;
+}
+
+size_t scatter_smem_bytes() { return sizeof(ScatterSmem); }
+
+cudaError_t launch_bin_sort(const gs_batch *b, const Layout &L, unsigned char *ws, cudaStream_t s, int sms) {
+    (void)sms;
+    Stats *stats = reinterpret_cast<Stats *>(ws + L.stats);
+    const uint2 *rect = reinterpret_cast<const uint2 *>(ws + L.rect);
+    const float *depth = reinterpret_cast<const float *>(ws + L.depth);
+    unsigned long long *sums = reinterpret_cast<unsigned long long *>(ws + L.emit_sums);
+    unsigned long long *keys[2] = {reinterpret_cast<unsigned long long *>(ws + L.keys[0]),
+                                   reinterpret_cast<unsigned long long *>(ws + L.keys[1])};
+    uint32_t *vals[2] = {reinterpret_cast<uint32_t *>(ws + L.vals[0]), reinterpret_cast<uint32_t *>(ws + L.vals[1])};
+    uint32_t *hist = reinterpret_cast<uint32_t *>(ws + L.sort_hist);
+    uint2 *ranges = reinterpret_cast<uint2 *>(ws + L.ranges);
+    cudaError_t e;
+    if (L.emit_blocks > 0) {
+        k_pair_count<<<L.emit_blocks, kEmitThreads, 0, s>>>(rect, b->num_records, sums);
+        k_pair_scan<<<1, 1024, 0, s>>>(sums, L.emit_blocks, b->pair_capacity, stats);
+        k_pair_emit<<<L.emit_blocks, kEmitThreads, 0, s>>>(b->frames_dev, b->num_frames, rect, depth,
+                                                           b->num_records, sums, stats, keys[L.first_buffer],
+                                                           vals[L.first_buffer]);
+    } else {
+        if ((e = cudaMemsetAsync(&stats->num_pairs, 0, sizeof(unsigned long long), s)) != cudaSuccess) return e;
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    static bool attr_set = false;
+    if (!attr_set) {
+        e = cudaFuncSetAttribute(k_radix_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sizeof(ScatterSmem));
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    int cur = L.first_buffer;
+    for (int p = 0; p < L.passes; p++) {
+        const int shift = p * kRadixBits;
+        k_radix_hist<<<L.sort_blocks, kSortThreads, 0, s>>>(keys[cur], stats, shift, L.sort_blocks, hist);
+        k_radix_scan<<<1, 1024, 0, s>>>(hist, kRadix * L.sort_blocks);
+        k_radix_scatter<<<L.sort_blocks, kSortThreads, sizeof(ScatterSmem), s>>>(
+            keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], stats, shift, L.sort_blocks, hist);
+        cur ^= 1;
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(ranges, 0, sizeof(uint2) * (size_t)b->num_tiles, s)) != cudaSuccess) return e;
+    k_tile_ranges<<<1216, 256, 0, s>>>(keys[0], stats, ranges);
+    return cudaGetLastError();
+}
+
+}  // namespace gs

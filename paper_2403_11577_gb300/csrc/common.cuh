@@ -1,0 +1,83 @@
+// Internal definitions shared by the CUDA translation units of
+// libgs3dcalib.so (workspace layout, frame lookup, small device helpers).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gs3dcalib.h"
+
+namespace gs {
+
+constexpr int kPose32Stride = 16;   // floats per frame: R_cw[9], c_hi[3], c_lo[3], pad
+constexpr int kPose64Stride = 32;   // doubles per frame, see pose.cu
+constexpr int kEmitItems = 1024;    // records per pair-emission block
+constexpr int kEmitThreads = 256;
+constexpr int kSortThreads = 512;   // radix sort block
+constexpr int kSortItems = 8;       // keys per thread per tile
+constexpr int kSortTile = kSortThreads * kSortItems;
+constexpr int kRadixBits = 8;
+constexpr int kRadix = 1 << kRadixBits;
+constexpr int kProjThreads = 128;
+constexpr int kLossBlocks = 608;
+constexpr int kLossThreads = 256;
+constexpr int kMaxFrames = 1024;    // frames per batch
+
+// Workspace counters; the head of the workspace.
+struct Stats {
+    unsigned int status;
+    unsigned int reserved;
+    unsigned long long num_pairs;   // valid pairs (0 after an overflow)
+    unsigned long long eval_fwd;
+    unsigned long long eval_bwd;
+    unsigned long long raw_pairs;   // pairs requested before the capacity check
+    unsigned long long pad[3];
+};
+
+struct Layout {
+    size_t stats, pose32, pose64, rect, depth, splat, grad2d, keys[2], vals[2], ranges,
+        emit_sums, sort_hist, twist_part, loss_part, total;
+    int emit_blocks;     // blocks of the pair count / emit kernels
+    int sort_blocks;     // blocks of the radix sort kernels
+    int twist_blocks;    // blocks of the projection backward
+    int passes;          // radix passes
+    int first_buffer;    // buffer the emission writes (the last pass ends in 0)
+};
+
+inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+int radix_passes(int num_tiles);
+bool make_layout(const gs_batch *b, Layout *L);
+
+// ------------------------------------------------------------ device side
+
+// Frame owning global tile t (binary search over tile offsets).
+__device__ __forceinline__ int frame_of_tile(const gs_frame *fr, int F, int t) {
+    int lo = 0, hi = F - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (fr[mid].tile_offset <= t) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Frame owning record r.
+__device__ __forceinline__ int frame_of_record(const gs_frame *fr, int F, long long r) {
+    int lo = 0, hi = F - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (fr[mid].record_offset <= r) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+constexpr float kLog2e = 1.4426950408889634f;
+constexpr float kLn2 = 0.6931471805599453f;
+
+}  // namespace gs

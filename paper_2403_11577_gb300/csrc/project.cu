@@ -1,0 +1,361 @@
+// EWA projection of the Gaussians (Eq. 2-3 and the projection step of Phi,
+// Eq. 5) and its backward.
+//
+// Layout: one thread per Gaussian of the whole batch; the thread reads the
+// Gaussian's parameters once (44 bytes) and loops over the frames of its
+// scene, writing one record per frame.  Frame-dependent work uses
+//   d = (X - c_hi) - c_lo   (camera centre c = c_hi + c_lo in two floats),
+//   p = R_cw d              (Eq. 2: X^n = (T^n)^-1 X = R_cw (X - c)),
+//   T = J R_cw              (J: Jacobian of the pinhole map at p),
+//   cov = T Sigma T^T + lowpass I   (= J Sigma_c J^T, Sigma_c of Eq. 3),
+// with Sigma = R_g diag(s)^2 R_g^T built once per Gaussian.
+//
+// Record outputs (frame f, Gaussian g -> record r):
+//   rect[r]   tiles [x0,x1]x[y0,y1] where alpha >= alpha_min is possible:
+//             the box of the ellipse d^T conic d <= 2 ln(opacity/alpha_min),
+//             half-widths sqrt(k cov_xx), sqrt(k cov_yy), widened by a
+//             relative 1e-4 and 0.01 px against float32 rounding;
+//   depth[r]  camera depth p.z;
+//   splat[r]  (mean_x, mean_y, A, B), (C, F, opacity, depth) with the
+//             exponent in base 2: log2 alpha = A dx^2 + B dx dy + C dy^2 + F,
+//             A = -a/2 log2 e, B = -b log2 e, C = -c/2 log2 e, F = log2 opacity,
+//             (a, b, c) the conic;
+//   grad2d[r] zeroed for visible records (the render backward accumulates
+//             into it).
+#include "common.cuh"
+
+namespace gs {
+
+namespace {
+
+struct GaussParams {
+    float X[3];
+    float q[4];       // normalised
+    float qn;         // norm of the input quaternion
+    float Rg[9];
+    float s[3];
+    bool s_clamped[3];
+    float Sig[6];     // xx, xy, xz, yy, yz, zz
+    float o, F, kext; // opacity, log2 opacity, 2 ln(opacity / alpha_min)
+};
+
+__device__ __forceinline__ void load_gauss(int g, const float *__restrict__ X, const float *__restrict__ quat,
+                                           const float *__restrict__ log_s, const float *__restrict__ logit_o,
+                                           const gs_opts &o, GaussParams &G) {
+    G.X[0] = X[3 * g]; G.X[1] = X[3 * g + 1]; G.X[2] = X[3 * g + 2];
+    float qw = quat[4 * g], qx = quat[4 * g + 1], qy = quat[4 * g + 2], qz = quat[4 * g + 3];
+    float n2 = qw * qw + qx * qx + qy * qy + qz * qz;
+    float inv = rsqrtf(n2);
+    G.qn = n2 * inv;
+    qw *= inv; qx *= inv; qy *= inv; qz *= inv;
+    G.q[0] = qw; G.q[1] = qx; G.q[2] = qy; G.q[3] = qz;
+    float *R = G.Rg;
+    R[0] = 1.f - 2.f * (qy * qy + qz * qz); R[1] = 2.f * (qx * qy - qw * qz); R[2] = 2.f * (qx * qz + qw * qy);
+    R[3] = 2.f * (qx * qy + qw * qz); R[4] = 1.f - 2.f * (qx * qx + qz * qz); R[5] = 2.f * (qy * qz - qw * qx);
+    R[6] = 2.f * (qx * qz - qw * qy); R[7] = 2.f * (qy * qz + qw * qx); R[8] = 1.f - 2.f * (qx * qx + qy * qy);
+    for (int i = 0; i < 3; i++) {
+        float s = expf(log_s[3 * g + i]);
+        G.s_clamped[i] = s > o.scale_max;
+        G.s[i] = G.s_clamped[i] ? o.scale_max : s;
+    }
+    // Sigma = M M^T with M = R_g diag(s)
+    float M[9];
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++) M[3 * i + j] = R[3 * i + j] * G.s[j];
+    G.Sig[0] = M[0] * M[0] + M[1] * M[1] + M[2] * M[2];
+    G.Sig[1] = M[0] * M[3] + M[1] * M[4] + M[2] * M[5];
+    G.Sig[2] = M[0] * M[6] + M[1] * M[7] + M[2] * M[8];
+    G.Sig[3] = M[3] * M[3] + M[4] * M[4] + M[5] * M[5];
+    G.Sig[4] = M[3] * M[6] + M[4] * M[7] + M[5] * M[8];
+    G.Sig[5] = M[6] * M[6] + M[7] * M[7] + M[8] * M[8];
+    float lo = logit_o[g];
+    G.o = 1.f / (1.f + expf(-lo));
+    G.F = log2f(G.o);
+    G.kext = 2.f * kLn2 * (G.F - log2f(o.alpha_min));
+}
+
+// Frame-dependent projection.  Returns false if culled.
+struct Proj {
+    float p[3], iz, xz, yz;   // camera-frame centre, 1/z, x/z, y/z
+    float T[6];               // J R_cw
+    float U[6];               // T Sigma
+    float cov[3];             // xx, xy, yy (with low-pass)
+    float conic[3];           // a, b, c
+    float mean[2];
+};
+
+__device__ __forceinline__ bool project_frame(const GaussParams &G, const float *__restrict__ P,
+                                              const gs_frame &fr, const gs_opts &o, Proj &Q) {
+    float d0 = (G.X[0] - P[9]) - P[12];
+    float d1 = (G.X[1] - P[10]) - P[13];
+    float d2 = (G.X[2] - P[11]) - P[14];
+    for (int i = 0; i < 3; i++) Q.p[i] = P[3 * i] * d0 + P[3 * i + 1] * d1 + P[3 * i + 2] * d2;
+    float z = Q.p[2];
+    if (!(z > o.near_z)) return false;
+    Q.iz = 1.f / z;
+    Q.xz = Q.p[0] * Q.iz;
+    Q.yz = Q.p[1] * Q.iz;
+    float fxz = fr.fx * Q.iz, fyz = fr.fy * Q.iz;
+    for (int j = 0; j < 3; j++) {
+        Q.T[j] = fxz * (P[j] - Q.xz * P[6 + j]);
+        Q.T[3 + j] = fyz * (P[3 + j] - Q.yz * P[6 + j]);
+    }
+    const float *S = G.Sig;
+    for (int r = 0; r < 2; r++) {
+        const float *t = Q.T + 3 * r;
+        Q.U[3 * r + 0] = t[0] * S[0] + t[1] * S[1] + t[2] * S[2];
+        Q.U[3 * r + 1] = t[0] * S[1] + t[1] * S[3] + t[2] * S[4];
+        Q.U[3 * r + 2] = t[0] * S[2] + t[1] * S[4] + t[2] * S[5];
+    }
+    Q.cov[0] = Q.U[0] * Q.T[0] + Q.U[1] * Q.T[1] + Q.U[2] * Q.T[2] + o.lowpass;
+    Q.cov[1] = Q.U[0] * Q.T[3] + Q.U[1] * Q.T[4] + Q.U[2] * Q.T[5];
+    Q.cov[2] = Q.U[3] * Q.T[3] + Q.U[4] * Q.T[4] + Q.U[5] * Q.T[5] + o.lowpass;
+    float det = Q.cov[0] * Q.cov[2] - Q.cov[1] * Q.cov[1];
+    if (!(det > 0.f) || !isfinite(det)) return false;
+    float idet = 1.f / det;
+    Q.conic[0] = Q.cov[2] * idet;
+    Q.conic[1] = -Q.cov[1] * idet;
+    Q.conic[2] = Q.cov[0] * idet;
+    Q.mean[0] = fr.fx * Q.xz + fr.cx;
+    Q.mean[1] = fr.fy * Q.yz + fr.cy;
+    return isfinite(Q.mean[0]) && isfinite(Q.mean[1]);
+}
+
+constexpr uint32_t kEmptyLo = 1u | (1u << 16);  // x0 = y0 = 1
+constexpr uint32_t kEmptyHi = 0u;               // x1 = y1 = 0
+
+__device__ __forceinline__ int clamp_tile(float v, int n) {
+    // floor(v) clamped to [-1, n] before the integer conversion
+    v = fminf(fmaxf(v, -1.f), (float)n);
+    return (int)floorf(v);
+}
+
+__global__ void __launch_bounds__(kProjThreads)
+k_project(const gs_frame *__restrict__ frames, int F, int N, const float *__restrict__ pose32,
+          const float *__restrict__ X, const float *__restrict__ quat, const float *__restrict__ log_s,
+          const float *__restrict__ logit_o, gs_opts o, uint2 *__restrict__ rect, float *__restrict__ depth,
+          float4 *__restrict__ splat, float4 *__restrict__ grad2d, Stats *__restrict__ stats) {
+    int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= N) return;
+    GaussParams G;
+    load_gauss(g, X, quat, log_s, logit_o, o, G);
+    const bool opaque_enough = G.o >= o.alpha_min;
+    const float tile = (float)o.tile, itile = 1.f / tile;
+    bool nonfinite = false;
+    for (int f = 0; f < F; f++) {
+        const gs_frame &fr = frames[f];
+        if (g < fr.gauss_offset || g >= fr.gauss_offset + fr.gauss_count) continue;
+        const long long r = fr.record_offset + (g - fr.gauss_offset);
+        Proj Q;
+        bool vis = opaque_enough && project_frame(G, pose32 + kPose32Stride * f, fr, o, Q);
+        uint2 rc = make_uint2(kEmptyLo, kEmptyHi);
+        if (vis) {
+            float rx = sqrtf(G.kext * Q.cov[0]) * 1.0001f + 0.01f;
+            float ry = sqrtf(G.kext * Q.cov[2]) * 1.0001f + 0.01f;
+            if (!isfinite(rx) || !isfinite(ry)) { nonfinite = true; vis = false; }
+            if (vis) {
+                int x0 = max(clamp_tile((Q.mean[0] - rx) * itile, fr.tiles_x), 0);
+                int x1 = min(clamp_tile((Q.mean[0] + rx) * itile, fr.tiles_x), fr.tiles_x - 1);
+                int y0 = max(clamp_tile((Q.mean[1] - ry) * itile, fr.tiles_y), 0);
+                int y1 = min(clamp_tile((Q.mean[1] + ry) * itile, fr.tiles_y), fr.tiles_y - 1);
+                if (x0 <= x1 && y0 <= y1) {
+                    rc = make_uint2((uint32_t)x0 | ((uint32_t)y0 << 16), (uint32_t)x1 | ((uint32_t)y1 << 16));
+                    const float s2 = -0.5f * kLog2e;
+                    splat[2 * r] = make_float4(Q.mean[0], Q.mean[1], s2 * Q.conic[0], -kLog2e * Q.conic[1]);
+                    splat[2 * r + 1] = make_float4(s2 * Q.conic[2], G.F, G.o, Q.p[2]);
+                    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+                    grad2d[3 * r] = z4;
+                    grad2d[3 * r + 1] = z4;
+                    grad2d[3 * r + 2] = z4;
+                }
+            }
+        }
+        rect[r] = rc;
+        depth[r] = vis ? Q.p[2] : 0.f;
+    }
+    if (nonfinite) atomicOr(&stats->status, (unsigned)GS_DEV_NONFINITE);
+}
+
+// ---------------------------------------------------------------- backward
+
+__device__ __forceinline__ double warp_sum(double v) {
+    for (int s = 16; s > 0; s >>= 1) v += __shfl_xor_sync(0xffffffffu, v, s);
+    return v;
+}
+
+// Chain the per-record 2D gradients back to the Gaussian parameters (summed
+// over frames) and to the per-frame camera twist g_eps = (rho, phi) of the
+// left perturbation T_cw <- Exp(eps) T_cw:
+//   g_rho = sum dL/dp,  g_phi = sum p x dL/dp + axial(R_cw (dL/dT)^T J),
+// where axial(M) = (M12 - M21, M20 - M02, M01 - M10) is the vector with
+// tr(M [phi]x) = phi . axial(M).
+template <int NT>
+__global__ void __launch_bounds__(NT)
+k_project_bwd(const gs_frame *__restrict__ frames, int F, int N, const float *__restrict__ pose32,
+              const float *__restrict__ X, const float *__restrict__ quat, const float *__restrict__ log_s,
+              const float *__restrict__ logit_o, gs_opts o, const uint2 *__restrict__ rect,
+              const float4 *__restrict__ grad2d, float *__restrict__ d_quat, float *__restrict__ d_log_s,
+              float *__restrict__ d_logit, float *__restrict__ d_col, double *__restrict__ twist_part,
+              int nparts, bool acc) {
+    __shared__ double red[NT / 32][6];
+    const int g = blockIdx.x * NT + threadIdx.x;
+    const bool active = g < N;
+    GaussParams G;
+    if (active) load_gauss(g, X, quat, log_s, logit_o, o, G);
+    float dSig[6] = {0, 0, 0, 0, 0, 0};
+    float dF = 0.f, dc0 = 0.f, dc1 = 0.f, dc2 = 0.f;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int f = 0; f < F; f++) {
+        const gs_frame &fr = frames[f];
+        double tw[6] = {0, 0, 0, 0, 0, 0};
+        bool mine = active && g >= fr.gauss_offset && g < fr.gauss_offset + fr.gauss_count;
+        if (mine) {
+            const long long r = fr.record_offset + (g - fr.gauss_offset);
+            uint2 rc = rect[r];
+            bool vis = (rc.x & 0xffffu) <= (rc.y & 0xffffu);
+            Proj Q;
+            const float *P = pose32 + kPose32Stride * f;
+            if (vis && project_frame(G, P, fr, o, Q)) {
+                float4 g0 = grad2d[3 * r], g1 = grad2d[3 * r + 1], g2 = grad2d[3 * r + 2];
+                dc0 += g1.z; dc1 += g1.w; dc2 += g2.x;
+                dF += g1.y;
+                // stored exponent coefficients -> conic (a, b, c)
+                const float ga = g0.z * (-0.5f * kLog2e), gb = g0.w * (-kLog2e), gc = g1.x * (-0.5f * kLog2e);
+                const float a = Q.conic[0], b = Q.conic[1], c = Q.conic[2];
+                // conic = cov^-1 -> cov (xx, xy, yy); xy appears once in cov
+                const float gxx = -(a * a * ga + a * b * gb + b * b * gc);
+                const float gxy = -(2.f * a * b * ga + (a * c + b * b) * gb + 2.f * b * c * gc);
+                const float gyy = -(b * b * ga + b * c * gb + c * c * gc);
+                // H = dL/dcov as a symmetric 2x2
+                const float h00 = gxx, h01 = 0.5f * gxy, h11 = gyy;
+                float HT[6];
+                for (int j = 0; j < 3; j++) {
+                    HT[j] = h00 * Q.T[j] + h01 * Q.T[3 + j];
+                    HT[3 + j] = h01 * Q.T[j] + h11 * Q.T[3 + j];
+                }
+                // G = dL/dSigma = T^T H T, a full symmetric matrix (six entries kept)
+                dSig[0] += Q.T[0] * HT[0] + Q.T[3] * HT[3];
+                dSig[1] += Q.T[0] * HT[1] + Q.T[3] * HT[4];
+                dSig[2] += Q.T[0] * HT[2] + Q.T[3] * HT[5];
+                dSig[3] += Q.T[1] * HT[1] + Q.T[4] * HT[4];
+                dSig[4] += Q.T[1] * HT[2] + Q.T[4] * HT[5];
+                dSig[5] += Q.T[2] * HT[2] + Q.T[5] * HT[5];
+                // dL/dT = 2 H U (U = T Sigma)
+                float dT[6];
+                for (int j = 0; j < 3; j++) {
+                    dT[j] = 2.f * (h00 * Q.U[j] + h01 * Q.U[3 + j]);
+                    dT[3 + j] = 2.f * (h01 * Q.U[j] + h11 * Q.U[3 + j]);
+                }
+                // dL/dJ = dL/dT R_cw^T (only the non-zero entries of J)
+                float dJ00 = dT[0] * P[0] + dT[1] * P[1] + dT[2] * P[2];
+                float dJ02 = dT[0] * P[6] + dT[1] * P[7] + dT[2] * P[8];
+                float dJ11 = dT[3] * P[3] + dT[4] * P[4] + dT[5] * P[5];
+                float dJ12 = dT[3] * P[6] + dT[4] * P[7] + dT[5] * P[8];
+                const float iz = Q.iz, iz2 = iz * iz;
+                const float fx = fr.fx, fy = fr.fy;
+                const float gmx = g0.x, gmy = g0.y;
+                float dp[3];
+                dp[0] = -fx * iz2 * dJ02 + fx * iz * gmx;
+                dp[1] = -fy * iz2 * dJ12 + fy * iz * gmy;
+                dp[2] = -fx * iz2 * dJ00 + 2.f * fx * Q.xz * iz2 * dJ02 - fy * iz2 * dJ11 +
+                        2.f * fy * Q.yz * iz2 * dJ12 - fx * Q.xz * iz * gmx - fy * Q.yz * iz * gmy;
+                // twist: rotation part through T = J R_cw: M = R_cw N, N = dT^T J
+                float J00 = fx * iz, J02 = -fx * Q.xz * iz, J11 = fy * iz, J12 = -fy * Q.yz * iz;
+                float Nm[9];
+                for (int i = 0; i < 3; i++) {
+                    Nm[3 * i + 0] = dT[i] * J00;
+                    Nm[3 * i + 1] = dT[3 + i] * J11;
+                    Nm[3 * i + 2] = dT[i] * J02 + dT[3 + i] * J12;
+                }
+                float Mm[9];
+                for (int i = 0; i < 3; i++)
+                    for (int j = 0; j < 3; j++)
+                        Mm[3 * i + j] = P[3 * i] * Nm[j] + P[3 * i + 1] * Nm[3 + j] + P[3 * i + 2] * Nm[6 + j];
+                const float *p = Q.p;
+                tw[0] = dp[0];
+                tw[1] = dp[1];
+                tw[2] = dp[2];
+                tw[3] = (double)(p[1] * dp[2] - p[2] * dp[1]) + (double)(Mm[5] - Mm[7]);
+                tw[4] = (double)(p[2] * dp[0] - p[0] * dp[2]) + (double)(Mm[6] - Mm[2]);
+                tw[5] = (double)(p[0] * dp[1] - p[1] * dp[0]) + (double)(Mm[1] - Mm[3]);
+            }
+        }
+        // deterministic block reduction of the frame's twist (FP64)
+        for (int i = 0; i < 6; i++) tw[i] = warp_sum(tw[i]);
+        if (lane == 0)
+            for (int i = 0; i < 6; i++) red[warp][i] = tw[i];
+        __syncthreads();
+        if (threadIdx.x < 6) {
+            double s = 0;
+            for (int w = 0; w < NT / 32; w++) s += red[w][threadIdx.x];
+            twist_part[((size_t)f * nparts + blockIdx.x) * 6 + threadIdx.x] = s;
+        }
+        __syncthreads();
+    }
+    if (!active) return;
+    // colour and opacity
+    auto put = [acc](float *dst, float v) { *dst = acc ? *dst + v : v; };
+    put(d_col + 3 * g, dc0);
+    put(d_col + 3 * g + 1, dc1);
+    put(d_col + 3 * g + 2, dc2);
+    // F = log2(sigmoid(l)):  dF/dl = (1 - o) / ln 2
+    put(d_logit + g, dF * (1.f - G.o) * (1.f / kLn2));
+    // Sigma = M M^T, M = R_g diag(s): dL/dM = 2 G M, G = dL/dSigma as the
+    // full symmetric matrix T^T H T (dSig holds its six distinct entries)
+    const float S00 = dSig[0], S01 = dSig[1], S02 = dSig[2];
+    const float S11 = dSig[3], S12 = dSig[4], S22 = dSig[5];
+    const float Sg[9] = {S00, S01, S02, S01, S11, S12, S02, S12, S22};
+    const float *R = G.Rg;
+    float dR[9];
+    for (int j = 0; j < 3; j++) {
+        float sj = G.s[j];
+        float ds = 0.f;
+        for (int i = 0; i < 3; i++) {
+            float dM = 2.f * (Sg[3 * i] * R[j] + Sg[3 * i + 1] * R[3 + j] + Sg[3 * i + 2] * R[6 + j]) * sj;
+            ds += dM * R[3 * i + j];
+            dR[3 * i + j] = dM * sj;
+        }
+        put(d_log_s + 3 * g + j, G.s_clamped[j] ? 0.f : ds * sj);
+    }
+    // R(q) for the unit quaternion (w, x, y, z) -> dL/dq_unit
+    const float w = G.q[0], x = G.q[1], y = G.q[2], z = G.q[3];
+    float gw = 2.f * (z * (dR[3] - dR[1]) + y * (dR[2] - dR[6]) + x * (dR[7] - dR[5]));
+    float gx = 2.f * (y * (dR[1] + dR[3]) + z * (dR[2] + dR[6]) + w * (dR[7] - dR[5])) - 4.f * x * (dR[4] + dR[8]);
+    float gy = 2.f * (x * (dR[1] + dR[3]) + w * (dR[2] - dR[6]) + z * (dR[5] + dR[7])) - 4.f * y * (dR[0] + dR[8]);
+    float gz = 2.f * (w * (dR[3] - dR[1]) + x * (dR[2] + dR[6]) + y * (dR[5] + dR[7])) - 4.f * z * (dR[0] + dR[4]);
+    // normalisation q_unit = q / |q|
+    float dot = w * gw + x * gx + y * gy + z * gz;
+    float iq = 1.f / G.qn;
+    put(d_quat + 4 * g, (gw - w * dot) * iq);
+    put(d_quat + 4 * g + 1, (gx - x * dot) * iq);
+    put(d_quat + 4 * g + 2, (gy - y * dot) * iq);
+    put(d_quat + 4 * g + 3, (gz - z * dot) * iq);
+}
+
+}  // namespace
+
+cudaError_t launch_project(const gs_batch *b, const float *pose32, const float *X, const float *quat,
+                           const float *log_s, const float *logit_o, const gs_opts *o, uint2 *rect,
+                           float *depth, float4 *splat, float4 *grad2d, Stats *stats, cudaStream_t s) {
+    int N = b->num_gaussians;
+    if (N == 0) return cudaSuccess;
+    k_project<<<(N + kProjThreads - 1) / kProjThreads, kProjThreads, 0, s>>>(
+        b->frames_dev, b->num_frames, N, pose32, X, quat, log_s, logit_o, *o, rect, depth, splat, grad2d, stats);
+    return cudaGetLastError();
+}
+
+int project_bwd_blocks(const gs_batch *b) { return (b->num_gaussians + kProjThreads - 1) / kProjThreads; }
+
+cudaError_t launch_project_bwd(const gs_batch *b, const float *pose32, const float *X, const float *quat,
+                               const float *log_s, const float *logit_o, const gs_opts *o, const uint2 *rect,
+                               const float4 *grad2d, float *d_quat, float *d_log_s, float *d_logit,
+                               float *d_col, double *twist_part, bool acc, cudaStream_t s) {
+    int nb = project_bwd_blocks(b);
+    if (nb == 0) return cudaSuccess;
+    k_project_bwd<kProjThreads><<<nb, kProjThreads, 0, s>>>(b->frames_dev, b->num_frames, b->num_gaussians,
+                                                           pose32, X, quat, log_s, logit_o, *o, rect, grad2d,
+                                                           d_quat, d_log_s, d_logit, d_col, twist_part, nb, acc);
+    return cudaGetLastError();
+}
+
+}  // namespace gs

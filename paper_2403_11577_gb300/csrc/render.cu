@@ -1,0 +1,386 @@
+// Phi (Eq. 5): front-to-back alpha compositing of the depth-sorted splats of
+// each tile, and its backward (Sec. III-B).
+//
+// One block per (frame, tile) work item of the whole batch.  Per round the
+// block stages BATCH Gaussians of the tile's sorted range in shared memory
+// (mean, exponent coefficients, colour), then every thread walks them for
+// its PPT pixels.  A pixel stops when compositing the next Gaussian would
+// bring its transmittance below t_min; the block stops when all its pixels
+// have stopped (checked once per round with a block vote).
+//
+// Per pixel and Gaussian (both directions use the same arithmetic):
+//   dx = u - mean_x, dy = v - mean_y
+//   e2 = A dx^2 + B dx dy + C dy^2     (= power * log2 e)
+//   skip if e2 > 0;  e = e2 + F (F = log2 opacity); skip if e < log2 alpha_min
+//   alpha = min(alpha_max, 2^e)
+//
+// Backward: walks the pixel's range from its last composited Gaussian back
+// to the first, recovering T_i = T_{i+1} / (1 - alpha_i) from the final
+// transmittance instead of storing it, with accum = colour composited behind:
+//   dL/dc_i     = alpha_i T_i g
+//   dL/dalpha_i = T_i (c_i - accum) . g - T_final (bg . g) / (1 - alpha_i)
+//   dL/de       = dL/dalpha_i * alpha_i * ln 2   (0 where alpha is clamped)
+// giving dL/dF = dL/de, dL/dA = dL/de dx^2, dL/dB = dL/de dx dy,
+// dL/dC = dL/de dy^2, dL/dmean = -dL/de (2A dx + B dy, B dx + 2C dy).
+// The nine per-pixel values are summed over the thread's pixels, then over
+// the warp with shuffles (skipped when no lane contributes), and added to the
+// record's gradient with one float4/float4/float atomic triple per warp.
+#include "common.cuh"
+
+namespace gs {
+
+namespace {
+
+template <int TILE>
+struct Cfg {
+    static constexpr int NPIX = TILE * TILE;
+    static constexpr int NT = NPIX < 256 ? NPIX : 256;
+    static constexpr int PPT = NPIX / NT;
+};
+
+struct RenderParams {
+    float lmin;       // log2(alpha_min)
+    float amax, tmin;
+    float bg0, bg1, bg2;
+};
+
+// Exponent e2 = A dx^2 + B dx dy + C dy^2 with a fixed operation order
+// (no contraction freedom), shared by the forward and the backward.
+__device__ __forceinline__ float exponent2(float dx, float dy, float A, float B, float C) {
+    const float bdy = __fmul_rn(B, dy);
+    const float t = __fmaf_rn(A, dx, bdy);
+    const float cdy = __fmul_rn(C, dy);
+    const float q = __fmul_rn(cdy, dy);
+    return __fmaf_rn(dx, t, q);
+}
+
+// Pixel (lx, ly) of the tile handled by thread `tid` as its k-th pixel:
+// thread rows of TILE pixels, k stacks the thread over PPT row blocks.
+template <int TILE>
+__device__ __forceinline__ void pixel_of(int tid, int k, int &lx, int &ly) {
+    constexpr int NT = Cfg<TILE>::NT;
+    lx = tid % TILE;
+    ly = (tid / TILE) + k * (NT / TILE);
+}
+
+template <int TILE, int BATCH>
+__global__ void __launch_bounds__(Cfg<TILE>::NT)
+k_render_fwd(const gs_frame *__restrict__ frames, int F, const uint2 *__restrict__ ranges,
+             const uint32_t *__restrict__ vals, const float4 *__restrict__ splat,
+             const float *__restrict__ colors, RenderParams rp, Stats *__restrict__ stats,
+             float *__restrict__ out_rgb, float *__restrict__ out_T, int32_t *__restrict__ out_last) {
+    constexpr int NT = Cfg<TILE>::NT, PPT = Cfg<TILE>::PPT;
+    __shared__ float4 s0[BATCH];
+    __shared__ float4 s1[BATCH];
+    __shared__ float s2[BATCH];
+    __shared__ unsigned long long s_eval;
+    const int t = blockIdx.x;
+    const int f = frame_of_tile(frames, F, t);
+    const gs_frame &fr = frames[f];
+    const int W = fr.width, H = fr.height;
+    const int lt = t - fr.tile_offset;
+    const int tx = lt % fr.tiles_x, ty = lt / fr.tiles_x;
+    float px[PPT], py[PPT], T[PPT], c0[PPT], c1[PPT], c2[PPT];
+    int last[PPT];
+    bool done[PPT], inside[PPT];
+#pragma unroll
+    for (int k = 0; k < PPT; k++) {
+        int lx, ly;
+        pixel_of<TILE>(threadIdx.x, k, lx, ly);
+        const int u = tx * TILE + lx, v = ty * TILE + ly;
+        px[k] = (float)u;
+        py[k] = (float)v;
+        inside[k] = u < W && v < H;
+        done[k] = !inside[k];
+        T[k] = 1.f;
+        c0[k] = c1[k] = c2[k] = 0.f;
+        last[k] = 0;
+    }
+    if (threadIdx.x == 0) s_eval = 0;
+    const uint2 range = ranges[t];
+    const int n = (int)(range.y - range.x);
+    const long long rec0 = fr.record_offset;
+    const float *col = colors + 3 * (size_t)fr.gauss_offset;
+    unsigned evals = 0;
+    for (int b0 = 0; b0 < n; b0 += BATCH) {
+        bool mine_done = true;
+#pragma unroll
+        for (int k = 0; k < PPT; k++) mine_done &= done[k];
+        if (__syncthreads_and(mine_done)) break;
+        for (int i = threadIdx.x; i < BATCH; i += NT) {
+            const int j = b0 + i;
+            if (j < n) {
+                const uint32_t g = vals[range.x + j];
+                const long long r = rec0 + g;
+                const float4 a = splat[2 * r], b = splat[2 * r + 1];
+                s0[i] = a;
+                s1[i] = make_float4(b.x, b.y, __ldg(col + 3 * g), __ldg(col + 3 * g + 1));
+                s2[i] = __ldg(col + 3 * g + 2);
+            }
+        }
+        __syncthreads();
+        const int m = min(BATCH, n - b0);
+        for (int j = 0; j < m; j++) {
+            const float4 a = s0[j], b = s1[j];
+            const float cb = s2[j];
+#pragma unroll
+            for (int k = 0; k < PPT; k++) {
+                if (done[k]) continue;
+                evals++;
+                const float dx = px[k] - a.x, dy = py[k] - a.y;
+                const float e2 = exponent2(dx, dy, a.z, a.w, b.x);
+                if (e2 > 0.f) continue;
+                const float e = e2 + b.y;
+                if (e < rp.lmin) continue;
+                const float alpha = fminf(rp.amax, ex2_approx(e));
+                const float nT = T[k] * (1.f - alpha);
+                if (nT < rp.tmin) {
+                    done[k] = true;
+                    continue;
+                }
+                const float w = alpha * T[k];
+                c0[k] = fmaf(b.z, w, c0[k]);
+                c1[k] = fmaf(b.w, w, c1[k]);
+                c2[k] = fmaf(cb, w, c2[k]);
+                T[k] = nT;
+                last[k] = b0 + j + 1;
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int k = 0; k < PPT; k++) {
+        if (!inside[k]) continue;
+        int lx, ly;
+        pixel_of<TILE>(threadIdx.x, k, lx, ly);
+        const long long pix = fr.pixel_offset + (long long)(ty * TILE + ly) * W + (tx * TILE + lx);
+        out_rgb[3 * pix] = c0[k] + T[k] * rp.bg0;
+        out_rgb[3 * pix + 1] = c1[k] + T[k] * rp.bg1;
+        out_rgb[3 * pix + 2] = c2[k] + T[k] * rp.bg2;
+        out_T[pix] = T[k];
+        out_last[pix] = last[k];
+    }
+    // evaluation counter (for the roofline): warp sums, one atomic per warp
+    unsigned long long ev = evals;
+    for (int s = 16; s > 0; s >>= 1) ev += __shfl_xor_sync(0xffffffffu, ev, s);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) atomicAdd(&s_eval, ev);
+    __syncthreads();
+    if (threadIdx.x == 0) atomicAdd(&stats->eval_fwd, s_eval);
+}
+
+__device__ __forceinline__ float warp_sum_f(float v) {
+    for (int s = 16; s > 0; s >>= 1) v += __shfl_xor_sync(0xffffffffu, v, s);
+    return v;
+}
+
+template <int TILE, int BATCH>
+__global__ void __launch_bounds__(Cfg<TILE>::NT)
+k_render_bwd(const gs_frame *__restrict__ frames, int F, const uint2 *__restrict__ ranges,
+             const uint32_t *__restrict__ vals, const float4 *__restrict__ splat,
+             const float *__restrict__ colors, RenderParams rp, Stats *__restrict__ stats,
+             const float *__restrict__ in_T, const int32_t *__restrict__ in_last,
+             const float *__restrict__ dL_drgb, float4 *__restrict__ grad2d) {
+    constexpr int NT = Cfg<TILE>::NT, PPT = Cfg<TILE>::PPT;
+    __shared__ float4 s0[BATCH];
+    __shared__ float4 s1[BATCH];
+    __shared__ float s2[BATCH];
+    __shared__ long long s_rec[BATCH];
+    __shared__ int s_maxlast;
+    __shared__ unsigned long long s_eval;
+    const int t = blockIdx.x;
+    const int f = frame_of_tile(frames, F, t);
+    const gs_frame &fr = frames[f];
+    const int W = fr.width, H = fr.height;
+    const int lt = t - fr.tile_offset;
+    const int tx = lt % fr.tiles_x, ty = lt / fr.tiles_x;
+    float px[PPT], py[PPT], T[PPT], Tf[PPT], g0[PPT], g1[PPT], g2[PPT], bgd[PPT];
+    float a0[PPT], a1[PPT], a2[PPT];
+    int last[PPT];
+    if (threadIdx.x == 0) {
+        s_maxlast = 0;
+        s_eval = 0;
+    }
+    __syncthreads();
+    int mylast = 0;
+#pragma unroll
+    for (int k = 0; k < PPT; k++) {
+        int lx, ly;
+        pixel_of<TILE>(threadIdx.x, k, lx, ly);
+        const int u = tx * TILE + lx, v = ty * TILE + ly;
+        px[k] = (float)u;
+        py[k] = (float)v;
+        a0[k] = a1[k] = a2[k] = 0.f;
+        if (u < W && v < H) {
+            const long long pix = fr.pixel_offset + (long long)v * W + u;
+            Tf[k] = in_T[pix];
+            last[k] = in_last[pix];
+            g0[k] = dL_drgb[3 * pix];
+            g1[k] = dL_drgb[3 * pix + 1];
+            g2[k] = dL_drgb[3 * pix + 2];
+        } else {
+            Tf[k] = 1.f;
+            last[k] = 0;
+            g0[k] = g1[k] = g2[k] = 0.f;
+        }
+        T[k] = Tf[k];
+        bgd[k] = rp.bg0 * g0[k] + rp.bg1 * g1[k] + rp.bg2 * g2[k];
+        mylast = max(mylast, last[k]);
+    }
+    // the range of this tile; a pixel's start position never exceeds it
+    const uint2 range = ranges[t];
+    const int n = (int)(range.y - range.x);
+#pragma unroll
+    for (int k = 0; k < PPT; k++) last[k] = min(max(last[k], 0), n);
+    mylast = min(max(mylast, 0), n);
+    atomicMax(&s_maxlast, mylast);
+    __syncthreads();
+    const int maxlast = s_maxlast;
+    const long long rec0 = fr.record_offset;
+    const float *col = colors + 3 * (size_t)fr.gauss_offset;
+    const int lane = threadIdx.x & 31;
+    unsigned evals = 0;
+    for (int b_end = maxlast; b_end > 0; b_end -= BATCH) {
+        const int b0 = max(0, b_end - BATCH);
+        const int m = b_end - b0;
+        for (int i = threadIdx.x; i < m; i += NT) {
+            const uint32_t g = vals[range.x + b0 + i];
+            const long long r = rec0 + g;
+            const float4 a = splat[2 * r], b = splat[2 * r + 1];
+            s0[i] = a;
+            s1[i] = make_float4(b.x, b.y, __ldg(col + 3 * g), __ldg(col + 3 * g + 1));
+            s2[i] = __ldg(col + 3 * g + 2);
+            s_rec[i] = r;
+        }
+        __syncthreads();
+        for (int j = m - 1; j >= 0; j--) {
+            const int pos = b0 + j;
+            const float4 a = s0[j], b = s1[j];
+            const float cb = s2[j];
+            float dmx = 0.f, dmy = 0.f, dA = 0.f, dB = 0.f, dC = 0.f, dF = 0.f, dr = 0.f, dg = 0.f, db = 0.f;
+            bool any = false;
+#pragma unroll
+            for (int k = 0; k < PPT; k++) {
+                if (pos >= last[k]) continue;
+                evals++;
+                const float dx = px[k] - a.x, dy = py[k] - a.y;
+                const float e2 = exponent2(dx, dy, a.z, a.w, b.x);
+                if (e2 > 0.f) continue;
+                const float e = e2 + b.y;
+                if (e < rp.lmin) continue;
+                const float G = ex2_approx(e);
+                const float alpha = fminf(rp.amax, G);
+                const float om = 1.f - alpha;
+                T[k] = T[k] / om;
+                const float w = alpha * T[k];
+                dr = fmaf(w, g0[k], dr);
+                dg = fmaf(w, g1[k], dg);
+                db = fmaf(w, g2[k], db);
+                const float dalpha = T[k] * ((b.z - a0[k]) * g0[k] + (b.w - a1[k]) * g1[k] + (cb - a2[k]) * g2[k]) -
+                                     Tf[k] * bgd[k] / om;
+                a0[k] = fmaf(alpha, b.z - a0[k], a0[k]);
+                a1[k] = fmaf(alpha, b.w - a1[k], a1[k]);
+                a2[k] = fmaf(alpha, cb - a2[k], a2[k]);
+                any = true;
+                if (G > rp.amax) continue;
+                const float de = dalpha * alpha * kLn2;
+                dF += de;
+                dA = fmaf(de * dx, dx, dA);
+                dB = fmaf(de * dx, dy, dB);
+                dC = fmaf(de * dy, dy, dC);
+                dmx -= de * (2.f * a.z * dx + a.w * dy);
+                dmy -= de * (a.w * dx + 2.f * b.x * dy);
+            }
+            if (__any_sync(0xffffffffu, any)) {
+                dmx = warp_sum_f(dmx);
+                dmy = warp_sum_f(dmy);
+                dA = warp_sum_f(dA);
+                dB = warp_sum_f(dB);
+                dC = warp_sum_f(dC);
+                dF = warp_sum_f(dF);
+                dr = warp_sum_f(dr);
+                dg = warp_sum_f(dg);
+                db = warp_sum_f(db);
+                if (lane == 0) {
+                    const long long r = s_rec[j];
+                    atomicAdd(&grad2d[3 * r], make_float4(dmx, dmy, dA, dB));
+                    atomicAdd(&grad2d[3 * r + 1], make_float4(dC, dF, dr, dg));
+                    atomicAdd(&grad2d[3 * r + 2].x, db);
+                }
+            }
+        }
+        __syncthreads();
+    }
+    unsigned long long ev = evals;
+    for (int s = 16; s > 0; s >>= 1) ev += __shfl_xor_sync(0xffffffffu, ev, s);
+    if (lane == 0) atomicAdd(&s_eval, ev);
+    __syncthreads();
+    if (threadIdx.x == 0) atomicAdd(&stats->eval_bwd, s_eval);
+}
+
+template <int TILE, int BATCH>
+cudaError_t run_fwd(const gs_batch *b, const uint2 *ranges, const uint32_t *vals, const float4 *splat,
+                    const float *colors, RenderParams rp, Stats *stats, float *out_rgb, float *out_T,
+                    int32_t *out_last, cudaStream_t s) {
+    k_render_fwd<TILE, BATCH><<<b->num_tiles, Cfg<TILE>::NT, 0, s>>>(
+        b->frames_dev, b->num_frames, ranges, vals, splat, colors, rp, stats, out_rgb, out_T, out_last);
+    return cudaGetLastError();
+}
+
+template <int TILE, int BATCH>
+cudaError_t run_bwd(const gs_batch *b, const uint2 *ranges, const uint32_t *vals, const float4 *splat,
+                    const float *colors, RenderParams rp, Stats *stats, const float *in_T, const int32_t *in_last,
+                    const float *dL, float4 *grad2d, cudaStream_t s) {
+    k_render_bwd<TILE, BATCH><<<b->num_tiles, Cfg<TILE>::NT, 0, s>>>(
+        b->frames_dev, b->num_frames, ranges, vals, splat, colors, rp, stats, in_T, in_last, dL, grad2d);
+    return cudaGetLastError();
+}
+
+RenderParams make_params(const gs_opts *o) {
+    RenderParams rp;
+    rp.lmin = log2f(o->alpha_min);
+    rp.amax = o->alpha_max;
+    rp.tmin = o->t_min;
+    rp.bg0 = o->bg[0];
+    rp.bg1 = o->bg[1];
+    rp.bg2 = o->bg[2];
+    return rp;
+}
+
+}  // namespace
+
+#define GS_DISPATCH(TILE_, BATCH_, CALL)                          \
+    switch (TILE_ * 1000 + BATCH_) {                               \
+    case 8064: return CALL(8, 64);                                 \
+    case 8128: return CALL(8, 128);                                \
+    case 8256: return CALL(8, 256);                                \
+    case 16064: return CALL(16, 64);                               \
+    case 16128: return CALL(16, 128);                              \
+    case 16256: return CALL(16, 256);                              \
+    case 32064: return CALL(32, 64);                               \
+    case 32128: return CALL(32, 128);                              \
+    case 32256: return CALL(32, 256);                              \
+    default: return cudaErrorInvalidValue;                         \
+    }
+
+cudaError_t launch_render_fwd(const gs_batch *b, const gs_opts *o, const uint2 *ranges, const uint32_t *vals,
+                              const float4 *splat, const float *colors, Stats *stats, float *out_rgb,
+                              float *out_T, int32_t *out_last, cudaStream_t s) {
+    if (b->num_tiles == 0) return cudaSuccess;
+    const RenderParams rp = make_params(o);
+#define GS_FWD(T_, B_) run_fwd<T_, B_>(b, ranges, vals, splat, colors, rp, stats, out_rgb, out_T, out_last, s)
+    GS_DISPATCH(o->tile, o->batch, GS_FWD)
+#undef GS_FWD
+}
+
+cudaError_t launch_render_bwd(const gs_batch *b, const gs_opts *o, const uint2 *ranges, const uint32_t *vals,
+                              const float4 *splat, const float *colors, Stats *stats, const float *in_T,
+                              const int32_t *in_last, const float *dL, float4 *grad2d, cudaStream_t s) {
+    if (b->num_tiles == 0) return cudaSuccess;
+    const RenderParams rp = make_params(o);
+#define GS_BWD(T_, B_) run_bwd<T_, B_>(b, ranges, vals, splat, colors, rp, stats, in_T, in_last, dL, grad2d, s)
+    GS_DISPATCH(o->tile, o->batch, GS_BWD)
+#undef GS_BWD
+}
+
+}  // namespace gs

@@ -1,0 +1,71 @@
+"""The C-ABI library builds for sm_103a, loads without a GPU, exports every
+function include/gs3dcalib.h declares, and its host-only planning entry
+points behave (no kernel is launched here)."""
+import ctypes as C
+import re
+
+import pytest
+
+from paper_2403_11577_gb300 import build, capi
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return capi.lib()
+
+
+def test_exports_every_declared_symbol(lib):
+    declared = capi.declared_symbols()
+    assert len(declared) >= 14
+    for name in declared:
+        assert hasattr(lib, name), name
+    # and the binding wraps every one of them under the same name
+    for name in declared:
+        assert hasattr(capi, name), name
+
+
+def test_struct_layout_and_version(lib):
+    assert capi.gs_version().startswith("gs3dcalib")
+    sizes = (C.c_size_t * 4)()
+    assert lib.gs_struct_sizes(sizes, 4) == 4
+    assert list(sizes) == [C.sizeof(capi.GsFrame), C.sizeof(capi.GsOpts), C.sizeof(capi.GsBatch),
+                           C.sizeof(capi.GsStats)]
+
+
+def test_batch_init_rejects_bad_frames_without_device(lib):
+    frames = (capi.GsFrame * 1)()
+    frames[0].width, frames[0].height = 0, 10  # invalid size
+    b = capi.GsBatch()
+    code = lib.gs_batch_init(frames, 1, 10, 1, 1, 16, 1000, C.c_void_p(0x1000), C.byref(b))
+    assert code == capi.GS_ERR_INVALID_ARG
+    frames[0].width = 64
+    for tile in (7, 12, 64):
+        assert lib.gs_batch_init(frames, 1, 10, 1, 1, tile, 1000, C.c_void_p(0x1000), C.byref(b)) == \
+            capi.GS_ERR_INVALID_ARG
+    frames[0].camera_id = 3  # beyond num_cameras
+    assert lib.gs_batch_init(frames, 1, 10, 1, 1, 16, 1000, C.c_void_p(0x1000), C.byref(b)) == \
+        capi.GS_ERR_INVALID_ARG
+
+
+def test_workspace_size_is_host_only(lib):
+    b = capi.GsBatch()
+    b.frames_dev = 0x1000
+    b.num_frames, b.num_cameras, b.num_trajs, b.num_gaussians = 8, 1, 1, 1_000_000
+    b.tile, b.num_tiles = 16, 8 * 88 * 24
+    b.num_records, b.num_pixels, b.pair_capacity = 8_000_000, 8 * 1408 * 376, 100_000_000
+    n = capi.gs_workspace_size(b)
+    # records (8+4+32+48 B) + pairs (2 x 12 B) dominate
+    assert n >= 8_000_000 * 92 + 100_000_000 * 24
+    offs = capi.gs_workspace_offsets(b)
+    assert len(offs) == 10 and offs == sorted(offs) and all(o % 256 == 0 for o in offs)
+    b.num_frames = 0
+    assert lib.gs_workspace_size(C.byref(b)) == 0
+
+
+def test_header_documents_each_entry_point():
+    text = open(build.INCLUDE + "/gs3dcalib.h").read()
+    for name in capi.declared_symbols():
+        # a comment block directly precedes every declaration
+        m = re.search(r"\*/\s*\n(?:[^\n]*\n)?[^\n]*\b%s\s*\(" % name, text)
+        assert m, name

@@ -1,0 +1,472 @@
+"""Parity of the CUDA path (through the C-ABI) with the FP64 CPU oracle.
+
+Tolerances (from the stated targets): rendered colour and transmittance
+within 1e-4 max-abs on pixels the oracle does not flag as lying on a
+float32/float64 discontinuity; the last composited Gaussian identical there;
+tile binning and sort order bit-exact; gradients within 1e-3 relative L2 per
+parameter group.
+"""
+import copy
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2403_11577_gb300 import capi, render, scenes
+
+from _util import ensure_built, ext_delta, last_gaussian_ids, oracle_opts, rel_l2, sample_pixels, setup
+
+pytestmark = pytest.mark.gpu
+
+COLOUR_TOL = 1e-4
+GRAD_TOL = 1e-3
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    ensure_built()
+
+
+def _tiny(width=64, height=48, seed=0, n=64):
+    return scenes.tiny_problem(seed=seed, n=n, width=width, height=height)
+
+
+# ------------------------------------------------------------------ pose
+
+
+@pytest.mark.parametrize("delta", [0.0, 0.037, -0.05])
+def test_pose_compose_matches_oracle(delta):
+    p = scenes.batched_problem(n=2000, frames=8)
+    p.ext = np.array([[0.3, -1.1, 0.4, 1.0, 0.3, -0.2]])
+    p.delta = np.array([delta])
+    # a turning trajectory so that SLERP matters
+    sc = p.scenes[0]
+    yaw = np.linspace(0, 0.8, len(sc.traj_t))
+    sc.traj_q = np.stack([np.cos(yaw / 2), 0 * yaw, 0.1 * np.sin(yaw / 2), np.sin(yaw / 2)], 1)
+    scene, plan, ext, dl = setup(p)
+    plan.pose(scene, ext, dl)
+    pose64 = plan.ws_view(capi.WS_POSE64, torch.float64, 32 * 8).cpu().numpy().reshape(8, 32)
+    pose32 = plan.ws_view(capi.WS_POSE32, torch.float32, 16 * 8).cpu().numpy().reshape(8, 16)
+    for i, f in enumerate(p.frames):
+        R, t = oracle.frame_pose(sc, p.ext[0], delta, f.timestamp)
+        c = -R.T @ t
+        np.testing.assert_allclose(pose64[i, :9].reshape(3, 3), R, atol=1e-12)
+        np.testing.assert_allclose(pose64[i, 9:12], c, atol=1e-9)
+        hi, lo = pose32[i, 9:12].astype(np.float64), pose32[i, 12:15].astype(np.float64)
+        np.testing.assert_allclose(hi + lo, c, atol=1e-9 * (1 + np.abs(c)))
+
+
+# -------------------------------------------------------------- projection
+
+
+def test_project_matches_oracle():
+    p = scenes.lidar_frame_problem(n=20000)
+    opts = render.RenderOptions()
+    scene, plan, ext, dl = setup(p, opts)
+    plan.pose(scene, ext, dl)
+    plan.project(scene)
+    n = p.scenes[0].n
+    rect = plan.ws_view(capi.WS_RECT, torch.int32, 2 * n).cpu().numpy().view(np.uint32).reshape(n, 2)
+    splat = plan.ws_view(capi.WS_SPLAT, torch.float32, 8 * n).cpu().numpy().reshape(n, 8)
+    gx0, gy0 = rect[:, 0] & 0xFFFF, rect[:, 0] >> 16
+    gx1, gy1 = rect[:, 1] & 0xFFFF, rect[:, 1] >> 16
+    gvis = (gx0 <= gx1) & (gy0 <= gy1)
+    R, t = oracle.frame_pose(p.scenes[0], p.ext[0], 0.0, 0.0)
+    o = oracle.project(p.scenes[0], p.frames[0].camera, R, t, oracle_opts(opts), tile=16)
+    r = o["rect"]
+    ovis = (r[:, 0] <= r[:, 2]) & (r[:, 1] <= r[:, 3])
+    assert gvis.sum() > 1000
+    # every Gaussian the oracle keeps is kept (the GPU rect is a guarded superset)
+    assert np.all(gvis[ovis])
+    # extra GPU rects only where the oracle's extent sits within the guard of a tile edge
+    extra = gvis & ~ovis
+    assert extra.sum() <= max(3, 1e-3 * gvis.sum())
+    k = ovis
+    log2e = 1.0 / math.log(2.0)
+    np.testing.assert_allclose(splat[k, 0], o["mean"][k, 0], rtol=0, atol=2e-3)
+    np.testing.assert_allclose(splat[k, 1], o["mean"][k, 1], rtol=0, atol=2e-3)
+    conic = np.stack([splat[k, 2] / (-0.5 * log2e), splat[k, 3] / (-log2e), splat[k, 4] / (-0.5 * log2e)], 1)
+    scale = np.abs(o["conic"][k]).max(1, keepdims=True)
+    assert np.max(np.abs(conic - o["conic"][k]) / scale) < 1e-4
+    np.testing.assert_allclose(splat[k, 6], o["opacity"][k], rtol=1e-5)
+    np.testing.assert_allclose(splat[k, 7], o["depth"][k], rtol=1e-5)
+    # rect: GPU contains the oracle's; equal unless an extent edge is near a tile boundary
+    ext_ = o["extent"][k]
+    m = o["mean"][k]
+    def near_edge(v, e):
+        return np.abs((v / 16.0) - np.round(v / 16.0)) * 16.0 < 2e-4 * e + 0.02
+    near = (near_edge(m[:, 0] - ext_[:, 0], ext_[:, 0]) | near_edge(m[:, 0] + ext_[:, 0], ext_[:, 0]) |
+            near_edge(m[:, 1] - ext_[:, 1], ext_[:, 1]) | near_edge(m[:, 1] + ext_[:, 1], ext_[:, 1]))
+    g_r = np.stack([gx0[k], gy0[k], gx1[k], gy1[k]], 1).astype(np.int64)
+    o_r = r[k].astype(np.int64)
+    assert np.all(g_r[:, :2] <= o_r[:, :2]) and np.all(g_r[:, 2:] >= o_r[:, 2:])
+    same = np.all(g_r == o_r, axis=1)
+    assert np.all(same | near)
+
+
+# ---------------------------------------------------------- bin and sort
+
+
+def _write_records(plan, rect, depth):
+    n = len(depth)
+    packed = np.zeros((n, 2), np.uint32)
+    packed[:, 0] = (rect[:, 0].astype(np.uint32) & 0xFFFF) | ((rect[:, 1].astype(np.uint32) & 0xFFFF) << 16)
+    packed[:, 1] = (rect[:, 2].astype(np.uint32) & 0xFFFF) | ((rect[:, 3].astype(np.uint32) & 0xFFFF) << 16)
+    plan.ws_view(capi.WS_RECT, torch.int32, 2 * n).copy_(torch.from_numpy(packed.view(np.int32).ravel()))
+    plan.ws_view(capi.WS_DEPTH, torch.float32, n).copy_(torch.from_numpy(depth))
+
+
+def _bin_plan(frames_wh, counts, tile=16, cap=None):
+    frames = [dict(width=w, height=h, fx=100.0, fy=100.0, cx=w / 2, cy=h / 2, camera_id=0, traj_id=0,
+                   gauss_offset=0, gauss_count=c, timestamp=0.0) for (w, h), c in zip(frames_wh, counts)]
+    opts = render.RenderOptions(tile=tile)
+    return render.Plan(frames, max(counts), 1, 1, opts, cap if cap is not None else 4_000_000)
+
+
+@pytest.mark.parametrize("tile", [8, 16, 32])
+def test_bin_sort_bit_exact_synthetic(tile):
+    """Seeded synthetic records (with exact depth ties and empty rects)
+    against the oracle's binning + stable sort."""
+    frames_wh = [(1408, 376), (300, 200), (77, 50), (1920, 1080)]
+    counts = [30000, 5000, 700, 20000]
+    plan = _bin_plan(frames_wh, counts, tile)
+    tiles = [((w + tile - 1) // tile, (h + tile - 1) // tile) for w, h in frames_wh]
+    rect, depth = scenes.random_splat_records(5, tiles, counts, tie_fraction=0.3, max_extent_tiles=7)
+    _write_records(plan, rect, depth)
+    plan.bin_sort()
+    st = plan.stats()
+    keys, vals, ranges = oracle.bin_sort(tiles, counts, rect, depth)
+    P = len(keys)
+    assert st.num_pairs == P and st.status == 0
+    gk = plan.ws_view(capi.WS_KEYS, torch.int64, P).cpu().numpy().view(np.uint64)
+    gv = plan.ws_view(capi.WS_VALS, torch.int32, P).cpu().numpy().view(np.uint32)
+    gr = plan.ws_view(capi.WS_RANGES, torch.int32, 2 * plan.batch.num_tiles).cpu().numpy().view(np.uint32)
+    np.testing.assert_array_equal(gk, keys)
+    np.testing.assert_array_equal(gv, vals)
+    np.testing.assert_array_equal(gr.reshape(-1, 2).astype(np.int64), ranges)
+
+
+def test_bin_sort_overflow_sets_status():
+    frames_wh = [(320, 240)]
+    counts = [2000]
+    plan = _bin_plan(frames_wh, counts, 16, cap=1000)
+    tiles = [(20, 15)]
+    rect, depth = scenes.random_splat_records(1, tiles, counts)
+    _write_records(plan, rect, depth)
+    plan.bin_sort()
+    st = plan.stats()
+    assert st.status & capi.GS_DEV_PAIR_OVERFLOW and st.num_pairs == 0
+    capi.gs_reset_status(plan.batch, plan.ws)
+    assert plan.stats().status == 0
+
+
+def test_bin_sort_empty_and_single():
+    plan = _bin_plan([(16, 16), (5, 3)], [3, 1], 16)
+    rect = np.array([[1, 1, 0, 0], [0, 0, 0, 0], [1, 1, 0, 0], [0, 0, 0, 0]], np.int32)
+    depth = np.array([1.0, 2.0, 3.0, 0.5], np.float32)
+    _write_records(plan, rect, depth)
+    plan.bin_sort()
+    keys, vals, ranges = oracle.bin_sort([(1, 1), (1, 1)], [3, 1], rect, depth)
+    assert plan.stats().num_pairs == 2
+    gk = plan.ws_view(capi.WS_KEYS, torch.int64, 2).cpu().numpy().view(np.uint64)
+    np.testing.assert_array_equal(gk, keys)
+
+
+# ----------------------------------------------------------------- render
+
+
+def _compare_frame(plan, p, fi, opts, ext=None, delta=None, pixels=None):
+    f = p.frames[fi]
+    sc = p.scenes[f.scene_id]
+    e = (p.ext if ext is None else ext)[f.camera_id]
+    d = float((p.delta if delta is None else delta)[f.camera_id])
+    cam = f.camera
+    rgb_o, T_o, last_o, flags = oracle.render(sc, f, e, d, oracle_opts(opts), pixels)
+    rgb_g = plan.image(plan.rgb, fi).cpu().numpy().reshape(-1, 3)
+    T_g = plan.image(plan.T, fi).cpu().numpy().reshape(-1)
+    gid = last_gaussian_ids(plan, fi)
+    if pixels is not None:
+        idx = pixels[:, 1] * cam.width + pixels[:, 0]
+        rgb_g, T_g, gid = rgb_g[idx], T_g[idx], gid[idx]
+    ok = flags == 0
+    assert ok.mean() > 0.99, "too many flagged pixels: %d" % (~ok).sum()
+    err = np.abs(rgb_g[ok] - rgb_o[ok]).max()
+    assert err <= COLOUR_TOL, err
+    assert np.abs(T_g[ok] - T_o[ok]).max() <= COLOUR_TOL
+    np.testing.assert_array_equal(gid[ok], last_o[ok])
+    return ok
+
+
+@pytest.mark.parametrize("size", [(64, 48), (70, 45), (16, 16), (1, 1), (33, 130)])
+def test_render_fwd_tiny(size):
+    p = _tiny(*size)
+    opts = render.RenderOptions(bg=(0.1, 0.2, 0.3))
+    scene, plan, ext, dl = setup(p, opts)
+    plan.forward(scene, ext, dl)
+    assert plan.stats().status == 0
+    _compare_frame(plan, p, 0, opts)
+
+
+@pytest.mark.parametrize("tile,batch", [(8, 64), (8, 256), (16, 64), (16, 128), (16, 256), (32, 64), (32, 256)])
+def test_render_fwd_tile_batch_independent(tile, batch):
+    """Tile edge and shared-memory batch do not change the image (the same
+    Gaussians meet each pixel in the same order), bit for bit."""
+    p = _tiny(97, 61, seed=3, n=300)
+    ref_opts = render.RenderOptions(tile=16, batch=128)
+    scene, ref, ext, dl = setup(p, ref_opts)
+    ref.forward(scene, ext, dl)
+    opts = render.RenderOptions(tile=tile, batch=batch)
+    plan = render.Plan.for_problem(p, scene, opts)
+    plan.forward(scene, ext, dl)
+    assert torch.equal(plan.rgb, ref.rgb) and torch.equal(plan.T, ref.T)
+    _compare_frame(plan, p, 0, opts)
+
+
+def test_render_fwd_deterministic():
+    p = _tiny(128, 96, seed=4, n=500)
+    scene, plan, ext, dl = setup(p)
+    plan.forward(scene, ext, dl)
+    a = (plan.rgb.clone(), plan.T.clone(), plan.last.clone())
+    plan.forward(scene, ext, dl)
+    assert torch.equal(a[0], plan.rgb) and torch.equal(a[1], plan.T) and torch.equal(a[2], plan.last)
+
+
+def test_render_all_culled_and_opacity_zero():
+    p = _tiny()
+    opts = render.RenderOptions(bg=(0.25, 0.5, 0.75))
+    p2 = copy.deepcopy(p)
+    p2.scenes[0].logit_opacity = np.full(p2.scenes[0].n, -30.0, np.float32)
+    scene, plan, ext, dl = setup(p2, opts)
+    plan.forward(scene, ext, dl)
+    assert plan.stats().num_pairs == 0
+    rgb = plan.rgb.cpu().numpy()
+    assert np.all(rgb == np.array([0.25, 0.5, 0.75], np.float32))
+    assert torch.all(plan.T == 1) and torch.all(plan.last == 0)
+    # everything behind the camera
+    p3 = copy.deepcopy(p)
+    p3.scenes[0].X = p3.scenes[0].X * np.array([1, 1, -1], np.float32)
+    scene, plan, ext, dl = setup(p3, opts)
+    plan.forward(scene, ext, dl)
+    assert plan.stats().num_pairs == 0 and torch.all(plan.T == 1)
+
+
+def test_render_fwd_lidar_frame_sampled():
+    """Full-size single LiDAR frame (200k Gaussians, 1408x376, tile 16) on
+    sampled pixels the oracle composites one by one."""
+    p = scenes.lidar_frame_problem()
+    opts = render.RenderOptions()
+    scene, plan, ext, dl = setup(p, opts)
+    plan.forward(scene, ext, dl)
+    st = plan.stats()
+    assert st.status == 0 and st.num_pairs > 100000
+    pix = sample_pixels(np.random.default_rng(0), p.frames[0].camera, 400)
+    _compare_frame(plan, p, 0, opts, pixels=pix)
+
+
+def test_render_fwd_uneven_batch_sampled():
+    """Three scenes of uneven size and resolution in one launch per stage."""
+    p = scenes.uneven_problem(sizes=(3000, 20000, 8000), frames_per_scene=2)
+    opts = render.RenderOptions()
+    scene, plan, ext, dl = setup(p, opts)
+    plan.forward(scene, ext, dl)
+    rng = np.random.default_rng(1)
+    for fi, f in enumerate(p.frames):
+        _compare_frame(plan, p, fi, opts, pixels=sample_pixels(rng, f.camera, 120))
+
+
+# --------------------------------------------------------------- backward
+
+
+def _grads_vs_oracle(p, opts, W_frames, pixels=None, groups=None):
+    """Run the CUDA forward + backward with dL/dC = W and compare all
+    gradients with the oracle's."""
+    scene, plan, ext, dl = setup(p, opts)
+    plan.forward(scene, ext, dl)
+    dL = torch.zeros_like(plan.rgb)
+    for fi in range(len(p.frames)):
+        plan.image(dL, fi).copy_(torch.from_numpy(W_frames[fi].astype(np.float32)).view(plan.image(dL, fi).shape))
+    g = render.empty_grads(scene, p.num_cameras)
+    plan.backward(scene, dL, g, ext)
+    og_scenes, od_ext, od_delta = oracle.backward_problem(p, [w.reshape(-1, 3) for w in W_frames], oracle_opts(opts))
+    res = {}
+    off = 0
+    for s, og in enumerate(og_scenes):
+        n = p.scenes[s].n
+        for k in ("quat", "log_scale", "logit_opacity", "rgb"):
+            res.setdefault(k, [[], []])
+            res[k][0].append(g[k][off:off + n].cpu().numpy().reshape(-1))
+            res[k][1].append(np.asarray(og[k]).reshape(-1))
+        off += n
+    out = {k: rel_l2(np.concatenate(v[0]), np.concatenate(v[1])) for k, v in res.items()}
+    ge = g["ext"].cpu().numpy()
+    out["ext_rot"] = rel_l2(ge[:, :3], od_ext[:, :3])
+    out["ext_trans"] = rel_l2(ge[:, 3:], od_ext[:, 3:])
+    out["delta"] = rel_l2(g["delta"].cpu().numpy(), od_delta)
+    return out
+
+
+def _weights(p, opts, seed, density=1.0):
+    """Random dL/dC per frame, zero on pixels the oracle flags."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for f in p.frames:
+        cam = f.camera
+        flags = oracle.render(p.scenes[f.scene_id], f, p.ext[f.camera_id], float(p.delta[f.camera_id]),
+                              oracle_opts(opts))[3]
+        W = rng.normal(size=(cam.height * cam.width, 3))
+        if density < 1.0:
+            W *= (rng.uniform(size=(cam.height * cam.width, 1)) < density)
+        W[flags != 0] = 0
+        out.append(W)
+    return out
+
+
+@pytest.mark.parametrize("size,bg", [((64, 48), (0, 0, 0)), ((70, 45), (0.2, 0.5, 0.8))])
+def test_render_bwd_tiny(size, bg):
+    p = _tiny(*size)
+    p.ext = p.ext_target.copy()  # a non-identity extrinsic
+    p.delta = np.array([0.013])
+    opts = render.RenderOptions(bg=bg)
+    errs = _grads_vs_oracle(p, opts, _weights(p, opts, 2))
+    bad = {k: v for k, v in errs.items() if not v <= GRAD_TOL}
+    assert not bad, errs
+
+
+def test_render_bwd_opaque_early_termination():
+    p = _tiny(80, 60, seed=5, n=200)
+    p.scenes[0].logit_opacity = p.scenes[0].logit_opacity + 4.0
+    opts = render.RenderOptions(bg=(0.3, 0.3, 0.3))
+    errs = _grads_vs_oracle(p, opts, _weights(p, opts, 3))
+    bad = {k: v for k, v in errs.items() if not v <= GRAD_TOL}
+    assert not bad, errs
+
+
+def test_render_bwd_lidar_frame_sparse_pixels():
+    """Full-size LiDAR frame; dL/dC non-zero on 300 sampled pixels only, so
+    the oracle's backward over those pixels is the exact reference."""
+    p = scenes.lidar_frame_problem()
+    opts = render.RenderOptions()
+    cam = p.frames[0].camera
+    rng = np.random.default_rng(7)
+    pix = np.unique(sample_pixels(rng, cam, 300), axis=0)
+    rgb_o, _, _, flags = oracle.render(p.scenes[0], p.frames[0], p.ext[0], 0.0, oracle_opts(opts), pix)
+    pix = pix[flags == 0]
+    Wp = rng.normal(size=(len(pix), 3))
+    W = np.zeros((cam.height * cam.width, 3))
+    W[pix[:, 1] * cam.width + pix[:, 0]] = Wp
+    scene, plan, ext, dl = setup(p, opts)
+    plan.forward(scene, ext, dl)
+    dL = torch.from_numpy(W.astype(np.float32)).cuda()
+    g = render.empty_grads(scene, 1)
+    plan.backward(scene, dL, g, ext)
+    og = oracle.backward(p.scenes[0], p.frames[0], p.ext[0], 0.0, Wp, oracle_opts(opts), pixels=pix)
+    for k in ("quat", "log_scale", "logit_opacity", "rgb"):
+        assert rel_l2(g[k].cpu().numpy(), og[k]) <= GRAD_TOL, k
+    ge = g["ext"].cpu().numpy()[0]
+    assert rel_l2(ge[:3], og["ext"][:3]) <= GRAD_TOL
+    assert rel_l2(ge[3:], og["ext"][3:]) <= GRAD_TOL
+    assert rel_l2(g["delta"].cpu().numpy(), og["delta"]) <= GRAD_TOL
+
+
+def test_render_bwd_uneven_batch():
+    p = scenes.uneven_problem(sizes=(2000, 6000, 3000), frames_per_scene=2,
+                              cams=(scenes.Camera(176, 47, 69.0, 69.0, 85.0, 30.0),
+                                    scenes.Camera(352, 94, 138.0, 138.0, 170.0, 59.0),
+                                    scenes.Camera(240, 135, 120.0, 120.0, 119.5, 67.5)))
+    p.delta = np.array([0.01, -0.02, 0.03])
+    opts = render.RenderOptions()
+    errs = _grads_vs_oracle(p, opts, _weights(p, opts, 4))
+    bad = {k: v for k, v in errs.items() if not v <= GRAD_TOL}
+    assert not bad, errs
+
+
+def test_autograd_function_matches_oracle():
+    p = _tiny(70, 45)
+    p.ext = p.ext_target.copy()
+    opts = render.RenderOptions()
+    scene, plan, ext, dl = setup(p, opts)
+    params = [t.clone().requires_grad_(True) for t in (scene.quat, scene.log_scale, scene.logit_opacity, scene.rgb)]
+    e = ext.clone().requires_grad_(True)
+    d = dl.clone().requires_grad_(True)
+    W = _weights(p, opts, 9)[0]
+    Wt = torch.from_numpy(W.astype(np.float32)).cuda()
+    out = render.render(plan, scene, *params, e, d)
+    (out * Wt).sum().backward()
+    og = oracle.backward(p.scenes[0], p.frames[0], p.ext[0], 0.0, W, oracle_opts(opts))
+    for t, k in zip(params, ("quat", "log_scale", "logit_opacity", "rgb")):
+        assert rel_l2(t.grad.cpu().numpy(), og[k]) <= GRAD_TOL, k
+    assert rel_l2(e.grad.cpu().numpy()[0], og["ext"]) <= GRAD_TOL
+    assert rel_l2(d.grad.cpu().numpy(), og["delta"]) <= GRAD_TOL
+
+
+# -------------------------------------------------------- loss and steps
+
+
+def test_loss_l1_matches_oracle():
+    p = _tiny()
+    scene, plan, ext, dl = setup(p)
+    rng = np.random.default_rng(0)
+    a = torch.from_numpy(rng.uniform(size=(plan.batch.num_pixels, 3)).astype(np.float32)).cuda()
+    b = torch.from_numpy(rng.uniform(size=(plan.batch.num_pixels, 3)).astype(np.float32)).cuda()
+    b[:7] = a[:7]
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    grad = torch.empty_like(a)
+    capi.gs_loss_l1(plan.batch, a, b, 1.0, loss, grad, plan.ws)
+    lo, go = oracle.l1(a.cpu().numpy().astype(np.float64), b.cpu().numpy().astype(np.float64))
+    assert abs(loss.item() - lo) <= 1e-12 * max(1, lo) + 1e-9
+    np.testing.assert_allclose(grad.cpu().numpy(), go, rtol=1e-6, atol=0)
+
+
+def _small_batched():
+    p = scenes.batched_problem(n=40000, frames=4)
+    for f in p.frames:
+        f.camera = scenes.Camera(352, 94, 138.0, 138.0, 170.5, 59.5)
+    return p
+
+
+def test_graph_replay_matches_eager_and_per_frame():
+    p = _small_batched()
+    opts = render.RenderOptions()
+    scene, plan, ext, dl = setup(p, opts)
+    tgt_ext, tgt_delta = ext_delta(p)
+    tgt_ext = tgt_ext.clone()
+    tgt_ext[0, 3] += 0.05
+    plan.forward(scene, tgt_ext, tgt_delta)
+    target = plan.rgb.clone()
+    eager = render.CalibStep(plan, scene, target, ext, dl, graph=False)
+    eager()
+    e_loss = eager.loss.clone()
+    e_grads = {k: v.clone() for k, v in eager.grads.items()}
+    plan2 = render.Plan.for_problem(p, scene, opts)
+    step = render.CalibStep(plan2, scene, target, ext, dl, graph=True)
+    step()
+    torch.cuda.synchronize()
+    assert torch.equal(plan2.rgb, plan.rgb)
+    assert abs(step.loss.item() - e_loss.item()) <= 1e-12
+    for k in e_grads:
+        assert rel_l2(step.grads[k].cpu().numpy(), e_grads[k].cpu().numpy()) <= 1e-5, k
+    pf = render.PerFrameStep(p, scene, target, ext, dl, opts)
+    pf()
+    torch.cuda.synchronize()
+    off = 0
+    for q in pf.plans:
+        n = q.batch.num_pixels
+        assert torch.equal(q.rgb, plan.rgb[off:off + n])
+        off += n
+    for k in e_grads:
+        assert rel_l2(pf.grads[k].cpu().numpy(), e_grads[k].cpu().numpy()) <= 1e-4, k
+
+
+def test_invalid_arguments_rejected():
+    p = _tiny()
+    scene, plan, ext, dl = setup(p)
+    bad = render.RenderOptions(tile=16, batch=100).c()
+    with pytest.raises(capi.GsError):
+        capi.gs_project(plan.batch, scene.X, scene.quat, scene.log_scale, scene.logit_opacity, bad, plan.ws)
+    with pytest.raises(capi.GsError):
+        capi.gs_bin_sort(plan.batch, render.RenderOptions(tile=8).c(), plan.ws)
+    with pytest.raises(ValueError):
+        capi.gs_project(plan.batch, scene.X.cpu(), scene.quat, scene.log_scale, scene.logit_opacity,
+                        plan.copts, plan.ws)
