@@ -164,6 +164,15 @@ gs_status gs_read_stats(const gs_batch *batch, const void *ws_dev, void *stream,
 /* Clear the device status bits (async). */
 gs_status gs_reset_status(const gs_batch *batch, void *ws_dev, void *stream);
 
+/* kernels selectable by gs_profile_events */
+enum {
+    GS_PROF_NONE = 0,
+    GS_PROF_PROJECT = 1,
+    GS_PROF_BIN_SORT = 2,
+    GS_PROF_RENDER_FWD = 3,
+    GS_PROF_RENDER_BWD = 4,
+    GS_PROF_PROJECT_BWD = 5
+};
 /* Kernel timing hook.  After this call, every launch of the selected
  * kernel is bracketed by cudaEventRecordWithFlags(start/stop, stream,
  * cudaEventRecordExternal) on the kernel's own stream, so the events also
@@ -174,14 +183,6 @@ gs_status gs_reset_status(const gs_batch *batch, void *ws_dev, void *stream);
  * GS_PROF_PROJECT_BWD.  The events are cudaEvent_t handles owned by the
  * caller (created with timing enabled).  Process-wide setting; not thread
  * safe.  Errors: GS_ERR_INVALID_ARG for an unknown kernel or NULL events. */
-enum {
-    GS_PROF_NONE = 0,
-    GS_PROF_PROJECT = 1,
-    GS_PROF_BIN_SORT = 2,
-    GS_PROF_RENDER_FWD = 3,
-    GS_PROF_RENDER_BWD = 4,
-    GS_PROF_PROJECT_BWD = 5
-};
 gs_status gs_profile_events(int32_t kernel, void *start_event, void *stop_event);
 
 /* ----------------------------------------------------------- hot path -- */
