@@ -24,7 +24,7 @@ _lib = None
 class OrOpts(C.Structure):
     _fields_ = [("near_z", C.c_double), ("lowpass", C.c_double), ("alpha_min", C.c_double),
                 ("alpha_max", C.c_double), ("t_min", C.c_double), ("scale_max", C.c_double),
-                ("bg", C.c_double * 3)]
+                ("bg", C.c_double * 3), ("frustum_margin", C.c_double)]
 
 
 class OrCam(C.Structure):
@@ -46,10 +46,11 @@ class Opts:
     t_min: float = 1e-4
     scale_max: float = float("inf")
     bg: tuple = (0.0, 0.0, 0.0)
+    frustum_margin: float = 0.15
 
     def c(self) -> OrOpts:
         return OrOpts(self.near_z, self.lowpass, self.alpha_min, self.alpha_max, self.t_min,
-                      self.scale_max, (C.c_double * 3)(*self.bg))
+                      self.scale_max, (C.c_double * 3)(*self.bg), self.frustum_margin)
 
 
 SMOOTH = Opts(alpha_min=0.0, alpha_max=1.0, t_min=0.0)
@@ -153,12 +154,14 @@ def render(scene, frame, ext, delta, opts: Opts = Opts(), pixels=None):
 
 def backward(scene, frame, ext, delta, dL_dC, opts: Opts = Opts(), pixels=None):
     """Gradients of sum_p dL_dC[p] . C(p) for one frame: Gaussian parameters
-    (q, log_scale, logit_opacity, rgb) and calibration (ext[6], delta)."""
+    (q, log_scale, logit_opacity, rgb), calibration (ext[6], delta), and the
+    per-Gaussian 2D gradients (mean2d, conic, opacity)."""
     X, q, ls, lo, rgb = _gauss(scene)
     pix, npix = _pix(pixels)
     n = scene.n
     g = dict(quat=np.zeros((n, 4)), log_scale=np.zeros((n, 3)), logit_opacity=np.zeros(n),
-             rgb=np.zeros((n, 3)), ext=np.zeros(6), delta=np.zeros(1))
+             rgb=np.zeros((n, 3)), ext=np.zeros(6), delta=np.zeros(1), mean2d=np.zeros((n, 2)),
+             conic=np.zeros((n, 3)), opacity=np.zeros(n))
     tt, tp, tq = _f64(scene.traj_t), _f64(scene.traj_p), _f64(scene.traj_q)
     dl = _f64(dL_dC).reshape(-1, 3)
     lib().or_backward(C.c_int(n), _p(X), _p(q), _p(ls), _p(lo), _p(rgb), C.byref(_cam(frame.camera)),
@@ -166,7 +169,7 @@ def backward(scene, frame, ext, delta, dL_dC, opts: Opts = Opts(), pixels=None):
                       C.c_double(frame.timestamp), C.byref(opts.c()), C.c_int(npix),
                       _p(pix) if pix is not None else None, _p(dl),
                       _p(g["quat"]), _p(g["log_scale"]), _p(g["logit_opacity"]), _p(g["rgb"]),
-                      _p(g["ext"]), _p(g["delta"]))
+                      _p(g["ext"]), _p(g["delta"]), _p(g["mean2d"]), _p(g["conic"]), _p(g["opacity"]))
     return g
 
 

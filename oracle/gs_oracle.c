@@ -43,6 +43,10 @@ typedef struct {
     double t_min;      /* compositing stops before T would drop below this */
     double scale_max;  /* axis scales are clamped to at most this */
     double bg[3];      /* background colour */
+    double frustum_margin; /* the EWA Jacobian is evaluated with x/z, y/z clamped to
+                              the image's field of view widened by this fraction of
+                              the image size on each side (3DGS uses 1.3x the half
+                              field of view, i.e. 0.15); negative = no clamp */
 } or_opts;
 
 typedef struct {
@@ -257,6 +261,8 @@ typedef struct {
     int s_clamped[3];
     double Sig[9], Sigc[9];
     double J[6];
+    double jx, jy;      /* x/z and y/z used in J (clamped to the widened field of view) */
+    int jclamp_x, jclamp_y;
     double cov[3];      /* 2D covariance (xx, xy, yy), including the low-pass */
     double conic[3];    /* inverse 2D covariance (a, b, c) */
     double mean[2];
@@ -299,10 +305,23 @@ static void project_one(const double *X, const double *q, const double *log_s, d
     P->opacity = 1.0 / (1.0 + exp(-logit_o));
     if (z <= o->near_z && !P->near_edge) return;
     if (z <= 1e-9) return;
-    /* EWA: Jacobian of (x,y,z) -> (fx x/z + cx, fy y/z + cy) */
+    /* EWA: Jacobian of (x,y,z) -> (fx x/z + cx, fy y/z + cy), evaluated at
+     * x/z and y/z limited to the widened field of view (3DGS's EWA), which
+     * bounds the footprint of centres far outside the image */
     double x = P->pc[0], y = P->pc[1];
-    P->J[0] = cam->fx / z; P->J[1] = 0;             P->J[2] = -cam->fx * x / (z * z);
-    P->J[3] = 0;           P->J[4] = cam->fy / z;   P->J[5] = -cam->fy * y / (z * z);
+    P->jx = x / z;
+    P->jy = y / z;
+    if (o->frustum_margin >= 0) {
+        double mx = o->frustum_margin * cam->width, my = o->frustum_margin * cam->height;
+        double xlo = -(cam->cx + mx) / cam->fx, xhi = (cam->width - cam->cx + mx) / cam->fx;
+        double ylo = -(cam->cy + my) / cam->fy, yhi = (cam->height - cam->cy + my) / cam->fy;
+        if (P->jx < xlo) { P->jx = xlo; P->jclamp_x = 1; }
+        if (P->jx > xhi) { P->jx = xhi; P->jclamp_x = 1; }
+        if (P->jy < ylo) { P->jy = ylo; P->jclamp_y = 1; }
+        if (P->jy > yhi) { P->jy = yhi; P->jclamp_y = 1; }
+    }
+    P->J[0] = cam->fx / z; P->J[1] = 0;             P->J[2] = -cam->fx * P->jx / z;
+    P->J[3] = 0;           P->J[4] = cam->fy / z;   P->J[5] = -cam->fy * P->jy / z;
     double JS[6];
     for (int r = 0; r < 2; r++)
         for (int c = 0; c < 3; c++) {
@@ -561,7 +580,8 @@ void or_backward(int N, const double *X, const double *q, const double *log_s, c
                  const double *ext, double delta, double t_frame, const or_opts *o,
                  int npix, const int32_t *pix, const double *dL_dC,
                  double *d_q, double *d_log_s, double *d_logit_o, double *d_rgb,
-                 double *d_ext, double *d_delta) {
+                 double *d_ext, double *d_delta, double *out_g_mean, double *out_g_conic,
+                 double *out_g_opacity) {
     double R_cw[9], t_cw[3];
     or_frame_pose(traj_t, traj_p, traj_q, K, ext, delta, t_frame, R_cw, t_cw);
     or_frame_state S;
@@ -607,6 +627,12 @@ void or_backward(int N, const double *X, const double *q, const double *log_s, c
             g_conic[3 * g + 2] += dpower * (-0.5 * dy * dy);
         }
     }
+    /* optional: the per-Gaussian 2D gradients (mean, conic (a,b,c), opacity) */
+    for (int g = 0; g < N; g++) {
+        if (out_g_mean) { out_g_mean[2 * g] += g_mean[2 * g]; out_g_mean[2 * g + 1] += g_mean[2 * g + 1]; }
+        if (out_g_conic) for (int i = 0; i < 3; i++) out_g_conic[3 * g + i] += g_conic[3 * g + i];
+        if (out_g_opacity) out_g_opacity[g] += g_opac[g];
+    }
     /* 3D chain per Gaussian; pose gradient as dL/dR_cw and dL/dt_cw */
     double gR_cw[9] = {0}, gt_cw[3] = {0};
     for (int g = 0; g < N; g++) {
@@ -642,14 +668,17 @@ void or_backward(int N, const double *X, const double *q, const double *log_s, c
                     for (int k = 0; k < 3; k++) s += Gc[2 * r + c] * P->J[3 * c + k] * P->Sigc[3 * k + j];
                 GJ[3 * r + j] = 2.0 * s;
             }
-        /* J and mean as functions of p_c */
+        /* J and mean as functions of p_c: J02 = -fx jx / z with jx = x/z, or
+         * a constant where clamped (then jx carries no gradient) */
         double x = P->pc[0], y = P->pc[1], z = P->pc[2];
         double fx = cam->fx, fy = cam->fy;
+        double djx_dx = P->jclamp_x ? 0.0 : 1.0 / z, djx_dz = P->jclamp_x ? 0.0 : -x / (z * z);
+        double djy_dy = P->jclamp_y ? 0.0 : 1.0 / z, djy_dz = P->jclamp_y ? 0.0 : -y / (z * z);
         double gp[3];
-        gp[0] = GJ[2] * (-fx / (z * z)) + gm0 * fx / z;
-        gp[1] = GJ[5] * (-fy / (z * z)) + gm1 * fy / z;
-        gp[2] = GJ[0] * (-fx / (z * z)) + GJ[2] * (2 * fx * x / (z * z * z))
-              + GJ[4] * (-fy / (z * z)) + GJ[5] * (2 * fy * y / (z * z * z))
+        gp[0] = GJ[2] * (-fx / z) * djx_dx + gm0 * fx / z;
+        gp[1] = GJ[5] * (-fy / z) * djy_dy + gm1 * fy / z;
+        gp[2] = GJ[0] * (-fx / (z * z)) + GJ[2] * (fx * P->jx / (z * z) - fx / z * djx_dz)
+              + GJ[4] * (-fy / (z * z)) + GJ[5] * (fy * P->jy / (z * z) - fy / z * djy_dz)
               + gm0 * (-fx * x / (z * z)) + gm1 * (-fy * y / (z * z));
         /* Sigma_c = R_cw Sigma R_cw^T */
         double Rt[9], T2[9], GSig[9];

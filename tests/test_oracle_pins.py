@@ -213,6 +213,47 @@ def test_rotated_anisotropic_projection():
         assert pr["depth"][g] == pytest.approx(pc[2], rel=1e-12)
 
 
+def test_jacobian_frustum_clamp():
+    """Centres outside the field of view widened by 15% of the image per
+    side (3DGS's EWA) use the Jacobian of the pinhole map at the clamped
+    ray (x/z, y/z limited), computed here by finite differences at that ray;
+    inside it the plain Jacobian is used."""
+    cam = scenes.Camera(200, 100, 100.0, 90.0, 90.0, 45.0)
+    lim = [(-(cam.cx + 0.15 * cam.width) / cam.fx, (cam.width - cam.cx + 0.15 * cam.width) / cam.fx),
+           (-(cam.cy + 0.15 * cam.height) / cam.fy, (cam.height - cam.cy + 0.15 * cam.height) / cam.fy)]
+    X = np.array([[5.0, 0.3, 2.0], [-4.0, -3.0, 1.5], [0.2, 0.1, 3.0], [1.0, 2.5, 1.0]])
+    rng = np.random.default_rng(2)
+    q = rng.normal(size=(4, 4))
+    ls = np.log(rng.uniform(0.2, 0.6, (4, 3)))
+    sc = scenes.Scene(X, q, ls, np.full(4, 3.0), np.ones((4, 3)), np.array([0.0]), np.zeros((1, 3)),
+                      np.array([[1.0, 0, 0, 0]]))
+    pr = oracle.project(sc, cam, np.eye(3), np.zeros(3), oracle.Opts())
+    pr_free = oracle.project(sc, cam, np.eye(3), np.zeros(3), oracle.Opts(frustum_margin=-1.0))
+    clamped = 0
+    for g in range(4):
+        x, y, z = X[g]
+        jx = min(max(x / z, lim[0][0]), lim[0][1])
+        jy = min(max(y / z, lim[1][0]), lim[1][1])
+        clamped += (jx != x / z) or (jy != y / z)
+        pc = np.array([jx * z, jy * z, z])
+
+        def pin(v):
+            return np.array([cam.fx * v[0] / v[2] + cam.cx, cam.fy * v[1] / v[2] + cam.cy])
+        J = np.zeros((2, 3))
+        for k in range(3):
+            e = np.zeros(3)
+            e[k] = 1e-6
+            J[:, k] = (pin(pc + e) - pin(pc - e)) / 2e-6
+        Rg = Rotation.from_quat(np.r_[q[g, 1:], q[g, 0]]).as_matrix()
+        S = Rg @ np.diag(np.exp(2 * ls[g])) @ Rg.T
+        cov = J @ S @ J.T + 0.3 * np.eye(2)
+        np.testing.assert_allclose(pr["cov"][g], [cov[0, 0], cov[0, 1], cov[1, 1]], rtol=1e-6)
+        np.testing.assert_allclose(pr["mean"][g], pin(X[g]), rtol=1e-12)  # the mean is not clamped
+        if (jx == x / z) and (jy == y / z):
+            np.testing.assert_allclose(pr["cov"][g], pr_free["cov"][g], rtol=1e-12)
+    assert clamped == 3
+
+
 def test_rigid_motion_invariance():
     """Moving the points, the Gaussian orientations and the LiDAR trajectory
     by one rigid motion leaves every image unchanged (Eq. 1-3)."""
@@ -246,13 +287,29 @@ def test_stationary_trajectory_has_zero_time_gradient():
     assert np.any(g["ext"] != 0)
 
 
-def _fd_check(opts, seed, opacity_shift=0.0):
+def _clamped_scene():
+    """Large Gaussians centred beyond the Jacobian clamp on every side of a
+    64x48 image (|x/z| > 0.685 or |y/z| > 0.52), plus a few inside."""
+    p = scenes.tiny_problem()
+    sc = p.scenes[0]
+    rng = np.random.default_rng(21)
+    X = np.array([[1.7, 0.2, 2.0], [-1.8, -0.3, 2.4], [0.3, 1.3, 2.2], [-0.2, -1.25, 2.1],
+                  [1.6, 1.2, 2.0], [0.1, 0.05, 4.0], [-0.4, 0.3, 3.0], [0.5, -0.2, 5.0]])
+    n = len(X)
+    sc2 = scenes.Scene(X, rng.normal(size=(n, 4)), np.log(rng.uniform(0.3, 0.6, (n, 3))),
+                       rng.normal(size=n), rng.uniform(size=(n, 3)), sc.traj_t, sc.traj_p, sc.traj_q)
+    return p, sc2
+
+
+def _fd_check(opts, seed, opacity_shift=0.0, clamped=False):
     p = scenes.tiny_problem()
     sc, fr = p.scenes[0], p.frames[0]
+    if clamped:
+        p, sc = _clamped_scene()
     sc.logit_opacity = sc.logit_opacity.astype(np.float64) + opacity_shift
     ext = p.ext_target[0]  # a non-identity extrinsic
     delta = 0.013
-    W = np.random.default_rng(seed).normal(size=(64 * 48, 3))
+    W = np.random.default_rng(seed).normal(size=(fr.camera.width * fr.camera.height, 3))
     # pixels on a discontinuity (alpha skip/clamp, T stop) get no weight
     W[oracle.render(sc, fr, ext, delta, opts)[3] != 0] = 0.0
 
@@ -289,7 +346,7 @@ def _fd_check(opts, seed, opacity_shift=0.0):
     return errs, flags[W[:, 0] != 0]
 
 
-@pytest.mark.parametrize("mode", ["smooth", "default", "opaque_bg"])
+@pytest.mark.parametrize("mode", ["smooth", "default", "opaque_bg", "clamped"])
 def test_gradients_match_finite_differences(mode):
     """Every oracle gradient (Gaussian parameters, extrinsic, time offset)
     against FP64 central differences of the oracle's forward.  'opaque_bg'
@@ -299,8 +356,10 @@ def test_gradients_match_finite_differences(mode):
         errs, flags = _fd_check(oracle.SMOOTH, 7)
     elif mode == "default":
         errs, flags = _fd_check(oracle.Opts(), 7)
-    else:
+    elif mode == "opaque_bg":
         errs, flags = _fd_check(oracle.Opts(bg=(0.2, 0.5, 0.8)), 8, opacity_shift=5.0)
+    else:
+        errs, flags = _fd_check(oracle.Opts(), 9, clamped=True)
     assert np.all(flags == 0)
     worst = max(errs, key=errs.get)
     assert errs[worst] < 1e-6, (worst, errs[worst])
