@@ -1,0 +1,427 @@
+#!/usr/bin/env python
+"""Calibration iterations per second of the differentiable splatting path.
+
+One iteration ("step") = the whole hot path for every frame of the batch:
+camera poses (Eq. 1), projection (Eq. 2-3), tile binning + depth sort,
+compositing (Phi, Eq. 5), L1 loss (Eq. 4) and its gradient, the reverse
+compositing backward, the projection backward and the gradient w.r.t. the
+extrinsic and the time offset.  The optimiser step is not included.
+
+Workload (default): 1,000,000 LiDAR-anchored Gaussians accumulated from 50
+synthetic 64-beam sweeps along a 10 m/s drive; 8 camera frames of 1408x376;
+the current extrinsic perturbed by 5 deg / 0.5 m and the time offset by
+50 ms from the one the target images were rendered with.  The batched path
+is one CUDA-graph replay per iteration; the per-frame path launches the
+same kernels frame by frame.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Prints one JSON line (rank 0).
+"""
+import argparse
+import csv
+import hashlib
+import io
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "calib iters/s (fwd+bwd, 8×1408×376, 1M Gaussians) batched vs per-frame"
+WORKLOAD = "1M LiDAR-anchored Gaussians (50 synthetic 64-beam sweeps, 10 m/s drive), 8 frames 1408x376, tile 16"
+FLOP_PER_EVAL_FWD = 20.0   # per evaluated (pixel, Gaussian) pair, forward
+FLOP_PER_EVAL_BWD = 60.0   # backward: about three times the forward
+KERNEL_NAMES = {1: "project", 2: "bin_sort", 3: "render_fwd", 4: "render_bwd", 5: "project_bwd"}
+KERNEL_SOURCES = {1: "project.cu", 2: "binsort.cu", 3: "render.cu", 4: "render.cu", 5: "project.cu"}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--tile", type=int, default=16)
+    ap.add_argument("--batch", type=int, default=128)
+    ap.add_argument("--gaussians", type=int, default=1_000_000)
+    ap.add_argument("--frames", type=int, default=8)
+    ap.add_argument("--per-frame-steps", type=int, default=20)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-pixels", type=int, default=48, help="oracle pixels per frame sample")
+    ap.add_argument("--autotune", action="store_true", help="pick tile/batch with the autotuner first")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = list(csv.reader(io.StringIO(open(self.path).read())))
+        os.unlink(self.path)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------- distributed
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# --------------------------------------------------------- CPU oracle leg
+
+def oracle_iteration_seconds(problem, pixels_per_frame, frame_ids, seed=0):
+    """Seconds the FP64 oracle needs for one calibration iteration over the
+    whole workload, extrapolated from a bounded sample: for each frame in
+    frame_ids, the projection + depth sort, the forward of `pixels_per_frame`
+    sampled pixels and the backward of those pixels are timed; per-pixel
+    costs are scaled to all pixels of all frames."""
+    import oracle
+    rng = np.random.default_rng(seed)
+    per_frame_fixed, per_pixel, sample_s = [], [], 0.0
+    for fi in frame_ids:
+        f = problem.frames[fi]
+        sc = problem.scenes[f.scene_id]
+        e, d = problem.ext[f.camera_id], float(problem.delta[f.camera_id])
+        cam = f.camera
+        one = np.array([[cam.width // 2, cam.height // 2]])
+        pix = np.stack([rng.integers(0, cam.width, pixels_per_frame),
+                        rng.integers(0, cam.height, pixels_per_frame)], 1)
+        t0 = time.perf_counter()
+        oracle.render(sc, f, e, d, pixels=one)
+        t1 = time.perf_counter()
+        oracle.render(sc, f, e, d, pixels=pix)
+        t2 = time.perf_counter()
+        oracle.backward(sc, f, e, d, np.ones((1, 3)), pixels=one)
+        t3 = time.perf_counter()
+        oracle.backward(sc, f, e, d, np.ones((len(pix), 3)), pixels=pix)
+        t4 = time.perf_counter()
+        fixed = (t1 - t0) + (t3 - t2)
+        per_frame_fixed.append(fixed)
+        per_pixel.append(max(((t2 - t1) - (t1 - t0)) + ((t4 - t3) - (t3 - t2)), 0.0) / pixels_per_frame)
+        sample_s += t4 - t0
+    n_pix = sum(f.camera.width * f.camera.height for f in problem.frames)
+    total = np.mean(per_frame_fixed) * len(problem.frames) + np.mean(per_pixel) * n_pix
+    return total, sample_s
+
+
+# ---------------------------------------------------------- our path
+
+def build_problem(args):
+    from paper_2403_11577_gb300 import scenes
+    return scenes.calibration_problem(seed=0, n=args.gaussians, frames=args.frames)
+
+
+def source_sha(kernel_id):
+    path = os.path.join(ROOT, "paper_2403_11577_gb300", "csrc", KERNEL_SOURCES[kernel_id])
+    return hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
+
+
+def load_traffic(kernel_id):
+    """DRAM bytes per launch of a kernel from the committed ncu summary, or
+    None if missing or taken on a different kernel source."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        d = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    ent = d.get(KERNEL_NAMES[kernel_id])
+    if not ent or ent.get("source_sha") != source_sha(kernel_id):
+        return None
+    return ent.get("bytes_per_launch_full")
+
+
+def run_ours(args, world, rank, local):
+    import torch
+
+    from paper_2403_11577_gb300 import build, capi, render
+    build.build()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    t_setup = time.time()
+    problem = build_problem(args)
+    scene = render.DeviceScene.from_problem(problem, dev)
+    opts = render.RenderOptions(tile=args.tile, batch=args.batch)
+    if args.autotune:
+        from paper_2403_11577_gb300 import autotune
+        best = autotune.tune(problem, scene)
+        opts = render.RenderOptions(tile=best["tile"], batch=best["batch"])
+    ext = torch.tensor(problem.ext, dtype=torch.float64, device=dev)
+    delta = torch.tensor(problem.delta, dtype=torch.float64, device=dev)
+    ext_t = torch.tensor(problem.ext_target, dtype=torch.float64, device=dev)
+    delta_t = torch.tensor(problem.delta_target, dtype=torch.float64, device=dev)
+    frames = render.Plan.frames_from_problem(problem, scene)
+    cap = render.default_pair_capacity(frames, opts.tile)
+    while True:
+        plan = render.Plan(frames, scene.n, problem.num_cameras, len(problem.scenes), opts, cap, dev)
+        plan.forward(scene, ext_t, delta_t)
+        st = plan.stats()
+        plan.forward(scene, ext, delta)
+        st2 = plan.stats()
+        if not (st.status | st2.status) & capi.GS_DEV_PAIR_OVERFLOW:
+            break
+        cap = int(min(cap * 2, (1 << 32) - 1))
+    plan.forward(scene, ext_t, delta_t)
+    target = plan.rgb.clone()
+    step = render.CalibStep(plan, scene, target, ext, delta, graph=True)
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    stats = plan.stats()
+    setup_s = time.time() - t_setup
+
+    # timed region: K graph replays
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    barrier(world)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    w0 = time.perf_counter()
+    ev0.record()
+    for _ in range(args.steps):
+        step()
+    ev1.record()
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - w0
+    barrier(world)
+    t_ms = ev0.elapsed_time(ev1)
+    clocks = sampler.stop()
+    t_max = max_over_ranks(t_ms / 1e3, world)
+    value = world * args.steps / t_max
+
+    # per-frame path (same work, launched frame by frame, no graph)
+    pf = render.PerFrameStep(problem, scene, target, ext, delta, opts, pair_capacity=cap)
+    for _ in range(2):
+        pf()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.per_frame_steps):
+        pf()
+    e1.record()
+    torch.cuda.synchronize()
+    per_frame = args.per_frame_steps / (e0.elapsed_time(e1) / 1e3)
+    del pf
+
+    # per-kernel durations on the launching stream (eager, one step each)
+    kernel_ms = {}
+    for kid in KERNEL_NAMES:
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        capi.gs_profile_events(kid, a, b)
+        ts = []
+        for _ in range(3):
+            step._body()
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        kernel_ms[KERNEL_NAMES[kid]] = statistics.median(ts)
+    capi.gs_profile_events(capi.GS_PROF_NONE)
+    dom = max(KERNEL_NAMES, key=lambda k: kernel_ms[KERNEL_NAMES[k]])
+    # the dominant kernel inside graph replays: events captured as graph nodes
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    capi.gs_profile_events(dom, a, b)
+    pstep = render.CalibStep(plan, scene, target, ext, delta, graph=True)
+    capi.gs_profile_events(capi.GS_PROF_NONE)
+    durs = []
+    for _ in range(min(args.steps, 50)):
+        pstep()
+        torch.cuda.synchronize()
+        durs.append(a.elapsed_time(b))
+    dom_ms = statistics.mean(durs)
+    del pstep
+    st = plan.stats()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    clock_mhz = clocks["sm_mhz"] or peaks.get("sm_max_mhz", 2070.0)
+    if dom in (3, 4):
+        evals = st.eval_fwd if dom == 3 else st.eval_bwd
+        flops = (FLOP_PER_EVAL_FWD if dom == 3 else FLOP_PER_EVAL_BWD) * evals
+        achieved = flops / (dom_ms / 1e3) / 1e12
+        peak = sms * 128 * 2 * clock_mhz * 1e6 / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": load_traffic(dom), "kernel": KERNEL_NAMES[dom], "launch_ms": dom_ms,
+                "units_per_launch": int(evals), "unit_work": "%g flop per evaluated (pixel, Gaussian) pair" %
+                (FLOP_PER_EVAL_FWD if dom == 3 else FLOP_PER_EVAL_BWD),
+                "peak_basis": "FP32: %d SMs x 128 lanes x 2 flop x %.0f MHz (median SM clock in the timed region)"
+                % (sms, clock_mhz)}
+    else:
+        nrec = plan.batch.num_records
+        nbytes = {1: 44 * scene.n + nrec * (8 + 4 + 32 + 48),
+                  2: 24 * st.num_pairs * 2 * (3 + 0) + 8 * nrec,
+                  5: 44 * scene.n + nrec * (8 + 48) + 44 * scene.n}[dom]
+        achieved = nbytes / (dom_ms / 1e3) / 1e9
+        peak = peaks.get("hbm_gbs", 6800.0)
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": load_traffic(dom), "kernel": KERNEL_NAMES[dom], "launch_ms": dom_ms}
+
+    # end to end through the public API with host buffers: per step the
+    # target images go host->device from pinned memory and the loss and the
+    # calibration gradients come back
+    tgt_host = target.cpu().pin_memory()
+    loss_h = torch.zeros(1, dtype=torch.float64).pin_memory()
+    dext_h = torch.zeros_like(step.grads["ext"], device="cpu").pin_memory()
+    ddel_h = torch.zeros_like(step.grads["delta"], device="cpu").pin_memory()
+    h2d = tgt_host.numel() * 4
+    d2h = 8 + dext_h.numel() * 8 + ddel_h.numel() * 8
+    torch.cuda.synchronize()
+    e0.record()
+    w1 = time.perf_counter()
+    for _ in range(args.steps):
+        step.target.copy_(tgt_host, non_blocking=True)
+        step()
+        loss_h.copy_(step.loss, non_blocking=True)
+        dext_h.copy_(step.grads["ext"], non_blocking=True)
+        ddel_h.copy_(step.grads["delta"], non_blocking=True)
+    e1.record()
+    torch.cuda.synchronize()
+    e2e_wall = time.perf_counter() - w1
+    e2e_t = max_over_ranks(max(e0.elapsed_time(e1) / 1e3, e2e_wall), world)
+    e2e = world * args.steps / e2e_t
+
+    passes = int(math.ceil((32 + max(1, math.ceil(math.log2(max(plan.batch.num_tiles, 2))))) / 8))
+    launches_per_step = 1 + 1 + (3 + 3 * passes + 1) + 1 + 2 + 2 + 1
+    out = {
+        "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_max * 1e3 / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "gaussians": scene.n, "frames": plan.batch.num_frames,
+                   "image": "1408x376", "tile": opts.tile, "batch": opts.batch,
+                   "pairs_per_iter": int(st.num_pairs), "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "inputs larger than L2 (%.1f GB workspace per iteration)" % (plan.ws_bytes / 1e9)},
+        "per_frame": {"value": per_frame, "unit": "iters/s", "speedup_batched": value / world / per_frame},
+        "kernel_ms": kernel_ms,
+        "roofline": roof,
+        "e2e": {"value": e2e, "unit": "iters/s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clocks,
+        "wall_timed_s": wall, "setup_s": setup_s,
+        "loss": float(step.loss.item()),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        secs, sample = oracle_iteration_seconds(problem, args.cpu_pixels, [0, len(problem.frames) // 2])
+        out["cpu_baseline"] = {"value": 1.0 / secs, "unit": "iters/s", "cores": 1, "kind": "oracle",
+                               "sample": "FP64 oracle on frames 0 and %d: projection + global depth sort, "
+                                         "forward and backward of %d sampled pixels each (%.1f s of CPU); "
+                                         "extrapolated to 8 frames x 529,408 pixels" %
+                                         (len(problem.frames) // 2, args.cpu_pixels, sample)}
+    return out
+
+
+def run_reference(args, world, rank):
+    """The oracle as it stands on the host cores, on this workload; each step
+    is a bounded sample extrapolated to one full iteration."""
+    if rank != 0:
+        return None
+    problem = build_problem(args)
+    fr = len(problem.frames)
+    times, sample_total = [], 0.0
+    for i in range(args.warmup + args.steps):
+        secs, sample = oracle_iteration_seconds(problem, 8, [i % fr], seed=i)
+        if i >= args.warmup:
+            times.append(secs)
+            sample_total += sample
+    secs = float(np.mean(times))
+    v = 1.0 / secs
+    return {"metric": METRIC, "value": v, "unit": "iters/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": secs * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, "gaussians": problem.scenes[0].n, "frames": fr, "image": "1408x376"},
+            "cpu_baseline": {"value": v, "unit": "iters/s", "cores": 1, "kind": "oracle",
+                             "sample": "per step: one frame's projection + global sort, forward and backward of 8 "
+                                       "sampled pixels, extrapolated to 8 frames x 529,408 pixels (%.1f s CPU total)"
+                                       % sample_total},
+            "e2e": {"value": v, "unit": "iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        out = run_reference(args, world, rank)
+    else:
+        out = run_ours(args, world, rank, local)
+    if rank == 0 and out is not None:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

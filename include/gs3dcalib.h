@@ -97,7 +97,10 @@ typedef struct {
     int32_t tile;     /* tile edge in pixels: 8, 16 or 32 */
     int32_t batch;    /* Gaussians staged in shared memory per round:
                          64, 128 or 256 */
-    int32_t reserved;
+    float frustum_margin; /* the EWA Jacobian is evaluated with x/z, y/z
+                         clamped to the field of view widened by this
+                         fraction of the image size per side (0.15, 3DGS's
+                         1.3x half field of view); negative = no clamp */
 } gs_opts;
 
 /* A batch of frames planned by gs_batch_init. */

@@ -6,7 +6,8 @@
 // scene, writing one record per frame.  Frame-dependent work uses
 //   d = (X - c_hi) - c_lo   (camera centre c = c_hi + c_lo in two floats),
 //   p = R_cw d              (Eq. 2: X^n = (T^n)^-1 X = R_cw (X - c)),
-//   T = J R_cw              (J: Jacobian of the pinhole map at p),
+//   T = J R_cw              (J: Jacobian of the pinhole map at p, with x/z
+//                            and y/z limited to the widened field of view),
 //   cov = T Sigma T^T + lowpass I   (= J Sigma_c J^T, Sigma_c of Eq. 3),
 // with Sigma = R_g diag(s)^2 R_g^T built once per Gaussian.
 //
@@ -77,6 +78,8 @@ __device__ __forceinline__ void load_gauss(int g, const float *__restrict__ X, c
 // Frame-dependent projection.  Returns false if culled.
 struct Proj {
     float p[3], iz, xz, yz;   // camera-frame centre, 1/z, x/z, y/z
+    float jx, jy;             // x/z, y/z as used in J (clamped to the widened view)
+    bool clx, cly;            // whether they were clamped
     float T[6];               // J R_cw
     float U[6];               // T Sigma
     float cov[3];             // xx, xy, yy (with low-pass)
@@ -95,10 +98,24 @@ __device__ __forceinline__ bool project_frame(const GaussParams &G, const float 
     Q.iz = 1.f / z;
     Q.xz = Q.p[0] * Q.iz;
     Q.yz = Q.p[1] * Q.iz;
+    // J at x/z, y/z limited to the field of view widened by frustum_margin
+    // of the image size per side (bounds the footprint of far off-image centres)
+    Q.jx = Q.xz;
+    Q.jy = Q.yz;
+    Q.clx = Q.cly = false;
+    if (o.frustum_margin >= 0.f) {
+        const float mx = o.frustum_margin * (float)fr.width, my = o.frustum_margin * (float)fr.height;
+        const float xlo = -(fr.cx + mx) / fr.fx, xhi = ((float)fr.width - fr.cx + mx) / fr.fx;
+        const float ylo = -(fr.cy + my) / fr.fy, yhi = ((float)fr.height - fr.cy + my) / fr.fy;
+        Q.jx = fminf(fmaxf(Q.xz, xlo), xhi);
+        Q.jy = fminf(fmaxf(Q.yz, ylo), yhi);
+        Q.clx = Q.jx != Q.xz;
+        Q.cly = Q.jy != Q.yz;
+    }
     float fxz = fr.fx * Q.iz, fyz = fr.fy * Q.iz;
     for (int j = 0; j < 3; j++) {
-        Q.T[j] = fxz * (P[j] - Q.xz * P[6 + j]);
-        Q.T[3 + j] = fyz * (P[3 + j] - Q.yz * P[6 + j]);
+        Q.T[j] = fxz * (P[j] - Q.jx * P[6 + j]);
+        Q.T[3 + j] = fyz * (P[3 + j] - Q.jy * P[6 + j]);
     }
     const float *S = G.Sig;
     for (int r = 0; r < 2; r++) {
@@ -254,13 +271,18 @@ k_project_bwd(const gs_frame *__restrict__ frames, int F, int N, const float *__
                 const float iz = Q.iz, iz2 = iz * iz;
                 const float fx = fr.fx, fy = fr.fy;
                 const float gmx = g0.x, gmy = g0.y;
+                // J00 = fx/z, J02 = -fx jx/z, J11 = fy/z, J12 = -fy jy/z, with
+                // jx = x/z (jy = y/z) unless clamped, where it is a constant
+                const float dJ02_dx = Q.clx ? 0.f : -fx * iz2, dJ12_dy = Q.cly ? 0.f : -fy * iz2;
+                const float dJ02_dz = Q.clx ? fx * Q.jx * iz2 : 2.f * fx * Q.xz * iz2;
+                const float dJ12_dz = Q.cly ? fy * Q.jy * iz2 : 2.f * fy * Q.yz * iz2;
                 float dp[3];
-                dp[0] = -fx * iz2 * dJ02 + fx * iz * gmx;
-                dp[1] = -fy * iz2 * dJ12 + fy * iz * gmy;
-                dp[2] = -fx * iz2 * dJ00 + 2.f * fx * Q.xz * iz2 * dJ02 - fy * iz2 * dJ11 +
-                        2.f * fy * Q.yz * iz2 * dJ12 - fx * Q.xz * iz * gmx - fy * Q.yz * iz * gmy;
+                dp[0] = dJ02_dx * dJ02 + fx * iz * gmx;
+                dp[1] = dJ12_dy * dJ12 + fy * iz * gmy;
+                dp[2] = -fx * iz2 * dJ00 + dJ02_dz * dJ02 - fy * iz2 * dJ11 + dJ12_dz * dJ12 -
+                        fx * Q.xz * iz * gmx - fy * Q.yz * iz * gmy;
                 // twist: rotation part through T = J R_cw: M = R_cw N, N = dT^T J
-                float J00 = fx * iz, J02 = -fx * Q.xz * iz, J11 = fy * iz, J12 = -fy * Q.yz * iz;
+                float J00 = fx * iz, J02 = -fx * Q.jx * iz, J11 = fy * iz, J12 = -fy * Q.jy * iz;
                 float Nm[9];
                 for (int i = 0; i < 3; i++) {
                     Nm[3 * i + 0] = dT[i] * J00;

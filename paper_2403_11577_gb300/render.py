@@ -29,13 +29,14 @@ class RenderOptions:
     bg: tuple = (0.0, 0.0, 0.0)
     tile: int = 16
     batch: int = 128
+    frustum_margin: float = 0.15
 
     def c(self) -> capi.GsOpts:
         o = capi.GsOpts()
         o.near_z, o.lowpass, o.alpha_min = self.near_z, self.lowpass, self.alpha_min
         o.alpha_max, o.t_min, o.scale_max = self.alpha_max, self.t_min, self.scale_max
         o.bg = (C.c_float * 3)(*self.bg)
-        o.tile, o.batch, o.reserved = self.tile, self.batch, 0
+        o.tile, o.batch, o.frustum_margin = self.tile, self.batch, self.frustum_margin
         return o
 
 

