@@ -177,9 +177,10 @@ enum {
     GS_PROF_PROJECT_BWD = 5
 };
 /* Kernel timing hook.  After this call, every launch of the selected
- * kernel is bracketed by cudaEventRecordWithFlags(start/stop, stream,
- * cudaEventRecordExternal) on the kernel's own stream, so the events also
- * become event-record nodes when the launch is captured into a CUDA graph.
+ * kernel is bracketed by records of the start/stop events on the kernel's
+ * own stream; while the stream is being captured into a CUDA graph they are
+ * recorded with cudaEventRecordExternal, so they become event-record nodes
+ * that fire on every replay.
  * kernel: GS_PROF_NONE (0) disables the hook; GS_PROF_PROJECT,
  * GS_PROF_BIN_SORT (the whole binning and sorting sequence),
  * GS_PROF_RENDER_FWD, GS_PROF_RENDER_BWD (the compositing backward only),

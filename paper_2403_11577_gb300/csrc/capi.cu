@@ -93,9 +93,15 @@ int g_prof_kernel = GS_PROF_NONE;
 cudaEvent_t g_prof_start = nullptr, g_prof_stop = nullptr;
 
 // Records the timing hook's start (or stop) event before (after) `kernel`.
+// Captured launches get an external event-record node; eager ones a plain record.
 cudaError_t prof_mark(int kernel, bool start, cudaStream_t s) {
     if (g_prof_kernel != kernel || kernel == GS_PROF_NONE) return cudaSuccess;
-    return cudaEventRecordWithFlags(start ? g_prof_start : g_prof_stop, s, cudaEventRecordExternal);
+    cudaEvent_t ev = start ? g_prof_start : g_prof_stop;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(s, &cs);
+    if (e != cudaSuccess) return e;
+    if (cs == cudaStreamCaptureStatusActive) return cudaEventRecordWithFlags(ev, s, cudaEventRecordExternal);
+    return cudaEventRecord(ev, s);
 }
 
 }  // namespace

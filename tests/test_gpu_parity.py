@@ -472,3 +472,28 @@ def test_invalid_arguments_rejected():
     with pytest.raises(ValueError):
         capi.gs_project(plan.batch, scene.X.cpu(), scene.quat, scene.log_scale, scene.logit_opacity,
                         plan.copts, plan.ws)
+
+
+def test_profile_events_eager_and_graph():
+    """The kernel timing hook brackets the selected kernel with the caller's
+    events, in eager launches and inside graph replays."""
+    p = _small_batched()
+    scene, plan, ext, dl = setup(p)
+    plan.forward(scene, ext, dl)
+    target = plan.rgb.clone()
+    for kid in (capi.GS_PROF_PROJECT, capi.GS_PROF_BIN_SORT, capi.GS_PROF_RENDER_FWD,
+                capi.GS_PROF_RENDER_BWD, capi.GS_PROF_PROJECT_BWD):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        capi.gs_profile_events(kid, a, b)
+        step = render.CalibStep(plan, scene, target, ext, dl, graph=False)
+        step()
+        torch.cuda.synchronize()
+        eager_ms = a.elapsed_time(b)
+        gstep = render.CalibStep(plan, scene, target, ext, dl, graph=True)
+        capi.gs_profile_events(capi.GS_PROF_NONE)
+        gstep()
+        torch.cuda.synchronize()
+        graph_ms = a.elapsed_time(b)
+        assert 0 < eager_ms < 1000 and 0 < graph_ms < 1000, (kid, eager_ms, graph_ms)
+    with pytest.raises(capi.GsError):
+        capi.gs_profile_events(9, a, b)
