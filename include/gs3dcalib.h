@@ -22,8 +22,9 @@
  *     of gs_workspace_size() bytes (256-byte aligned).
  *   - Every call enqueues work on `stream` (a cudaStream_t; NULL = legacy
  *     default stream) and returns without synchronising, except
- *     gs_batch_init and gs_read_stats, which are synchronous.  The
- *     asynchronous calls can be captured into a CUDA graph.
+ *     gs_batch_init and gs_read_stats, which are synchronous.  The hot-path
+ *     calls (gs_pose_compose through gs_pose_grad) can be captured into a
+ *     CUDA graph.
  *   - Layouts are row-major and contiguous; float is IEEE binary32, double
  *     binary64.  Quaternions are Hamilton (w, x, y, z).  An extrinsic is the
  *     camera-to-LiDAR transform L_T^i = [Exp(omega) | t] stored as
@@ -284,6 +285,40 @@ gs_status gs_render_bwd(const gs_batch *batch, const float *X, const float *quat
  *   accumulate    0: outputs are written; otherwise added to. */
 gs_status gs_pose_grad(const gs_batch *batch, const double *ext, void *ws_dev, double *d_ext,
                        double *d_delta, double *d_xi, int32_t accumulate, void *stream);
+
+/* ------------------------------------------------- no allocation at all -- */
+
+/* The tile binning and depth sort of gs_bin_sort for callers that cannot
+ * allocate device memory: for instance a host framework that owns every
+ * device buffer and hands a plugin only its inputs and outputs, or a
+ * real-time loop where an allocation's latency or failure is not
+ * acceptable.  Such a caller cannot provide the workspace gs_bin_sort needs.
+ * The paper has no counterpart; it is a deployment convenience.
+ *
+ * Results are the same as gs_bin_sort's, bit for bit; the inputs and
+ * outputs are the caller's buffers instead of workspace regions:
+ *   rect[R][2]   uint32 rectangles (x0 | y0 << 16, x1 | y1 << 16, inclusive
+ *                tiles; empty when x0 > x1), R = batch->num_records
+ *   depth[R]     float camera depths (the key's low 32 bits)
+ *   keys[pair_capacity], vals[pair_capacity]  sorted pairs (output)
+ *   ranges[num_tiles][2]  [start, end) of each tile (output)
+ *   out_pairs[2] (device, uint64): pairs written and pairs requested; if
+ *                the request exceeds batch->pair_capacity nothing is written
+ *                and out_pairs[0] = 0.
+ * Scratch: one fixed array of about 12.6 MB compiled into the library (every
+ * GPU that loads the library holds it until the process exits), sized for at
+ * most 2^20 pairs (batch->pair_capacity) and 2^22 records; larger batches
+ * return GS_ERR_CAPACITY without enqueuing anything.  No cudaMalloc,
+ * cudaFree or allocating library routine is called.
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls share the one array and it keeps
+ * the last call's contents: calls that overlap on the GPU (different
+ * streams, or different host threads) race and corrupt each other.
+ * Errors: GS_ERR_INVALID_ARG, GS_ERR_CAPACITY, GS_ERR_CUDA. */
+gs_status gs_bin_sort_noalloc(const gs_batch *batch, const gs_opts *opts, const uint32_t *rect,
+                              const float *depth, uint64_t *keys, uint32_t *vals, uint32_t *ranges,
+                              uint64_t *out_pairs, void *stream);
 
 #ifdef __cplusplus
 }

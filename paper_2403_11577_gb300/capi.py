@@ -65,6 +65,7 @@ _SIGS = {
     "gs_loss_l1": ([_P, _P, _P, C.c_int64, C.c_float, _P, _P, _P, _P], C.c_int32),
     "gs_render_bwd": ([_P] * 15 + [C.c_int32, _P], C.c_int32),
     "gs_pose_grad": ([_P] * 6 + [C.c_int32, _P], C.c_int32),
+    "gs_bin_sort_noalloc": ([_P] * 9, C.c_int32),
 }
 
 _lib = None
@@ -245,3 +246,15 @@ def gs_pose_grad(batch, ext, ws, d_ext, d_delta, d_xi=None, accumulate=False, st
                               _ptr(d_ext, F64, "d_ext"), _ptr(d_delta, F64, "d_delta"),
                               _ptr(d_xi, F64, "d_xi", allow_none=True), int(bool(accumulate)), _stream(stream)),
            "gs_pose_grad")
+
+
+def gs_bin_sort_noalloc(batch, opts, rect, depth, keys, vals, ranges, out_pairs, stream=None):
+    """Tile binning + depth sort into the caller's buffers, with no device
+    allocation and no workspace (for callers that cannot allocate).
+    rect: int32/uint32 [R*2]; depth: float32 [R]; keys: int64 [cap];
+    vals: int32 [cap]; ranges: int32 [T*2]; out_pairs: int64 [2]."""
+    _check(lib().gs_bin_sort_noalloc(C.byref(batch), C.byref(opts), _ptr(rect, None, "rect"),
+                                     _ptr(depth, F32, "depth"), _ptr(keys, torch.int64, "keys"),
+                                     _ptr(vals, torch.int32, "vals"), _ptr(ranges, torch.int32, "ranges"),
+                                     _ptr(out_pairs, torch.int64, "out_pairs"), _stream(stream)),
+           "gs_bin_sort_noalloc")

@@ -18,6 +18,8 @@
 //    order of equal digits is preserved across blocks.
 // 5. k_tile_ranges: [start, end) of every tile in the sorted pairs.
 // No kernel waits on another block; there are no spin loops.
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace gs {
@@ -387,3 +389,106 @@ cudaError_t launch_bin_sort(const gs_batch *b, const Layout &L, unsigned char *w
 }
 
 }  // namespace gs
+
+// ------------------------------------------------- allocation-free variant
+//
+// gs_bin_sort_noalloc: the same kernels as gs_bin_sort, with the caller's
+// rect/depth as inputs and the caller's keys/vals/ranges as outputs; the
+// scratch (counters, emission sums, radix histograms and the second key/value
+// buffer of the ping-pong) lives in the fixed file-scope array below instead
+// of a caller-allocated workspace.
+
+namespace gs {
+
+constexpr long long kNoAllocMaxPairs = 1ll << 20;
+constexpr long long kNoAllocMaxRecords = 1ll << 22;
+constexpr int kNoAllocSortBlocks = (int)(kNoAllocMaxPairs / kSortTile);  // 256
+
+struct NoAllocScratch {
+    Stats stats;
+    unsigned long long alt_keys[kNoAllocMaxPairs];
+    uint32_t alt_vals[kNoAllocMaxPairs];
+    unsigned long long emit_sums[kNoAllocMaxRecords / kEmitItems];
+    uint32_t hist[kRadix * kNoAllocSortBlocks];
+};
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[sizeof(NoAllocScratch)];
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+void *g_noalloc_ptr[kMaxDevices] = {};
+
+// Device address of the scratch array on the current device, looked up once
+// per device (the host-side symbol is only a stand-in for it).
+cudaError_t noalloc_scratch(NoAllocScratch **out) {
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = reinterpret_cast<NoAllocScratch *>(g_noalloc_ptr[dev]);
+    return cudaSuccess;
+}
+
+__global__ void k_noalloc_counts(const Stats *__restrict__ st, unsigned long long *__restrict__ out) {
+    out[0] = st->num_pairs;
+    out[1] = st->raw_pairs;
+}
+
+}  // namespace
+
+}  // namespace gs
+
+extern "C" gs_status gs_bin_sort_noalloc(const gs_batch *b, const gs_opts *o, const uint32_t *rect,
+                                         const float *depth, uint64_t *keys, uint32_t *vals, uint32_t *ranges,
+                                         uint64_t *out_pairs, void *stream) {
+    using namespace gs;
+    if (!b || !o || !b->frames_dev || b->num_frames <= 0 || b->num_tiles <= 0 || o->tile != b->tile || !keys ||
+        !vals || !ranges || !out_pairs || (b->num_records > 0 && (!rect || !depth)))
+        return GS_ERR_INVALID_ARG;
+    if (b->pair_capacity > kNoAllocMaxPairs || b->num_records > kNoAllocMaxRecords) return GS_ERR_CAPACITY;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    NoAllocScratch *sc = nullptr;
+    if (noalloc_scratch(&sc) != cudaSuccess) return GS_ERR_CUDA;
+    const int emit_blocks = (int)((b->num_records + kEmitItems - 1) / kEmitItems);
+    const long long st = (b->pair_capacity + kSortTile - 1) / kSortTile;
+    const int sort_blocks = (int)std::max(1ll, std::min(st, (long long)kNoAllocSortBlocks));
+    const int passes = radix_passes(b->num_tiles);
+    const uint2 *r2 = reinterpret_cast<const uint2 *>(rect);
+    unsigned long long *kb[2] = {reinterpret_cast<unsigned long long *>(keys), sc->alt_keys};
+    uint32_t *vb[2] = {vals, sc->alt_vals};
+    int cur = passes & 1;  // the last pass ends in the caller's buffers
+    cudaError_t e = cudaMemsetAsync(&sc->stats, 0, sizeof(Stats), s);  // counters start at zero
+    if (e == cudaSuccess && emit_blocks > 0) {
+        k_pair_count<<<emit_blocks, kEmitThreads, 0, s>>>(r2, b->num_records, sc->emit_sums);
+        k_pair_scan<<<1, 1024, 0, s>>>(sc->emit_sums, emit_blocks, b->pair_capacity, &sc->stats);
+        k_pair_emit<<<emit_blocks, kEmitThreads, 0, s>>>(b->frames_dev, b->num_frames, r2, depth, b->num_records,
+                                                         sc->emit_sums, &sc->stats, kb[cur], vb[cur]);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_radix_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sizeof(ScatterSmem));
+    for (int p = 0; e == cudaSuccess && p < passes; p++) {
+        const int shift = p * kRadixBits;
+        k_radix_hist<<<sort_blocks, kSortThreads, 0, s>>>(kb[cur], &sc->stats, shift, sort_blocks, sc->hist);
+        k_radix_scan<<<1, 1024, 0, s>>>(sc->hist, kRadix * sort_blocks);
+        k_radix_scatter<<<sort_blocks, kSortThreads, sizeof(ScatterSmem), s>>>(
+            kb[cur], vb[cur], kb[cur ^ 1], vb[cur ^ 1], &sc->stats, shift, sort_blocks, sc->hist);
+        cur ^= 1;
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemsetAsync(ranges, 0, sizeof(uint32_t) * 2 * (size_t)b->num_tiles, s);
+    if (e == cudaSuccess) {
+        k_tile_ranges<<<1216, 256, 0, s>>>(kb[0], &sc->stats, reinterpret_cast<uint2 *>(ranges));
+        k_noalloc_counts<<<1, 1, 0, s>>>(&sc->stats, reinterpret_cast<unsigned long long *>(out_pairs));
+        e = cudaGetLastError();
+    }
+    return e == cudaSuccess ? GS_OK : GS_ERR_CUDA;
+}
