@@ -10,13 +10,14 @@
 //    index within its scene.  Records are emitted in order, so for equal
 //    keys the emission order is ascending value.
 // 4. LSD radix sort, 8-bit digits over the key bits that can be non-zero,
-//    each pass: k_radix_hist (per-block digit counts) -> k_radix_scan (one
-//    exclusive scan of the digit-major count matrix) -> k_radix_scatter
+//    each pass: k_radix_hist (per-block digit counts) -> k_radix_colscan
+//    (per-digit prefix over blocks, digit totals) -> k_radix_scatter
 //    (stable: per-warp ranking with match_any in index order, per-tile
 //    prefix over warps, staging in shared memory by digit, then coalesced
 //    writes).  Each block owns one contiguous chunk of the input, so the
 //    order of equal digits is preserved across blocks.
-// 5. k_tile_ranges: [start, end) of every tile in the sorted pairs.
+// 5. k_tile_ranges: [start, end) of every tile in the sorted pairs;
+//    k_tile_order: the tiles sorted heavy-first for the render kernels.
 // No kernel waits on another block; there are no spin loops.
 #include <algorithm>
 
@@ -199,29 +200,29 @@ k_radix_hist(const unsigned long long *__restrict__ keys, const Stats *__restric
     }
 }
 
-// Exclusive scan of the digit-major matrix hist[d * nb + b] (u32; the total
-// fits: it is at most the pair capacity, checked on the host to be < 2^32).
-__global__ void __launch_bounds__(1024) k_radix_scan(uint32_t *__restrict__ hist, int n) {
-    __shared__ uint32_t part[1024];
-    const int T = blockDim.x;
-    const int per = (n + T - 1) / T;
-    const int lo = min((int)threadIdx.x * per, n), hi = min(lo + per, n);
-    uint32_t s = 0;
-    for (int i = lo; i < hi; i++) s += hist[i];
-    part[threadIdx.x] = s;
+// Column scans of the digit-major count matrix hist[d * nb + b]: block d
+// turns its column into exclusive prefixes over blocks and writes the digit's
+// total; the scatter adds the exclusive prefix of the totals.  Counts fit in
+// u32 (at most the pair capacity, checked on the host to be < 2^32).
+constexpr int kColThreads = 512;  // >= the number of sort blocks
+
+__global__ void __launch_bounds__(kColThreads)
+k_radix_colscan(uint32_t *__restrict__ hist, int nb, uint32_t *__restrict__ totals) {
+    __shared__ uint32_t wsum[kColThreads / 32];
+    const int d = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t *col = hist + (size_t)d * nb;
+    const uint32_t x = threadIdx.x < nb ? col[threadIdx.x] : 0u;
+    uint32_t incl = x;
+    for (int s = 1; s < 32; s <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, s);
+        if (lane >= s) incl += y;
+    }
+    if (lane == 31) wsum[warp] = incl;
     __syncthreads();
-    for (int off = 1; off < T; off <<= 1) {
-        uint32_t v = threadIdx.x >= off ? part[threadIdx.x - off] : 0u;
-        __syncthreads();
-        part[threadIdx.x] += v;
-        __syncthreads();
-    }
-    uint32_t run = part[threadIdx.x] - s;
-    for (int i = lo; i < hi; i++) {
-        uint32_t x = hist[i];
-        hist[i] = run;
-        run += x;
-    }
+    uint32_t pre = 0;
+    for (int w = 0; w < warp; w++) pre += wsum[w];
+    if (threadIdx.x < nb) col[threadIdx.x] = pre + incl - x;
+    if (threadIdx.x == kColThreads - 1) totals[d] = pre + incl;
 }
 
 constexpr int kWarps = kSortThreads / 32;
@@ -239,12 +240,30 @@ struct ScatterSmem {
 __global__ void __launch_bounds__(kSortThreads)
 k_radix_scatter(const unsigned long long *__restrict__ kin, const uint32_t *__restrict__ vin,
                 unsigned long long *__restrict__ kout, uint32_t *__restrict__ vout,
-                const Stats *__restrict__ stats, int shift, int nb, const uint32_t *__restrict__ hist) {
+                const Stats *__restrict__ stats, int shift, int nb, const uint32_t *__restrict__ hist,
+                const uint32_t *__restrict__ totals) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     ScatterSmem &S = *reinterpret_cast<ScatterSmem *>(smem_raw);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const Chunk c = sort_chunk(stats->num_pairs, nb, blockIdx.x);
-    for (int d = threadIdx.x; d < kRadix; d += kSortThreads) S.run[d] = hist[(size_t)d * nb + blockIdx.x];
+    // run[d] = (items of digits < d) + (items of digit d in earlier blocks)
+    if (threadIdx.x < kRadix) {
+        const uint32_t x = totals[threadIdx.x];
+        uint32_t incl = x;
+        for (int s = 1; s < 32; s <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, s);
+            if (lane >= s) incl += y;
+        }
+        if (lane == 31) S.wtot[warp] = incl;
+        S.run[threadIdx.x] = incl - x;
+    }
+    __syncthreads();
+    if (threadIdx.x < kRadix) {
+        uint32_t pre = 0;
+        for (int w = 0; w < warp; w++) pre += S.wtot[w];
+        S.run[threadIdx.x] += pre + hist[(size_t)threadIdx.x * nb + blockIdx.x];
+    }
+    __syncthreads();
     const uint32_t lt_mask = (1u << lane) - 1u;
     for (long long t0 = c.lo; t0 < c.hi; t0 += kSortTile) {
         for (int i = lane; i < kRadix; i += 32) S.wcnt[warp][i] = 0;
@@ -334,6 +353,38 @@ __global__ void k_tile_ranges(const unsigned long long *__restrict__ keys, const
     }
 }
 
+// Heavy-first processing order of the tiles (longest pair lists first), so
+// that the long tiles start at once and the short ones fill in behind them
+// instead of a few long ones running alone at the end.  Tiles are bucketed
+// by floor(log2(list length)); the order within a bucket is arbitrary (it
+// does not change any result: tiles are independent).
+constexpr int kOrderBuckets = 33;
+
+__global__ void __launch_bounds__(1024)
+k_tile_order(const uint2 *__restrict__ ranges, int T, uint32_t *__restrict__ order) {
+    __shared__ uint32_t cnt[kOrderBuckets], base[kOrderBuckets];
+    if (threadIdx.x < kOrderBuckets) cnt[threadIdx.x] = 0;
+    __syncthreads();
+    auto bucket = [](uint32_t len) { return len == 0 ? 0 : 32 - __clz(len); };  // 0..32
+    for (int t = threadIdx.x; t < T; t += blockDim.x) {
+        const uint2 r = ranges[t];
+        atomicAdd(&cnt[bucket(r.y - r.x)], 1u);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t s = 0;
+        for (int k = kOrderBuckets - 1; k >= 0; k--) {  // descending length
+            base[k] = s;
+            s += cnt[k];
+        }
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < T; t += blockDim.x) {
+        const uint2 r = ranges[t];
+        order[atomicAdd(&base[bucket(r.y - r.x)], 1u)] = (uint32_t)t;
+    }
+}
+
 }  // namespace
 
 int radix_passes(int num_tiles) {
@@ -354,6 +405,7 @@ cudaError_t launch_bin_sort(const gs_batch *b, const Layout &L, unsigned char *w
                                    reinterpret_cast<unsigned long long *>(ws + L.keys[1])};
     uint32_t *vals[2] = {reinterpret_cast<uint32_t *>(ws + L.vals[0]), reinterpret_cast<uint32_t *>(ws + L.vals[1])};
     uint32_t *hist = reinterpret_cast<uint32_t *>(ws + L.sort_hist);
+    uint32_t *totals = hist + (size_t)kRadix * L.sort_blocks;
     uint2 *ranges = reinterpret_cast<uint2 *>(ws + L.ranges);
     cudaError_t e;
     if (L.emit_blocks > 0) {
@@ -377,14 +429,15 @@ cudaError_t launch_bin_sort(const gs_batch *b, const Layout &L, unsigned char *w
     for (int p = 0; p < L.passes; p++) {
         const int shift = p * kRadixBits;
         k_radix_hist<<<L.sort_blocks, kSortThreads, 0, s>>>(keys[cur], stats, shift, L.sort_blocks, hist);
-        k_radix_scan<<<1, 1024, 0, s>>>(hist, kRadix * L.sort_blocks);
+        k_radix_colscan<<<kRadix, kColThreads, 0, s>>>(hist, L.sort_blocks, totals);
         k_radix_scatter<<<L.sort_blocks, kSortThreads, sizeof(ScatterSmem), s>>>(
-            keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], stats, shift, L.sort_blocks, hist);
+            keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], stats, shift, L.sort_blocks, hist, totals);
         cur ^= 1;
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(ranges, 0, sizeof(uint2) * (size_t)b->num_tiles, s)) != cudaSuccess) return e;
     k_tile_ranges<<<1216, 256, 0, s>>>(keys[0], stats, ranges);
+    k_tile_order<<<1, 1024, 0, s>>>(ranges, b->num_tiles, reinterpret_cast<uint32_t *>(ws + L.order));
     return cudaGetLastError();
 }
 
@@ -410,6 +463,7 @@ struct NoAllocScratch {
     uint32_t alt_vals[kNoAllocMaxPairs];
     unsigned long long emit_sums[kNoAllocMaxRecords / kEmitItems];
     uint32_t hist[kRadix * kNoAllocSortBlocks];
+    uint32_t totals[kRadix];
 };
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[sizeof(NoAllocScratch)];
@@ -478,9 +532,9 @@ extern "C" gs_status gs_bin_sort_noalloc(const gs_batch *b, const gs_opts *o, co
     for (int p = 0; e == cudaSuccess && p < passes; p++) {
         const int shift = p * kRadixBits;
         k_radix_hist<<<sort_blocks, kSortThreads, 0, s>>>(kb[cur], &sc->stats, shift, sort_blocks, sc->hist);
-        k_radix_scan<<<1, 1024, 0, s>>>(sc->hist, kRadix * sort_blocks);
+        k_radix_colscan<<<kRadix, kColThreads, 0, s>>>(sc->hist, sort_blocks, sc->totals);
         k_radix_scatter<<<sort_blocks, kSortThreads, sizeof(ScatterSmem), s>>>(
-            kb[cur], vb[cur], kb[cur ^ 1], vb[cur ^ 1], &sc->stats, shift, sort_blocks, sc->hist);
+            kb[cur], vb[cur], kb[cur ^ 1], vb[cur ^ 1], &sc->stats, shift, sort_blocks, sc->hist, sc->totals);
         cur ^= 1;
         e = cudaGetLastError();
     }

@@ -11,8 +11,8 @@ namespace gs {
 
 cudaError_t launch_pose_compose(const gs_batch *, const double *, const double *, const int32_t *,
                                 const double *, const double *, float *, double *, cudaStream_t);
-cudaError_t launch_pose_grad(const gs_batch *, int, const double *, const double *, const double *, double *,
-                             double *, double *, bool, cudaStream_t);
+cudaError_t launch_pose_grad(const gs_batch *, int, const double *, double *, const double *, const double *,
+                             double *, double *, double *, bool, cudaStream_t);
 cudaError_t launch_project(const gs_batch *, const float *, const float *, const float *, const float *,
                            const float *, const gs_opts *, uint2 *, float *, float4 *, float4 *, Stats *,
                            cudaStream_t);
@@ -21,11 +21,11 @@ cudaError_t launch_project_bwd(const gs_batch *, const float *, const float *, c
                                const float *, const gs_opts *, const uint2 *, const float4 *, float *, float *,
                                float *, float *, double *, bool, cudaStream_t);
 cudaError_t launch_bin_sort(const gs_batch *, const Layout &, unsigned char *, cudaStream_t, int);
-cudaError_t launch_render_fwd(const gs_batch *, const gs_opts *, const uint2 *, const uint32_t *, const float4 *,
-                              const float *, Stats *, float *, float *, int32_t *, cudaStream_t);
-cudaError_t launch_render_bwd(const gs_batch *, const gs_opts *, const uint2 *, const uint32_t *, const float4 *,
-                              const float *, Stats *, const float *, const int32_t *, const float *, float4 *,
-                              cudaStream_t);
+cudaError_t launch_render_fwd(const gs_batch *, const gs_opts *, const uint32_t *, const uint2 *, const uint32_t *,
+                              const float4 *, const float *, Stats *, float *, float *, int32_t *, cudaStream_t);
+cudaError_t launch_render_bwd(const gs_batch *, const gs_opts *, const uint32_t *, const uint2 *, const uint32_t *,
+                              const float4 *, const float *, Stats *, const float *, const int32_t *, const float *,
+                              float4 *, cudaStream_t);
 cudaError_t launch_l1(const float *, const float *, long long, float, double *, float *, double *, cudaStream_t);
 
 constexpr int kSortBlocksMax = 304;  // two per SM on a 152-SM GB300
@@ -54,9 +54,11 @@ bool make_layout(const gs_batch *b, Layout *L) {
     L->keys[1] = take(cap * 8);
     L->vals[1] = take(cap * 4);
     L->ranges = take(T * 8);
+    L->order = take(T * 4);
     L->emit_sums = take((size_t)std::max(1, L->emit_blocks) * 8);
-    L->sort_hist = take((size_t)kRadix * L->sort_blocks * 4);
+    L->sort_hist = take((size_t)kRadix * (L->sort_blocks + 1) * 4);  // counts + digit totals
     L->twist_part = take(F * (size_t)L->twist_blocks * 6 * 8);
+    L->twist_frame = take(F * 6 * 8);
     L->loss_part = take((size_t)kLossBlocks * 8);
     L->total = o;
     return true;
@@ -250,7 +252,8 @@ gs_status gs_render_fwd(const gs_batch *b, const float *colors, const gs_opts *o
     cudaError_t e = cudaMemsetAsync(&((Stats *)(w + L.stats))->eval_fwd, 0, 8, S(stream));
     if (e == cudaSuccess) e = prof_mark(GS_PROF_RENDER_FWD, true, S(stream));
     if (e == cudaSuccess)
-        e = launch_render_fwd(b, o, (const uint2 *)(w + L.ranges), (const uint32_t *)(w + L.vals[0]),
+        e = launch_render_fwd(b, o, (const uint32_t *)(w + L.order), (const uint2 *)(w + L.ranges),
+                              (const uint32_t *)(w + L.vals[0]),
                               (const float4 *)(w + L.splat), colors, (Stats *)(w + L.stats), out_rgb, out_T,
                               out_last, S(stream));
     if (e == cudaSuccess) e = prof_mark(GS_PROF_RENDER_FWD, false, S(stream));
@@ -281,7 +284,8 @@ gs_status gs_render_bwd(const gs_batch *b, const float *X, const float *quat, co
     cudaError_t e = cudaMemsetAsync(&st->eval_bwd, 0, 8, S(stream));
     if (e == cudaSuccess) e = prof_mark(GS_PROF_RENDER_BWD, true, S(stream));
     if (e == cudaSuccess)
-        e = launch_render_bwd(b, o, (const uint2 *)(w + L.ranges), (const uint32_t *)(w + L.vals[0]),
+        e = launch_render_bwd(b, o, (const uint32_t *)(w + L.order), (const uint2 *)(w + L.ranges),
+                              (const uint32_t *)(w + L.vals[0]),
                               (const float4 *)(w + L.splat), colors, st, out_T, out_last, dL_drgb,
                               (float4 *)(w + L.grad2d), S(stream));
     if (e == cudaSuccess) e = prof_mark(GS_PROF_RENDER_BWD, false, S(stream));
@@ -304,8 +308,8 @@ gs_status gs_pose_grad(const gs_batch *b, const double *ext, void *ws, double *d
     if (!batch_ok(b, ws) || !make_layout(b, &L) || !ext || !d_ext || !d_delta) return GS_ERR_INVALID_ARG;
     unsigned char *w = W(ws);
     return cuda_status(launch_pose_grad(b, L.twist_blocks, (const double *)(w + L.twist_part),
-                                        (const double *)(w + L.pose64), ext, d_ext, d_delta, d_xi, accumulate != 0,
-                                        S(stream)));
+                                        (double *)(w + L.twist_frame), (const double *)(w + L.pose64), ext, d_ext,
+                                        d_delta, d_xi, accumulate != 0, S(stream)));
 }
 
 }  // extern "C"

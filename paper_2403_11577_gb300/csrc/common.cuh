@@ -36,7 +36,7 @@ struct Stats {
 
 struct Layout {
     size_t stats, pose32, pose64, rect, depth, splat, grad2d, keys[2], vals[2], ranges,
-        emit_sums, sort_hist, twist_part, loss_part, total;
+        order, emit_sums, sort_hist, twist_part, twist_frame, loss_part, total;
     int emit_blocks;     // blocks of the pair count / emit kernels
     int sort_blocks;     // blocks of the radix sort kernels
     int twist_blocks;    // blocks of the projection backward

@@ -165,37 +165,47 @@ __global__ void k_pose_compose(const gs_frame *__restrict__ frames, int F, const
     for (int i = 27; i < kPose64Stride; i++) o64[i] = 0.0;
 }
 
-// One block per camera: sum the per-frame twist partials of the frames of
-// that camera (deterministic order), then map to the parameter gradients.
-__global__ void k_pose_grad(const gs_frame *__restrict__ frames, int F, int nparts,
-                            const double *__restrict__ twist_part, const double *__restrict__ pose64,
-                            const double *__restrict__ ext, double *__restrict__ d_ext,
-                            double *__restrict__ d_delta, double *__restrict__ d_xi, bool acc) {
-    const int cam = blockIdx.x;
-    __shared__ double red[256][7];
-    double sum7[7] = {0, 0, 0, 0, 0, 0, 0};  // g_eps (6) and -nu . g_eps
+// One block per frame: sum the frame's per-block twist partials (FP64, fixed
+// order) into g_eps[f][6].
+__global__ void __launch_bounds__(256)
+k_twist_reduce(int nparts, const double *__restrict__ twist_part, double *__restrict__ g_eps) {
+    __shared__ double red[256 / 32][6];
+    const int f = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double g[6] = {0, 0, 0, 0, 0, 0};
+    for (int b = threadIdx.x; b < nparts; b += blockDim.x) {
+        const double *src = twist_part + ((size_t)f * nparts + b) * 6;
+        for (int i = 0; i < 6; i++) g[i] += src[i];
+    }
+    for (int i = 0; i < 6; i++)
+        for (int s = 16; s > 0; s >>= 1) g[i] += __shfl_xor_sync(0xffffffffu, g[i], s);
+    if (lane == 0)
+        for (int i = 0; i < 6; i++) red[warp][i] = g[i];
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        double s = 0;
+        for (int w = 0; w < 256 / 32; w++) s += red[w][threadIdx.x];
+        g_eps[6 * f + threadIdx.x] = s;
+    }
+}
+
+// One thread per camera: sum the twists of the camera's frames and map them
+// to the parameter gradients.
+__global__ void k_pose_grad(const gs_frame *__restrict__ frames, int F, int C, const double *__restrict__ g_eps,
+                            const double *__restrict__ pose64, const double *__restrict__ ext,
+                            double *__restrict__ d_ext, double *__restrict__ d_delta, double *__restrict__ d_xi,
+                            bool acc) {
+    const int cam = blockIdx.x * blockDim.x + threadIdx.x;
+    if (cam >= C) return;
+    double g[7] = {0, 0, 0, 0, 0, 0, 0};  // g_eps (6) and -nu . g_eps
     for (int f = 0; f < F; f++) {
         if (frames[f].camera_id != cam) continue;
-        double g[6] = {0, 0, 0, 0, 0, 0};
-        for (int b = threadIdx.x; b < nparts; b += blockDim.x) {
-            const double *src = twist_part + ((size_t)f * nparts + b) * 6;
-            for (int i = 0; i < 6; i++) g[i] += src[i];
-        }
+        const double *ge = g_eps + 6 * f;
         const double *nu = pose64 + kPose64Stride * f + 12;
-        double dd = 0;
-        for (int i = 0; i < 6; i++) dd -= nu[i] * g[i];
-        for (int i = 0; i < 6; i++) sum7[i] += g[i];
-        sum7[6] += dd;
+        for (int i = 0; i < 6; i++) {
+            g[i] += ge[i];
+            g[6] -= nu[i] * ge[i];
+        }
     }
-    for (int i = 0; i < 7; i++) red[threadIdx.x][i] = sum7[i];
-    __syncthreads();
-    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-        if (threadIdx.x < s)
-            for (int i = 0; i < 7; i++) red[threadIdx.x][i] += red[threadIdx.x + s][i];
-        __syncthreads();
-    }
-    if (threadIdx.x != 0) return;
-    const double *g = red[0];
     const double *e = ext + 6 * cam;
     double R_e[9], Jr[9];
     so3_exp(e, R_e);
@@ -222,11 +232,13 @@ cudaError_t launch_pose_compose(const gs_batch *b, const double *traj_t, const d
     return cudaGetLastError();
 }
 
-cudaError_t launch_pose_grad(const gs_batch *b, int nparts, const double *twist_part,
+cudaError_t launch_pose_grad(const gs_batch *b, int nparts, const double *twist_part, double *g_eps,
                              const double *pose64, const double *ext, double *d_ext, double *d_delta,
                              double *d_xi, bool acc, cudaStream_t s) {
-    k_pose_grad<<<b->num_cameras, 256, 0, s>>>(b->frames_dev, b->num_frames, nparts, twist_part, pose64,
-                                               ext, d_ext, d_delta, d_xi, acc);
+    k_twist_reduce<<<b->num_frames, 256, 0, s>>>(nparts, twist_part, g_eps);
+    const int C = b->num_cameras;
+    k_pose_grad<<<(C + 31) / 32, 32, 0, s>>>(b->frames_dev, b->num_frames, C, g_eps, pose64, ext, d_ext, d_delta,
+                                             d_xi, acc);
     return cudaGetLastError();
 }
 

@@ -195,7 +195,7 @@ k_project(const gs_frame *__restrict__ frames, int F, int N, const float *__rest
 
 // ---------------------------------------------------------------- backward
 
-__device__ __forceinline__ double warp_sum(double v) {
+__device__ __forceinline__ float warp_sum(float v) {
     for (int s = 16; s > 0; s >>= 1) v += __shfl_xor_sync(0xffffffffu, v, s);
     return v;
 }
@@ -224,7 +224,7 @@ k_project_bwd(const gs_frame *__restrict__ frames, int F, int N, const float *__
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int f = 0; f < F; f++) {
         const gs_frame &fr = frames[f];
-        double tw[6] = {0, 0, 0, 0, 0, 0};
+        float tw[6] = {0, 0, 0, 0, 0, 0};
         bool mine = active && g >= fr.gauss_offset && g < fr.gauss_offset + fr.gauss_count;
         if (mine) {
             const long long r = fr.record_offset + (g - fr.gauss_offset);
@@ -297,15 +297,17 @@ k_project_bwd(const gs_frame *__restrict__ frames, int F, int N, const float *__
                 tw[0] = dp[0];
                 tw[1] = dp[1];
                 tw[2] = dp[2];
-                tw[3] = (double)(p[1] * dp[2] - p[2] * dp[1]) + (double)(Mm[5] - Mm[7]);
-                tw[4] = (double)(p[2] * dp[0] - p[0] * dp[2]) + (double)(Mm[6] - Mm[2]);
-                tw[5] = (double)(p[0] * dp[1] - p[1] * dp[0]) + (double)(Mm[1] - Mm[3]);
+                tw[3] = (p[1] * dp[2] - p[2] * dp[1]) + (Mm[5] - Mm[7]);
+                tw[4] = (p[2] * dp[0] - p[0] * dp[2]) + (Mm[6] - Mm[2]);
+                tw[5] = (p[0] * dp[1] - p[1] * dp[0]) + (Mm[1] - Mm[3]);
             }
         }
-        // deterministic block reduction of the frame's twist (FP64)
+        // deterministic block reduction of the frame's twist: float within
+        // the warp (32 terms), double across warps and blocks (GB300's FP64
+        // rate is low, so only per-warp partials are widened)
         for (int i = 0; i < 6; i++) tw[i] = warp_sum(tw[i]);
         if (lane == 0)
-            for (int i = 0; i < 6; i++) red[warp][i] = tw[i];
+            for (int i = 0; i < 6; i++) red[warp][i] = (double)tw[i];
         __syncthreads();
         if (threadIdx.x < 6) {
             double s = 0;

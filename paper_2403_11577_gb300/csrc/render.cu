@@ -1,7 +1,8 @@
 // Phi (Eq. 5): front-to-back alpha compositing of the depth-sorted splats of
 // each tile, and its backward (Sec. III-B).
 //
-// One block per (frame, tile) work item of the whole batch.  Per round the
+// One block per (frame, tile) work item of the whole batch, taken in the
+// heavy-first order gs_bin_sort computes (longest lists start first).  Per round the
 // block stages BATCH Gaussians of the tile's sorted range in shared memory
 // (mean, exponent coefficients, colour), then every thread walks them for
 // its PPT pixels.  A pixel stops when compositing the next Gaussian would
@@ -23,8 +24,10 @@
 // giving dL/dF = dL/de, dL/dA = dL/de dx^2, dL/dB = dL/de dx dy,
 // dL/dC = dL/de dy^2, dL/dmean = -dL/de (2A dx + B dy, B dx + 2C dy).
 // The nine per-pixel values are summed over the thread's pixels, then over
-// the warp with shuffles (skipped when no lane contributes), and added to the
-// record's gradient with one float4/float4/float atomic triple per warp.
+// the warp (skipped when no lane contributes): eight of them by a transposed
+// halving exchange that leaves one total per group of four lanes, which the
+// group's first lane adds to the record (eight lanes, contiguous addresses),
+// the ninth by a plain shuffle reduction.
 #include "common.cuh"
 
 namespace gs {
@@ -65,7 +68,8 @@ __device__ __forceinline__ void pixel_of(int tid, int k, int &lx, int &ly) {
 
 template <int TILE, int BATCH>
 __global__ void __launch_bounds__(Cfg<TILE>::NT)
-k_render_fwd(const gs_frame *__restrict__ frames, int F, const uint2 *__restrict__ ranges,
+k_render_fwd(const gs_frame *__restrict__ frames, int F, const uint32_t *__restrict__ order,
+             const uint2 *__restrict__ ranges,
              const uint32_t *__restrict__ vals, const float4 *__restrict__ splat,
              const float *__restrict__ colors, RenderParams rp, Stats *__restrict__ stats,
              float *__restrict__ out_rgb, float *__restrict__ out_T, int32_t *__restrict__ out_last) {
@@ -74,7 +78,7 @@ k_render_fwd(const gs_frame *__restrict__ frames, int F, const uint2 *__restrict
     __shared__ float4 s1[BATCH];
     __shared__ float s2[BATCH];
     __shared__ unsigned long long s_eval;
-    const int t = blockIdx.x;
+    const int t = (int)order[blockIdx.x];  // heavy tiles first
     const int f = frame_of_tile(frames, F, t);
     const gs_frame &fr = frames[f];
     const int W = fr.width, H = fr.height;
@@ -174,9 +178,38 @@ __device__ __forceinline__ float warp_sum_f(float v) {
     return v;
 }
 
+// Sum eight per-lane values over the warp by halving exchanges: at each step
+// a lane keeps half of its values and sends the other half to its partner,
+// so the exchanges shrink 4, 2, 1, 1, 1 (8 shuffles instead of 40).  On
+// return every lane holds the warp total of component
+// c = 4*bit4(lane) + 2*bit3(lane) + bit2(lane).
+__device__ __forceinline__ float warp_sum8_transposed(const float (&v)[8], int lane) {
+    const bool u16 = lane & 16, u8 = lane & 8, u4 = lane & 4;
+    float w[4];
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        const float send = u16 ? v[i] : v[i + 4];
+        const float keep = u16 ? v[i + 4] : v[i];
+        w[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+    float x[2];
+#pragma unroll
+    for (int i = 0; i < 2; i++) {
+        const float send = u8 ? w[i] : w[i + 2];
+        const float keep = u8 ? w[i + 2] : w[i];
+        x[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+    const float send = u4 ? x[0] : x[1];
+    float y = (u4 ? x[1] : x[0]) + __shfl_xor_sync(0xffffffffu, send, 4);
+    y += __shfl_xor_sync(0xffffffffu, y, 2);
+    y += __shfl_xor_sync(0xffffffffu, y, 1);
+    return y;
+}
+
 template <int TILE, int BATCH>
 __global__ void __launch_bounds__(Cfg<TILE>::NT)
-k_render_bwd(const gs_frame *__restrict__ frames, int F, const uint2 *__restrict__ ranges,
+k_render_bwd(const gs_frame *__restrict__ frames, int F, const uint32_t *__restrict__ order,
+             const uint2 *__restrict__ ranges,
              const uint32_t *__restrict__ vals, const float4 *__restrict__ splat,
              const float *__restrict__ colors, RenderParams rp, Stats *__restrict__ stats,
              const float *__restrict__ in_T, const int32_t *__restrict__ in_last,
@@ -188,7 +221,7 @@ k_render_bwd(const gs_frame *__restrict__ frames, int F, const uint2 *__restrict
     __shared__ long long s_rec[BATCH];
     __shared__ int s_maxlast;
     __shared__ unsigned long long s_eval;
-    const int t = blockIdx.x;
+    const int t = (int)order[blockIdx.x];  // heavy tiles first
     const int f = frame_of_tile(frames, F, t);
     const gs_frame &fr = frames[f];
     const int W = fr.width, H = fr.height;
@@ -292,21 +325,13 @@ k_render_bwd(const gs_frame *__restrict__ frames, int F, const uint2 *__restrict
                 dmy -= de * (a.w * dx + 2.f * b.x * dy);
             }
             if (__any_sync(0xffffffffu, any)) {
-                dmx = warp_sum_f(dmx);
-                dmy = warp_sum_f(dmy);
-                dA = warp_sum_f(dA);
-                dB = warp_sum_f(dB);
-                dC = warp_sum_f(dC);
-                dF = warp_sum_f(dF);
-                dr = warp_sum_f(dr);
-                dg = warp_sum_f(dg);
+                // record layout: (dmx, dmy, dA, dB), (dC, dF, dr, dg), (db, -, -, -)
+                const float v8[8] = {dmx, dmy, dA, dB, dC, dF, dr, dg};
+                const float tot = warp_sum8_transposed(v8, lane);
                 db = warp_sum_f(db);
-                if (lane == 0) {
-                    const long long r = s_rec[j];
-                    atomicAdd(&grad2d[3 * r], make_float4(dmx, dmy, dA, dB));
-                    atomicAdd(&grad2d[3 * r + 1], make_float4(dC, dF, dr, dg));
-                    atomicAdd(&grad2d[3 * r + 2].x, db);
-                }
+                float *rec = reinterpret_cast<float *>(grad2d + 3 * s_rec[j]);
+                if ((lane & 3) == 0) atomicAdd(rec + (lane >> 2), tot);
+                if (lane == 0) atomicAdd(rec + 8, db);
             }
         }
         __syncthreads();
@@ -319,20 +344,22 @@ k_render_bwd(const gs_frame *__restrict__ frames, int F, const uint2 *__restrict
 }
 
 template <int TILE, int BATCH>
-cudaError_t run_fwd(const gs_batch *b, const uint2 *ranges, const uint32_t *vals, const float4 *splat,
+cudaError_t run_fwd(const gs_batch *b, const uint32_t *order, const uint2 *ranges, const uint32_t *vals,
+                    const float4 *splat,
                     const float *colors, RenderParams rp, Stats *stats, float *out_rgb, float *out_T,
                     int32_t *out_last, cudaStream_t s) {
     k_render_fwd<TILE, BATCH><<<b->num_tiles, Cfg<TILE>::NT, 0, s>>>(
-        b->frames_dev, b->num_frames, ranges, vals, splat, colors, rp, stats, out_rgb, out_T, out_last);
+        b->frames_dev, b->num_frames, order, ranges, vals, splat, colors, rp, stats, out_rgb, out_T, out_last);
     return cudaGetLastError();
 }
 
 template <int TILE, int BATCH>
-cudaError_t run_bwd(const gs_batch *b, const uint2 *ranges, const uint32_t *vals, const float4 *splat,
+cudaError_t run_bwd(const gs_batch *b, const uint32_t *order, const uint2 *ranges, const uint32_t *vals,
+                    const float4 *splat,
                     const float *colors, RenderParams rp, Stats *stats, const float *in_T, const int32_t *in_last,
                     const float *dL, float4 *grad2d, cudaStream_t s) {
     k_render_bwd<TILE, BATCH><<<b->num_tiles, Cfg<TILE>::NT, 0, s>>>(
-        b->frames_dev, b->num_frames, ranges, vals, splat, colors, rp, stats, in_T, in_last, dL, grad2d);
+        b->frames_dev, b->num_frames, order, ranges, vals, splat, colors, rp, stats, in_T, in_last, dL, grad2d);
     return cudaGetLastError();
 }
 
@@ -363,22 +390,24 @@ RenderParams make_params(const gs_opts *o) {
     default: return cudaErrorInvalidValue;                         \
     }
 
-cudaError_t launch_render_fwd(const gs_batch *b, const gs_opts *o, const uint2 *ranges, const uint32_t *vals,
+cudaError_t launch_render_fwd(const gs_batch *b, const gs_opts *o, const uint32_t *order, const uint2 *ranges,
+                              const uint32_t *vals,
                               const float4 *splat, const float *colors, Stats *stats, float *out_rgb,
                               float *out_T, int32_t *out_last, cudaStream_t s) {
     if (b->num_tiles == 0) return cudaSuccess;
     const RenderParams rp = make_params(o);
-#define GS_FWD(T_, B_) run_fwd<T_, B_>(b, ranges, vals, splat, colors, rp, stats, out_rgb, out_T, out_last, s)
+#define GS_FWD(T_, B_) run_fwd<T_, B_>(b, order, ranges, vals, splat, colors, rp, stats, out_rgb, out_T, out_last, s)
     GS_DISPATCH(o->tile, o->batch, GS_FWD)
 #undef GS_FWD
 }
 
-cudaError_t launch_render_bwd(const gs_batch *b, const gs_opts *o, const uint2 *ranges, const uint32_t *vals,
+cudaError_t launch_render_bwd(const gs_batch *b, const gs_opts *o, const uint32_t *order, const uint2 *ranges,
+                              const uint32_t *vals,
                               const float4 *splat, const float *colors, Stats *stats, const float *in_T,
                               const int32_t *in_last, const float *dL, float4 *grad2d, cudaStream_t s) {
     if (b->num_tiles == 0) return cudaSuccess;
     const RenderParams rp = make_params(o);
-#define GS_BWD(T_, B_) run_bwd<T_, B_>(b, ranges, vals, splat, colors, rp, stats, in_T, in_last, dL, grad2d, s)
+#define GS_BWD(T_, B_) run_bwd<T_, B_>(b, order, ranges, vals, splat, colors, rp, stats, in_T, in_last, dL, grad2d, s)
     GS_DISPATCH(o->tile, o->batch, GS_BWD)
 #undef GS_BWD
 }
