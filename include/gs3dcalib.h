@@ -156,7 +156,10 @@ size_t gs_workspace_size(const gs_batch *batch);
  * row-major 9, camera centre hi 3, camera centre lo 3, pad), [2] pose64
  * (double[F][32]), [3] rect (uint32[R][2]: x0 | y0 << 16, x1 | y1 << 16,
  * inclusive tile coordinates, empty as x0 > x1), [4] depth (float[R]),
- * [5] splat (float4[R][2]), [6] grad2d (float4[R][3]), [7] keys
+ * [5] splat (float4[R][2]: (mean_x, mean_y, A, B), (C, F, rx, ry), the
+ * base-2 exponent log2 alpha = A dx^2 + B dx dy + C dy^2 + F and the
+ * half-widths of the box outside which alpha < alpha_min), [6] grad2d
+ * (float4[R][3]: d/d(mean_x, mean_y, A, B), d/d(C, F, r, g), d/d(b)), [7] keys
  * (uint64[pair_capacity]), [8] vals (uint32[pair_capacity]), [9] ranges
  * (uint32[T][2]: [start, end) of each tile in keys/vals).  Returns the
  * number of offsets written (<= max_entries). */

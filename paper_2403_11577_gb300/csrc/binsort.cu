@@ -365,10 +365,14 @@ k_tile_order(const uint2 *__restrict__ ranges, int T, uint32_t *__restrict__ ord
     __shared__ uint32_t cnt[kOrderBuckets], base[kOrderBuckets];
     if (threadIdx.x < kOrderBuckets) cnt[threadIdx.x] = 0;
     __syncthreads();
-    auto bucket = [](uint32_t len) { return len == 0 ? 0 : 32 - __clz(len); };  // 0..32
-    for (int t = threadIdx.x; t < T; t += blockDim.x) {
-        const uint2 r = ranges[t];
-        atomicAdd(&cnt[bucket(r.y - r.x)], 1u);
+    auto bucket = [](uint32_t len) { return len == 0 ? 0u : (uint32_t)(32 - __clz(len)); };  // 0..32
+    const int lane = threadIdx.x & 31;
+    // warp-aggregated counting: one shared atomic per distinct bucket per warp
+    for (int t0 = 0; t0 < T; t0 += blockDim.x) {
+        const int t = t0 + threadIdx.x;
+        const uint32_t k = t < T ? bucket(ranges[t].y - ranges[t].x) : (uint32_t)(kOrderBuckets + lane);
+        const uint32_t peers = __match_any_sync(0xffffffffu, k);
+        if (t < T && (__ffs(peers) - 1) == lane) atomicAdd(&cnt[k], (uint32_t)__popc(peers));
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -379,9 +383,15 @@ k_tile_order(const uint2 *__restrict__ ranges, int T, uint32_t *__restrict__ ord
         }
     }
     __syncthreads();
-    for (int t = threadIdx.x; t < T; t += blockDim.x) {
-        const uint2 r = ranges[t];
-        order[atomicAdd(&base[bucket(r.y - r.x)], 1u)] = (uint32_t)t;
+    for (int t0 = 0; t0 < T; t0 += blockDim.x) {
+        const int t = t0 + threadIdx.x;
+        const uint32_t k = t < T ? bucket(ranges[t].y - ranges[t].x) : (uint32_t)(kOrderBuckets + lane);
+        const uint32_t peers = __match_any_sync(0xffffffffu, k);
+        const int leader = __ffs(peers) - 1;
+        uint32_t start = 0;
+        if (t < T && leader == lane) start = atomicAdd(&base[k], (uint32_t)__popc(peers));
+        start = __shfl_sync(0xffffffffu, start, leader);
+        if (t < T) order[start + __popc(peers & ((1u << lane) - 1u))] = (uint32_t)t;
     }
 }
 

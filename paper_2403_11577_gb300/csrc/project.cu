@@ -17,10 +17,11 @@
 //             half-widths sqrt(k cov_xx), sqrt(k cov_yy), widened by a
 //             relative 1e-4 and 0.01 px against float32 rounding;
 //   depth[r]  camera depth p.z;
-//   splat[r]  (mean_x, mean_y, A, B), (C, F, opacity, depth) with the
-//             exponent in base 2: log2 alpha = A dx^2 + B dx dy + C dy^2 + F,
+//   splat[r]  (mean_x, mean_y, A, B), (C, F, rx, ry) with the exponent in
+//             base 2: log2 alpha = A dx^2 + B dx dy + C dy^2 + F,
 //             A = -a/2 log2 e, B = -b log2 e, C = -c/2 log2 e, F = log2 opacity,
-//             (a, b, c) the conic;
+//             (a, b, c) the conic, and (rx, ry) the guarded half-widths of the
+//             box outside which alpha < alpha_min (the rect's extents, in px);
 //   grad2d[r] zeroed for visible records (the render backward accumulates
 //             into it).
 #include "common.cuh"
@@ -179,7 +180,7 @@ k_project(const gs_frame *__restrict__ frames, int F, int N, const float *__rest
                     rc = make_uint2((uint32_t)x0 | ((uint32_t)y0 << 16), (uint32_t)x1 | ((uint32_t)y1 << 16));
                     const float s2 = -0.5f * kLog2e;
                     splat[2 * r] = make_float4(Q.mean[0], Q.mean[1], s2 * Q.conic[0], -kLog2e * Q.conic[1]);
-                    splat[2 * r + 1] = make_float4(s2 * Q.conic[2], G.F, G.o, Q.p[2]);
+                    splat[2 * r + 1] = make_float4(s2 * Q.conic[2], G.F, rx, ry);
                     const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
                     grad2d[3 * r] = z4;
                     grad2d[3 * r + 1] = z4;

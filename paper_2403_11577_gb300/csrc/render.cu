@@ -4,8 +4,11 @@
 // One block per (frame, tile) work item of the whole batch, taken in the
 // heavy-first order gs_bin_sort computes (longest lists start first).  Per round the
 // block stages BATCH Gaussians of the tile's sorted range in shared memory
-// (mean, exponent coefficients, colour), then every thread walks them for
-// its PPT pixels.  A pixel stops when compositing the next Gaussian would
+// (mean, exponent coefficients, colour, alpha box).  Each warp owns a compact
+// full-width band of the tile; it ballots which staged Gaussians' alpha >=
+// alpha_min boxes meet its band and walks only those (in depth order, for
+// its PPT pixels per thread): outside the box alpha is below alpha_min, so
+// the cull is exact, and it is the same in both directions.  A pixel stops when compositing the next Gaussian would
 // bring its transmittance below t_min; the block stops when all its pixels
 // have stopped (checked once per round with a block vote).
 //
@@ -38,7 +41,8 @@ template <int TILE>
 struct Cfg {
     static constexpr int NPIX = TILE * TILE;
     static constexpr int NT = NPIX < 256 ? NPIX : 256;
-    static constexpr int PPT = NPIX / NT;
+    static constexpr int PPT = NPIX / NT;          // pixels per thread
+    static constexpr int RPW = 32 * PPT / TILE;    // pixel rows per warp (full tile width)
 };
 
 struct RenderParams {
@@ -57,26 +61,34 @@ __device__ __forceinline__ float exponent2(float dx, float dy, float A, float B,
     return __fmaf_rn(dx, t, q);
 }
 
-// Pixel (lx, ly) of the tile handled by thread `tid` as its k-th pixel:
-// thread rows of TILE pixels, k stacks the thread over PPT row blocks.
+// Pixel (lx, ly) of the tile handled by thread `tid` as its k-th pixel.  A
+// warp covers RPW consecutive full-width rows, so its pixels form a compact
+// TILE x RPW region (used to cull Gaussians per warp).
 template <int TILE>
 __device__ __forceinline__ void pixel_of(int tid, int k, int &lx, int &ly) {
-    constexpr int NT = Cfg<TILE>::NT;
     lx = tid % TILE;
-    ly = (tid / TILE) + k * (NT / TILE);
+    ly = (tid / TILE) * Cfg<TILE>::PPT + k;
+}
+
+// Whether the Gaussian's alpha >= alpha_min box (centre m, half-widths e)
+// meets the warp's pixel region.  Outside that box alpha < alpha_min at
+// every pixel, so skipping is exact; forward and backward use this same test.
+__device__ __forceinline__ bool box_hits(float4 a, float2 e, float xlo, float xhi, float ylo, float yhi) {
+    return (a.x + e.x >= xlo) && (a.x - e.x <= xhi) && (a.y + e.y >= ylo) && (a.y - e.y <= yhi);
 }
 
 template <int TILE, int BATCH>
 __global__ void __launch_bounds__(Cfg<TILE>::NT)
 k_render_fwd(const gs_frame *__restrict__ frames, int F, const uint32_t *__restrict__ order,
-             const uint2 *__restrict__ ranges,
-             const uint32_t *__restrict__ vals, const float4 *__restrict__ splat,
-             const float *__restrict__ colors, RenderParams rp, Stats *__restrict__ stats,
-             float *__restrict__ out_rgb, float *__restrict__ out_T, int32_t *__restrict__ out_last) {
-    constexpr int NT = Cfg<TILE>::NT, PPT = Cfg<TILE>::PPT;
-    __shared__ float4 s0[BATCH];
-    __shared__ float4 s1[BATCH];
-    __shared__ float s2[BATCH];
+             const uint2 *__restrict__ ranges, const uint32_t *__restrict__ vals,
+             const float4 *__restrict__ splat, const float *__restrict__ colors, RenderParams rp,
+             Stats *__restrict__ stats, float *__restrict__ out_rgb, float *__restrict__ out_T,
+             int32_t *__restrict__ out_last) {
+    constexpr int NT = Cfg<TILE>::NT, PPT = Cfg<TILE>::PPT, RPW = Cfg<TILE>::RPW;
+    __shared__ float4 s0[BATCH];  // mean_x, mean_y, A, B
+    __shared__ float4 s1[BATCH];  // C, F, r, g
+    __shared__ float s2[BATCH];   // b
+    __shared__ float2 s3[BATCH];  // box half-widths
     __shared__ unsigned long long s_eval;
     const int t = (int)order[blockIdx.x];  // heavy tiles first
     const int f = frame_of_tile(frames, F, t);
@@ -84,6 +96,9 @@ k_render_fwd(const gs_frame *__restrict__ frames, int F, const uint32_t *__restr
     const int W = fr.width, H = fr.height;
     const int lt = t - fr.tile_offset;
     const int tx = lt % fr.tiles_x, ty = lt / fr.tiles_x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const float xlo = (float)(tx * TILE), xhi = xlo + (float)(TILE - 1);
+    const float ylo = (float)(ty * TILE + warp * RPW), yhi = ylo + (float)(RPW - 1);
     float px[PPT], py[PPT], T[PPT], c0[PPT], c1[PPT], c2[PPT];
     int last[PPT];
     bool done[PPT], inside[PPT];
@@ -120,34 +135,43 @@ k_render_fwd(const gs_frame *__restrict__ frames, int F, const uint32_t *__restr
                 s0[i] = a;
                 s1[i] = make_float4(b.x, b.y, __ldg(col + 3 * g), __ldg(col + 3 * g + 1));
                 s2[i] = __ldg(col + 3 * g + 2);
+                s3[i] = make_float2(b.z, b.w);
             }
         }
         __syncthreads();
         const int m = min(BATCH, n - b0);
-        for (int j = 0; j < m; j++) {
-            const float4 a = s0[j], b = s1[j];
-            const float cb = s2[j];
+        if (!__all_sync(0xffffffffu, mine_done)) {
+            for (int q = 0; q * 32 < m; q++) {
+                const int i = q * 32 + lane;
+                uint32_t msk = __ballot_sync(0xffffffffu, i < m && box_hits(s0[i], s3[i], xlo, xhi, ylo, yhi));
+                while (msk) {
+                    const int j = q * 32 + __ffs(msk) - 1;
+                    msk &= msk - 1;
+                    const float4 a = s0[j], b = s1[j];
+                    const float cb = s2[j];
 #pragma unroll
-            for (int k = 0; k < PPT; k++) {
-                if (done[k]) continue;
-                evals++;
-                const float dx = px[k] - a.x, dy = py[k] - a.y;
-                const float e2 = exponent2(dx, dy, a.z, a.w, b.x);
-                if (e2 > 0.f) continue;
-                const float e = e2 + b.y;
-                if (e < rp.lmin) continue;
-                const float alpha = fminf(rp.amax, ex2_approx(e));
-                const float nT = T[k] * (1.f - alpha);
-                if (nT < rp.tmin) {
-                    done[k] = true;
-                    continue;
+                    for (int k = 0; k < PPT; k++) {
+                        if (done[k]) continue;
+                        evals++;
+                        const float dx = px[k] - a.x, dy = py[k] - a.y;
+                        const float e2 = exponent2(dx, dy, a.z, a.w, b.x);
+                        if (e2 > 0.f) continue;
+                        const float e = e2 + b.y;
+                        if (e < rp.lmin) continue;
+                        const float alpha = fminf(rp.amax, ex2_approx(e));
+                        const float nT = T[k] * (1.f - alpha);
+                        if (nT < rp.tmin) {
+                            done[k] = true;
+                            continue;
+                        }
+                        const float w = alpha * T[k];
+                        c0[k] = fmaf(b.z, w, c0[k]);
+                        c1[k] = fmaf(b.w, w, c1[k]);
+                        c2[k] = fmaf(cb, w, c2[k]);
+                        T[k] = nT;
+                        last[k] = b0 + j + 1;
+                    }
                 }
-                const float w = alpha * T[k];
-                c0[k] = fmaf(b.z, w, c0[k]);
-                c1[k] = fmaf(b.w, w, c1[k]);
-                c2[k] = fmaf(cb, w, c2[k]);
-                T[k] = nT;
-                last[k] = b0 + j + 1;
             }
         }
         __syncthreads();
@@ -168,7 +192,7 @@ k_render_fwd(const gs_frame *__restrict__ frames, int F, const uint32_t *__restr
     unsigned long long ev = evals;
     for (int s = 16; s > 0; s >>= 1) ev += __shfl_xor_sync(0xffffffffu, ev, s);
     __syncthreads();
-    if ((threadIdx.x & 31) == 0) atomicAdd(&s_eval, ev);
+    if (lane == 0) atomicAdd(&s_eval, ev);
     __syncthreads();
     if (threadIdx.x == 0) atomicAdd(&stats->eval_fwd, s_eval);
 }
@@ -209,15 +233,15 @@ __device__ __forceinline__ float warp_sum8_transposed(const float (&v)[8], int l
 template <int TILE, int BATCH>
 __global__ void __launch_bounds__(Cfg<TILE>::NT)
 k_render_bwd(const gs_frame *__restrict__ frames, int F, const uint32_t *__restrict__ order,
-             const uint2 *__restrict__ ranges,
-             const uint32_t *__restrict__ vals, const float4 *__restrict__ splat,
-             const float *__restrict__ colors, RenderParams rp, Stats *__restrict__ stats,
-             const float *__restrict__ in_T, const int32_t *__restrict__ in_last,
+             const uint2 *__restrict__ ranges, const uint32_t *__restrict__ vals,
+             const float4 *__restrict__ splat, const float *__restrict__ colors, RenderParams rp,
+             Stats *__restrict__ stats, const float *__restrict__ in_T, const int32_t *__restrict__ in_last,
              const float *__restrict__ dL_drgb, float4 *__restrict__ grad2d) {
-    constexpr int NT = Cfg<TILE>::NT, PPT = Cfg<TILE>::PPT;
+    constexpr int NT = Cfg<TILE>::NT, PPT = Cfg<TILE>::PPT, RPW = Cfg<TILE>::RPW;
     __shared__ float4 s0[BATCH];
     __shared__ float4 s1[BATCH];
     __shared__ float s2[BATCH];
+    __shared__ float2 s3[BATCH];
     __shared__ long long s_rec[BATCH];
     __shared__ int s_maxlast;
     __shared__ unsigned long long s_eval;
@@ -227,6 +251,9 @@ k_render_bwd(const gs_frame *__restrict__ frames, int F, const uint32_t *__restr
     const int W = fr.width, H = fr.height;
     const int lt = t - fr.tile_offset;
     const int tx = lt % fr.tiles_x, ty = lt / fr.tiles_x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const float xlo = (float)(tx * TILE), xhi = xlo + (float)(TILE - 1);
+    const float ylo = (float)(ty * TILE + warp * RPW), yhi = ylo + (float)(RPW - 1);
     float px[PPT], py[PPT], T[PPT], Tf[PPT], g0[PPT], g1[PPT], g2[PPT], bgd[PPT];
     float a0[PPT], a1[PPT], a2[PPT];
     int last[PPT];
@@ -235,6 +262,9 @@ k_render_bwd(const gs_frame *__restrict__ frames, int F, const uint32_t *__restr
         s_eval = 0;
     }
     __syncthreads();
+    // the range of this tile; a pixel's start position never exceeds it
+    const uint2 range = ranges[t];
+    const int n = (int)(range.y - range.x);
     int mylast = 0;
 #pragma unroll
     for (int k = 0; k < PPT; k++) {
@@ -247,7 +277,7 @@ k_render_bwd(const gs_frame *__restrict__ frames, int F, const uint32_t *__restr
         if (u < W && v < H) {
             const long long pix = fr.pixel_offset + (long long)v * W + u;
             Tf[k] = in_T[pix];
-            last[k] = in_last[pix];
+            last[k] = min(max(in_last[pix], 0), n);
             g0[k] = dL_drgb[3 * pix];
             g1[k] = dL_drgb[3 * pix + 1];
             g2[k] = dL_drgb[3 * pix + 2];
@@ -260,18 +290,12 @@ k_render_bwd(const gs_frame *__restrict__ frames, int F, const uint32_t *__restr
         bgd[k] = rp.bg0 * g0[k] + rp.bg1 * g1[k] + rp.bg2 * g2[k];
         mylast = max(mylast, last[k]);
     }
-    // the range of this tile; a pixel's start position never exceeds it
-    const uint2 range = ranges[t];
-    const int n = (int)(range.y - range.x);
-#pragma unroll
-    for (int k = 0; k < PPT; k++) last[k] = min(max(last[k], 0), n);
-    mylast = min(max(mylast, 0), n);
-    atomicMax(&s_maxlast, mylast);
+    const int warp_last = __reduce_max_sync(0xffffffffu, mylast);
+    if (lane == 0) atomicMax(&s_maxlast, warp_last);
     __syncthreads();
     const int maxlast = s_maxlast;
     const long long rec0 = fr.record_offset;
     const float *col = colors + 3 * (size_t)fr.gauss_offset;
-    const int lane = threadIdx.x & 31;
     unsigned evals = 0;
     for (int b_end = maxlast; b_end > 0; b_end -= BATCH) {
         const int b0 = max(0, b_end - BATCH);
@@ -283,55 +307,65 @@ k_render_bwd(const gs_frame *__restrict__ frames, int F, const uint32_t *__restr
             s0[i] = a;
             s1[i] = make_float4(b.x, b.y, __ldg(col + 3 * g), __ldg(col + 3 * g + 1));
             s2[i] = __ldg(col + 3 * g + 2);
+            s3[i] = make_float2(b.z, b.w);
             s_rec[i] = r;
         }
         __syncthreads();
-        for (int j = m - 1; j >= 0; j--) {
-            const int pos = b0 + j;
-            const float4 a = s0[j], b = s1[j];
-            const float cb = s2[j];
-            float dmx = 0.f, dmy = 0.f, dA = 0.f, dB = 0.f, dC = 0.f, dF = 0.f, dr = 0.f, dg = 0.f, db = 0.f;
-            bool any = false;
+        // entries at or beyond the warp's largest start position concern none of its pixels
+        const int mw = min(m, warp_last - b0);
+        for (int q = (mw - 1) >> 5; q >= 0; q--) {
+            const int i = q * 32 + lane;
+            uint32_t msk = __ballot_sync(0xffffffffu, i < mw && box_hits(s0[i], s3[i], xlo, xhi, ylo, yhi));
+            while (msk) {
+                const int bit = 31 - __clz(msk);
+                msk &= ~(1u << bit);
+                const int j = q * 32 + bit;
+                const int pos = b0 + j;
+                const float4 a = s0[j], b = s1[j];
+                const float cb = s2[j];
+                float dmx = 0.f, dmy = 0.f, dA = 0.f, dB = 0.f, dC = 0.f, dF = 0.f, dr = 0.f, dg = 0.f, db = 0.f;
+                bool any = false;
 #pragma unroll
-            for (int k = 0; k < PPT; k++) {
-                if (pos >= last[k]) continue;
-                evals++;
-                const float dx = px[k] - a.x, dy = py[k] - a.y;
-                const float e2 = exponent2(dx, dy, a.z, a.w, b.x);
-                if (e2 > 0.f) continue;
-                const float e = e2 + b.y;
-                if (e < rp.lmin) continue;
-                const float G = ex2_approx(e);
-                const float alpha = fminf(rp.amax, G);
-                const float om = 1.f - alpha;
-                T[k] = T[k] / om;
-                const float w = alpha * T[k];
-                dr = fmaf(w, g0[k], dr);
-                dg = fmaf(w, g1[k], dg);
-                db = fmaf(w, g2[k], db);
-                const float dalpha = T[k] * ((b.z - a0[k]) * g0[k] + (b.w - a1[k]) * g1[k] + (cb - a2[k]) * g2[k]) -
-                                     Tf[k] * bgd[k] / om;
-                a0[k] = fmaf(alpha, b.z - a0[k], a0[k]);
-                a1[k] = fmaf(alpha, b.w - a1[k], a1[k]);
-                a2[k] = fmaf(alpha, cb - a2[k], a2[k]);
-                any = true;
-                if (G > rp.amax) continue;
-                const float de = dalpha * alpha * kLn2;
-                dF += de;
-                dA = fmaf(de * dx, dx, dA);
-                dB = fmaf(de * dx, dy, dB);
-                dC = fmaf(de * dy, dy, dC);
-                dmx -= de * (2.f * a.z * dx + a.w * dy);
-                dmy -= de * (a.w * dx + 2.f * b.x * dy);
-            }
-            if (__any_sync(0xffffffffu, any)) {
-                // record layout: (dmx, dmy, dA, dB), (dC, dF, dr, dg), (db, -, -, -)
-                const float v8[8] = {dmx, dmy, dA, dB, dC, dF, dr, dg};
-                const float tot = warp_sum8_transposed(v8, lane);
-                db = warp_sum_f(db);
-                float *rec = reinterpret_cast<float *>(grad2d + 3 * s_rec[j]);
-                if ((lane & 3) == 0) atomicAdd(rec + (lane >> 2), tot);
-                if (lane == 0) atomicAdd(rec + 8, db);
+                for (int k = 0; k < PPT; k++) {
+                    if (pos >= last[k]) continue;
+                    evals++;
+                    const float dx = px[k] - a.x, dy = py[k] - a.y;
+                    const float e2 = exponent2(dx, dy, a.z, a.w, b.x);
+                    if (e2 > 0.f) continue;
+                    const float e = e2 + b.y;
+                    if (e < rp.lmin) continue;
+                    const float G = ex2_approx(e);
+                    const float alpha = fminf(rp.amax, G);
+                    const float om = 1.f - alpha;
+                    T[k] = T[k] / om;
+                    const float w = alpha * T[k];
+                    dr = fmaf(w, g0[k], dr);
+                    dg = fmaf(w, g1[k], dg);
+                    db = fmaf(w, g2[k], db);
+                    const float dalpha = T[k] * ((b.z - a0[k]) * g0[k] + (b.w - a1[k]) * g1[k] + (cb - a2[k]) * g2[k]) -
+                                         Tf[k] * bgd[k] / om;
+                    a0[k] = fmaf(alpha, b.z - a0[k], a0[k]);
+                    a1[k] = fmaf(alpha, b.w - a1[k], a1[k]);
+                    a2[k] = fmaf(alpha, cb - a2[k], a2[k]);
+                    any = true;
+                    if (G > rp.amax) continue;
+                    const float de = dalpha * alpha * kLn2;
+                    dF += de;
+                    dA = fmaf(de * dx, dx, dA);
+                    dB = fmaf(de * dx, dy, dB);
+                    dC = fmaf(de * dy, dy, dC);
+                    dmx -= de * (2.f * a.z * dx + a.w * dy);
+                    dmy -= de * (a.w * dx + 2.f * b.x * dy);
+                }
+                if (__any_sync(0xffffffffu, any)) {
+                    // record layout: (dmx, dmy, dA, dB), (dC, dF, dr, dg), (db, -, -, -)
+                    const float v8[8] = {dmx, dmy, dA, dB, dC, dF, dr, dg};
+                    const float tot = warp_sum8_transposed(v8, lane);
+                    db = warp_sum_f(db);
+                    float *rec = reinterpret_cast<float *>(grad2d + 3 * s_rec[j]);
+                    if ((lane & 3) == 0) atomicAdd(rec + (lane >> 2), tot);
+                    if (lane == 0) atomicAdd(rec + 8, db);
+                }
             }
         }
         __syncthreads();

@@ -90,8 +90,12 @@ def test_project_matches_oracle():
     conic = np.stack([splat[k, 2] / (-0.5 * log2e), splat[k, 3] / (-log2e), splat[k, 4] / (-0.5 * log2e)], 1)
     scale = np.abs(o["conic"][k]).max(1, keepdims=True)
     assert np.max(np.abs(conic - o["conic"][k]) / scale) < 1e-4
-    np.testing.assert_allclose(splat[k, 6], o["opacity"][k], rtol=1e-5)
-    np.testing.assert_allclose(splat[k, 7], o["depth"][k], rtol=1e-5)
+    # F = log2(opacity); (rx, ry) = the alpha >= alpha_min box half-widths, guarded
+    np.testing.assert_allclose(np.exp2(splat[k, 5]), o["opacity"][k], rtol=1e-5)
+    np.testing.assert_allclose(splat[k, 6], o["extent"][k, 0] * 1.0001 + 0.01, rtol=1e-4)
+    np.testing.assert_allclose(splat[k, 7], o["extent"][k, 1] * 1.0001 + 0.01, rtol=1e-4)
+    depth = plan.ws_view(capi.WS_DEPTH, torch.float32, n).cpu().numpy()
+    np.testing.assert_allclose(depth[k], o["depth"][k], rtol=1e-5)
     # rect: GPU contains the oracle's; equal unless an extent edge is near a tile boundary
     ext_ = o["extent"][k]
     m = o["mean"][k]
