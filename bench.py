@@ -366,6 +366,7 @@ def run_ours(args, world, rank, local):
                    "l2": "inputs larger than L2 (%.1f GB workspace per iteration)" % (plan.ws_bytes / 1e9)},
         "per_frame": {"value": per_frame, "unit": "iters/s", "speedup_batched": value / world / per_frame},
         "kernel_ms": kernel_ms,
+        "evaluations": {"fwd": int(st.eval_fwd), "bwd": int(st.eval_bwd)},
         "roofline": roof,
         "e2e": {"value": e2e, "unit": "iters/s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": launches_per_step * args.steps,

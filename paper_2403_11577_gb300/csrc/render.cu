@@ -37,11 +37,13 @@ namespace gs {
 
 namespace {
 
+// Threads per block: 64 for 8x8 tiles (a pixel each), 128 for 16x16 (two
+// vertically adjacent pixels each), 256 for 32x32 (four each).
 template <int TILE>
 struct Cfg {
     static constexpr int NPIX = TILE * TILE;
-    static constexpr int NT = NPIX < 256 ? NPIX : 256;
-    static constexpr int PPT = NPIX / NT;          // pixels per thread
+    static constexpr int PPT = TILE == 8 ? 1 : (TILE == 16 ? 2 : 4);  // pixels per thread
+    static constexpr int NT = NPIX / PPT;
     static constexpr int RPW = 32 * PPT / TILE;    // pixel rows per warp (full tile width)
 };
 
@@ -149,27 +151,35 @@ k_render_fwd(const gs_frame *__restrict__ frames, int F, const uint32_t *__restr
                     msk &= msk - 1;
                     const float4 a = s0[j], b = s1[j];
                     const float cb = s2[j];
+                    // every lane evaluates the exponent; one warp vote decides
+                    // whether any pixel composites this Gaussian, and the
+                    // compositing itself runs predicated (no divergence)
+                    float e[PPT];
+                    bool ct[PPT];
+                    bool anyc = false;
 #pragma unroll
                     for (int k = 0; k < PPT; k++) {
-                        if (done[k]) continue;
-                        evals++;
+                        evals += !done[k];
                         const float dx = px[k] - a.x, dy = py[k] - a.y;
                         const float e2 = exponent2(dx, dy, a.z, a.w, b.x);
-                        if (e2 > 0.f) continue;
-                        const float e = e2 + b.y;
-                        if (e < rp.lmin) continue;
-                        const float alpha = fminf(rp.amax, ex2_approx(e));
+                        e[k] = e2 + b.y;
+                        ct[k] = !done[k] && !(e2 > 0.f) && !(e[k] < rp.lmin);
+                        anyc |= ct[k];
+                    }
+                    if (!__any_sync(0xffffffffu, anyc)) continue;
+#pragma unroll
+                    for (int k = 0; k < PPT; k++) {
+                        const float alpha = fminf(rp.amax, ex2_approx(e[k]));
                         const float nT = T[k] * (1.f - alpha);
-                        if (nT < rp.tmin) {
-                            done[k] = true;
-                            continue;
-                        }
-                        const float w = alpha * T[k];
+                        const bool stop = ct[k] && nT < rp.tmin;
+                        const bool blend = ct[k] && !stop;
+                        done[k] = done[k] || stop;
+                        const float w = blend ? alpha * T[k] : 0.f;
                         c0[k] = fmaf(b.z, w, c0[k]);
                         c1[k] = fmaf(b.w, w, c1[k]);
                         c2[k] = fmaf(cb, w, c2[k]);
-                        T[k] = nT;
-                        last[k] = b0 + j + 1;
+                        T[k] = blend ? nT : T[k];
+                        last[k] = blend ? b0 + j + 1 : last[k];
                     }
                 }
             }
@@ -323,33 +333,42 @@ k_render_bwd(const gs_frame *__restrict__ frames, int F, const uint32_t *__restr
                 const int pos = b0 + j;
                 const float4 a = s0[j], b = s1[j];
                 const float cb = s2[j];
-                float dmx = 0.f, dmy = 0.f, dA = 0.f, dB = 0.f, dC = 0.f, dF = 0.f, dr = 0.f, dg = 0.f, db = 0.f;
-                bool any = false;
+                // every lane evaluates the exponent; one warp vote decides
+                // whether any pixel composited this Gaussian; the gradient
+                // math then runs predicated (zero where a pixel did not)
+                float e[PPT], dxs[PPT], dys[PPT];
+                bool ct[PPT];
+                bool anyc = false;
 #pragma unroll
                 for (int k = 0; k < PPT; k++) {
-                    if (pos >= last[k]) continue;
-                    evals++;
-                    const float dx = px[k] - a.x, dy = py[k] - a.y;
-                    const float e2 = exponent2(dx, dy, a.z, a.w, b.x);
-                    if (e2 > 0.f) continue;
-                    const float e = e2 + b.y;
-                    if (e < rp.lmin) continue;
-                    const float G = ex2_approx(e);
-                    const float alpha = fminf(rp.amax, G);
-                    const float om = 1.f - alpha;
-                    T[k] = T[k] / om;
+                    const bool act = pos < last[k];
+                    evals += act;
+                    dxs[k] = px[k] - a.x;
+                    dys[k] = py[k] - a.y;
+                    const float e2 = exponent2(dxs[k], dys[k], a.z, a.w, b.x);
+                    e[k] = e2 + b.y;
+                    ct[k] = act && !(e2 > 0.f) && !(e[k] < rp.lmin);
+                    anyc |= ct[k];
+                }
+                if (!__any_sync(0xffffffffu, anyc)) continue;
+                float dmx = 0.f, dmy = 0.f, dA = 0.f, dB = 0.f, dC = 0.f, dF = 0.f, dr = 0.f, dg = 0.f, db = 0.f;
+#pragma unroll
+                for (int k = 0; k < PPT; k++) {
+                    const float G = ex2_approx(e[k]);
+                    const float alpha = ct[k] ? fminf(rp.amax, G) : 0.f;
+                    const float inv = rcp_approx(1.f - alpha);
+                    T[k] = ct[k] ? T[k] * inv : T[k];  // T before this Gaussian
                     const float w = alpha * T[k];
                     dr = fmaf(w, g0[k], dr);
                     dg = fmaf(w, g1[k], dg);
                     db = fmaf(w, g2[k], db);
                     const float dalpha = T[k] * ((b.z - a0[k]) * g0[k] + (b.w - a1[k]) * g1[k] + (cb - a2[k]) * g2[k]) -
-                                         Tf[k] * bgd[k] / om;
+                                         Tf[k] * bgd[k] * inv;
                     a0[k] = fmaf(alpha, b.z - a0[k], a0[k]);
                     a1[k] = fmaf(alpha, b.w - a1[k], a1[k]);
                     a2[k] = fmaf(alpha, cb - a2[k], a2[k]);
-                    any = true;
-                    if (G > rp.amax) continue;
-                    const float de = dalpha * alpha * kLn2;
+                    const float de = (ct[k] && !(G > rp.amax)) ? dalpha * alpha * kLn2 : 0.f;
+                    const float dx = dxs[k], dy = dys[k];
                     dF += de;
                     dA = fmaf(de * dx, dx, dA);
                     dB = fmaf(de * dx, dy, dB);
@@ -357,7 +376,7 @@ k_render_bwd(const gs_frame *__restrict__ frames, int F, const uint32_t *__restr
                     dmx -= de * (2.f * a.z * dx + a.w * dy);
                     dmy -= de * (a.w * dx + 2.f * b.x * dy);
                 }
-                if (__any_sync(0xffffffffu, any)) {
+                {
                     // record layout: (dmx, dmy, dA, dB), (dC, dF, dr, dg), (db, -, -, -)
                     const float v8[8] = {dmx, dmy, dA, dB, dC, dF, dr, dg};
                     const float tot = warp_sum8_transposed(v8, lane);
