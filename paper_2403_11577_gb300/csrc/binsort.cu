@@ -1,24 +1,28 @@
 // Tile binning and depth ordering for Phi (Eq. 5).
 //
-// 1. k_pair_count: tiles per record, summed per block of kEmitItems records.
-// 2. k_pair_scan:  exclusive scan of the block sums; total pairs P; if P
-//    exceeds the capacity the overflow bit is set and P is taken as 0.
-// 3. k_pair_emit:  each block re-derives its records' counts, scans them in
-//    shared memory and writes its pairs cooperatively (every thread strides
-//    over the block's output range and finds its record by binary search),
-//    key = (global tile << 32) | float bits of the depth, value = Gaussian
-//    index within its scene.  Records are emitted in order, so for equal
-//    keys the emission order is ascending value.
-// 4. LSD radix sort, 8-bit digits over the key bits that can be non-zero,
-//    each pass: k_radix_hist (per-block digit counts) -> k_radix_colscan
-//    (per-digit prefix over blocks, digit totals) -> k_radix_scatter
-//    (stable: per-warp ranking with match_any in index order, per-tile
-//    prefix over warps, staging in shared memory by digit, then coalesced
-//    writes).  Each block owns one contiguous chunk of the input, so the
-//    order of equal digits is preserved across blocks.
-// 5. k_tile_ranges: [start, end) of every tile in the sorted pairs;
-//    k_tile_order: the tiles sorted heavy-first for the render kernels.
-// No kernel waits on another block; there are no spin loops.
+// The pairs must end up ordered by (global tile, depth, Gaussian index):
+// key = (global tile << 32) | float bits of the depth, value = Gaussian index
+// within its scene, stable in record order.  gs_bin_sort gets there in two
+// cheap stages instead of one wide sort:
+// 1. k_rec_keys + 4 LSD passes over the per-(frame, Gaussian) records keyed
+//    by their 32-bit depth (culled records last): a stable depth order of the
+//    records (ties keep record order).
+// 2. k_pair_count / k_pair_scan / k_pair_emit over the records in that
+//    order: every record emits one pair per tile of its rectangle (emission
+//    is cooperative: threads stride over the block's output range and find
+//    their record by binary search).  The pairs are thus already in
+//    (depth, record) order.
+// 3. LSD passes over the tile bits only (2 for up to 65,536 tiles): a stable
+//    sort by tile keeps the depth order inside each tile, so the result is
+//    the full-key order bit for bit, with about a third of the traffic.
+// 4. k_tile_ranges: [start, end) of every tile; k_tile_order: the tiles
+//    sorted heavy-first for the render kernels.
+// Each radix pass: k_radix_hist (per-block digit counts) -> k_radix_colscan
+// (per-digit prefix over blocks, digit totals) -> k_radix_scatter (stable:
+// per-warp ranking with match_any in index order, per-tile prefix over
+// warps, staging in shared memory by digit, coalesced writes); each block
+// owns one contiguous chunk of the input.  No kernel waits on another
+// block; there are no spin loops.
 #include <algorithm>
 
 #include "common.cuh"
@@ -44,14 +48,29 @@ __device__ __forceinline__ unsigned long long block_sum_u64(unsigned long long v
     return t;  // valid in thread 0
 }
 
+// Depth keys of the records for the first stage: float bits of the depth
+// (ordered like the depths, which are positive), culled records last; the
+// value is the record index.  Also stores the record count for the sort.
+__global__ void k_rec_keys(const uint2 *__restrict__ rect, const float *__restrict__ depth, long long R,
+                           unsigned long long *__restrict__ keys, uint32_t *__restrict__ vals,
+                           Stats *__restrict__ stats) {
+    const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r == 0) stats->num_records = (unsigned long long)R;
+    if (r >= R) return;
+    keys[r] = rect_count(rect[r]) ? (unsigned long long)__float_as_uint(depth[r]) : 0xffffffffull;
+    vals[r] = (uint32_t)r;
+}
+
+// perm (optional): the order in which records are visited; NULL = record order.
 __global__ void __launch_bounds__(kEmitThreads)
-k_pair_count(const uint2 *__restrict__ rect, long long R, unsigned long long *__restrict__ sums) {
+k_pair_count(const uint2 *__restrict__ rect, long long R, const uint32_t *__restrict__ perm,
+             unsigned long long *__restrict__ sums) {
     __shared__ unsigned long long sh[kEmitThreads / 32];
     const long long base = (long long)blockIdx.x * kEmitItems;
     unsigned long long c = 0;
     for (int i = threadIdx.x; i < kEmitItems; i += kEmitThreads) {
-        long long r = base + i;
-        if (r < R) c += rect_count(rect[r]);
+        long long p = base + i;
+        if (p < R) c += rect_count(rect[perm ? (long long)perm[p] : p]);
     }
     unsigned long long t = block_sum_u64<kEmitThreads>(c, sh);
     if (threadIdx.x == 0) sums[blockIdx.x] = t;
@@ -100,8 +119,9 @@ k_pair_scan(unsigned long long *__restrict__ sums, int nb, long long capacity, S
 
 __global__ void __launch_bounds__(kEmitThreads)
 k_pair_emit(const gs_frame *__restrict__ frames, int F, const uint2 *__restrict__ rect,
-            const float *__restrict__ depth, long long R, const unsigned long long *__restrict__ sums,
-            const Stats *__restrict__ stats, unsigned long long *__restrict__ keys, uint32_t *__restrict__ vals) {
+            const float *__restrict__ depth, long long R, const uint32_t *__restrict__ perm,
+            const unsigned long long *__restrict__ sums, const Stats *__restrict__ stats,
+            unsigned long long *__restrict__ keys, uint32_t *__restrict__ vals) {
     __shared__ unsigned long long off[kEmitItems + 1];
     __shared__ uint32_t s_tile0[kEmitItems];   // global tile of the rect's first tile
     __shared__ uint32_t s_w[kEmitItems];       // rect width in tiles
@@ -117,9 +137,10 @@ k_pair_emit(const gs_frame *__restrict__ frames, int F, const uint2 *__restrict_
     unsigned long long mine = 0;
     for (int j = 0; j < PER; j++) {
         const int i = threadIdx.x * PER + j;
-        const long long r = base + i;
+        const long long p = base + i;
         c[j] = 0;
-        if (r < R) {
+        if (p < R) {
+            const long long r = perm ? (long long)perm[p] : p;
             uint2 rc = rect[r];
             c[j] = rect_count(rc);
             if (c[j]) {
@@ -183,13 +204,13 @@ __device__ __forceinline__ Chunk sort_chunk(unsigned long long P, int nb, int b)
 }
 
 __global__ void __launch_bounds__(kSortThreads)
-k_radix_hist(const unsigned long long *__restrict__ keys, const Stats *__restrict__ stats, int shift,
+k_radix_hist(const unsigned long long *__restrict__ keys, const unsigned long long *__restrict__ count, int shift,
              int nb, uint32_t *__restrict__ hist) {
     __shared__ uint32_t h[kSortThreads / 32][kRadix];
     const int warp = threadIdx.x >> 5;
     for (int i = threadIdx.x; i < (kSortThreads / 32) * kRadix; i += kSortThreads) (&h[0][0])[i] = 0;
     __syncthreads();
-    const Chunk c = sort_chunk(stats->num_pairs, nb, blockIdx.x);
+    const Chunk c = sort_chunk(*count, nb, blockIdx.x);
     for (long long i = c.lo + threadIdx.x; i < c.hi; i += kSortThreads)
         atomicAdd(&h[warp][(uint32_t)(keys[i] >> shift) & (kRadix - 1)], 1u);
     __syncthreads();
@@ -237,15 +258,15 @@ struct ScatterSmem {
     uint32_t wtot[kRadix / 32];
 };
 
-__global__ void __launch_bounds__(kSortThreads)
+__global__ void __launch_bounds__(kSortThreads, 2)
 k_radix_scatter(const unsigned long long *__restrict__ kin, const uint32_t *__restrict__ vin,
                 unsigned long long *__restrict__ kout, uint32_t *__restrict__ vout,
-                const Stats *__restrict__ stats, int shift, int nb, const uint32_t *__restrict__ hist,
+                const unsigned long long *__restrict__ count, int shift, int nb, const uint32_t *__restrict__ hist,
                 const uint32_t *__restrict__ totals) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     ScatterSmem &S = *reinterpret_cast<ScatterSmem *>(smem_raw);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const Chunk c = sort_chunk(stats->num_pairs, nb, blockIdx.x);
+    const Chunk c = sort_chunk(*count, nb, blockIdx.x);
     // run[d] = (items of digits < d) + (items of digit d in earlier blocks)
     if (threadIdx.x < kRadix) {
         const uint32_t x = totals[threadIdx.x];
@@ -342,9 +363,9 @@ k_radix_scatter(const unsigned long long *__restrict__ kin, const uint32_t *__re
     }
 }
 
-__global__ void k_tile_ranges(const unsigned long long *__restrict__ keys, const Stats *__restrict__ stats,
+__global__ void k_tile_ranges(const unsigned long long *__restrict__ keys, const unsigned long long *__restrict__ count,
                               uint2 *__restrict__ ranges) {
-    const long long P = (long long)stats->num_pairs;
+    const long long P = (long long)*count;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < P;
          i += (long long)gridDim.x * blockDim.x) {
         const uint32_t t = (uint32_t)(keys[i] >> 32);
@@ -397,13 +418,37 @@ k_tile_order(const uint2 *__restrict__ ranges, int T, uint32_t *__restrict__ ord
 
 }  // namespace
 
+// Radix passes over the tile bits of the pair keys (the depth order comes
+// from the record sort).
 int radix_passes(int num_tiles) {
     int tb = 0;
     while ((1ll << tb) < (long long)num_tiles) tb++;
-    return (32 + tb + kRadixBits - 1) / kRadixBits;
+    return (tb + kRadixBits - 1) / kRadixBits;
 }
 
-size_t scatter_smem_bytes() { return sizeof(ScatterSmem); }
+// Passes of a sort over the full 64-bit pair key (tile and depth bits).
+int full_key_passes(int num_tiles) { return radix_passes(num_tiles) + 32 / kRadixBits; }
+
+
+namespace {
+
+// One LSD pass (histogram, column scan, scatter) over *count items.
+cudaError_t radix_pass(const unsigned long long *kin, const uint32_t *vin, unsigned long long *kout, uint32_t *vout,
+                       const unsigned long long *count, int shift, int nb, uint32_t *hist, cudaStream_t s) {
+    uint32_t *totals = hist + (size_t)kRadix * nb;
+    k_radix_hist<<<nb, kSortThreads, 0, s>>>(kin, count, shift, nb, hist);
+    k_radix_colscan<<<kRadix, kColThreads, 0, s>>>(hist, nb, totals);
+    k_radix_scatter<<<nb, kSortThreads, sizeof(ScatterSmem), s>>>(kin, vin, kout, vout, count, shift, nb, hist,
+                                                                  totals);
+    return cudaGetLastError();
+}
+
+cudaError_t scatter_smem_attr() {
+    return cudaFuncSetAttribute(k_radix_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)sizeof(ScatterSmem));
+}
+
+}  // namespace
 
 cudaError_t launch_bin_sort(const gs_batch *b, const Layout &L, unsigned char *ws, cudaStream_t s, int sms) {
     (void)sms;
@@ -414,39 +459,41 @@ cudaError_t launch_bin_sort(const gs_batch *b, const Layout &L, unsigned char *w
     unsigned long long *keys[2] = {reinterpret_cast<unsigned long long *>(ws + L.keys[0]),
                                    reinterpret_cast<unsigned long long *>(ws + L.keys[1])};
     uint32_t *vals[2] = {reinterpret_cast<uint32_t *>(ws + L.vals[0]), reinterpret_cast<uint32_t *>(ws + L.vals[1])};
+    unsigned long long *rkeys[2] = {reinterpret_cast<unsigned long long *>(ws + L.rec_keys[0]),
+                                    reinterpret_cast<unsigned long long *>(ws + L.rec_keys[1])};
+    uint32_t *rvals[2] = {reinterpret_cast<uint32_t *>(ws + L.rec_vals[0]),
+                          reinterpret_cast<uint32_t *>(ws + L.rec_vals[1])};
     uint32_t *hist = reinterpret_cast<uint32_t *>(ws + L.sort_hist);
-    uint32_t *totals = hist + (size_t)kRadix * L.sort_blocks;
     uint2 *ranges = reinterpret_cast<uint2 *>(ws + L.ranges);
-    cudaError_t e;
+    const long long R = b->num_records;
+    cudaError_t e = scatter_smem_attr();
+    if (e != cudaSuccess) return e;
     if (L.emit_blocks > 0) {
-        k_pair_count<<<L.emit_blocks, kEmitThreads, 0, s>>>(rect, b->num_records, sums);
-        k_pair_scan<<<1, 1024, 0, s>>>(sums, L.emit_blocks, b->pair_capacity, stats);
-        k_pair_emit<<<L.emit_blocks, kEmitThreads, 0, s>>>(b->frames_dev, b->num_frames, rect, depth,
-                                                           b->num_records, sums, stats, keys[L.first_buffer],
-                                                           vals[L.first_buffer]);
-    } else {
-        if ((e = cudaMemsetAsync(&stats->num_pairs, 0, sizeof(unsigned long long), s)) != cudaSuccess) return e;
-    }
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    static bool attr_set = false;
-    if (!attr_set) {
-        e = cudaFuncSetAttribute(k_radix_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)sizeof(ScatterSmem));
+        // stage 1: stable depth order of the records (4 passes, ends in buffer 0)
+        k_rec_keys<<<(int)((R + 255) / 256), 256, 0, s>>>(rect, depth, R, rkeys[0], rvals[0], stats);
+        for (int p = 0; p < 4 && e == cudaSuccess; p++)
+            e = radix_pass(rkeys[p & 1], rvals[p & 1], rkeys[(p + 1) & 1], rvals[(p + 1) & 1], &stats->num_records,
+                           8 * p, L.rec_sort_blocks, hist, s);
         if (e != cudaSuccess) return e;
-        attr_set = true;
+        // stage 2: pairs emitted in that order
+        k_pair_count<<<L.emit_blocks, kEmitThreads, 0, s>>>(rect, R, rvals[0], sums);
+        k_pair_scan<<<1, 1024, 0, s>>>(sums, L.emit_blocks, b->pair_capacity, stats);
+        k_pair_emit<<<L.emit_blocks, kEmitThreads, 0, s>>>(b->frames_dev, b->num_frames, rect, depth, R, rvals[0],
+                                                           sums, stats, keys[L.first_buffer], vals[L.first_buffer]);
+    } else {
+        e = cudaMemsetAsync(&stats->num_pairs, 0, sizeof(unsigned long long), s);
     }
+    if (e == cudaSuccess) e = cudaGetLastError();
+    // stage 3: stable passes over the tile bits only (end in buffer 0)
     int cur = L.first_buffer;
-    for (int p = 0; p < L.passes; p++) {
-        const int shift = p * kRadixBits;
-        k_radix_hist<<<L.sort_blocks, kSortThreads, 0, s>>>(keys[cur], stats, shift, L.sort_blocks, hist);
-        k_radix_colscan<<<kRadix, kColThreads, 0, s>>>(hist, L.sort_blocks, totals);
-        k_radix_scatter<<<L.sort_blocks, kSortThreads, sizeof(ScatterSmem), s>>>(
-            keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], stats, shift, L.sort_blocks, hist, totals);
+    for (int p = 0; p < L.passes && e == cudaSuccess; p++) {
+        e = radix_pass(keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], &stats->num_pairs, 32 + 8 * p,
+                       L.sort_blocks, hist, s);
         cur ^= 1;
     }
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (e != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(ranges, 0, sizeof(uint2) * (size_t)b->num_tiles, s)) != cudaSuccess) return e;
-    k_tile_ranges<<<1216, 256, 0, s>>>(keys[0], stats, ranges);
+    k_tile_ranges<<<1216, 256, 0, s>>>(keys[0], &stats->num_pairs, ranges);
     k_tile_order<<<1, 1024, 0, s>>>(ranges, b->num_tiles, reinterpret_cast<uint32_t *>(ws + L.order));
     return cudaGetLastError();
 }
@@ -472,8 +519,7 @@ struct NoAllocScratch {
     unsigned long long alt_keys[kNoAllocMaxPairs];
     uint32_t alt_vals[kNoAllocMaxPairs];
     unsigned long long emit_sums[kNoAllocMaxRecords / kEmitItems];
-    uint32_t hist[kRadix * kNoAllocSortBlocks];
-    uint32_t totals[kRadix];
+    uint32_t hist[kRadix * (kNoAllocSortBlocks + 1)];  // counts, then digit totals
 };
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[sizeof(NoAllocScratch)];
@@ -523,34 +569,28 @@ extern "C" gs_status gs_bin_sort_noalloc(const gs_batch *b, const gs_opts *o, co
     const int emit_blocks = (int)((b->num_records + kEmitItems - 1) / kEmitItems);
     const long long st = (b->pair_capacity + kSortTile - 1) / kSortTile;
     const int sort_blocks = (int)std::max(1ll, std::min(st, (long long)kNoAllocSortBlocks));
-    const int passes = radix_passes(b->num_tiles);
+    const int passes = full_key_passes(b->num_tiles);
     const uint2 *r2 = reinterpret_cast<const uint2 *>(rect);
     unsigned long long *kb[2] = {reinterpret_cast<unsigned long long *>(keys), sc->alt_keys};
     uint32_t *vb[2] = {vals, sc->alt_vals};
     int cur = passes & 1;  // the last pass ends in the caller's buffers
     cudaError_t e = cudaMemsetAsync(&sc->stats, 0, sizeof(Stats), s);  // counters start at zero
     if (e == cudaSuccess && emit_blocks > 0) {
-        k_pair_count<<<emit_blocks, kEmitThreads, 0, s>>>(r2, b->num_records, sc->emit_sums);
+        k_pair_count<<<emit_blocks, kEmitThreads, 0, s>>>(r2, b->num_records, nullptr, sc->emit_sums);
         k_pair_scan<<<1, 1024, 0, s>>>(sc->emit_sums, emit_blocks, b->pair_capacity, &sc->stats);
         k_pair_emit<<<emit_blocks, kEmitThreads, 0, s>>>(b->frames_dev, b->num_frames, r2, depth, b->num_records,
-                                                         sc->emit_sums, &sc->stats, kb[cur], vb[cur]);
+                                                         nullptr, sc->emit_sums, &sc->stats, kb[cur], vb[cur]);
         e = cudaGetLastError();
     }
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_radix_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)sizeof(ScatterSmem));
+    if (e == cudaSuccess) e = scatter_smem_attr();
     for (int p = 0; e == cudaSuccess && p < passes; p++) {
-        const int shift = p * kRadixBits;
-        k_radix_hist<<<sort_blocks, kSortThreads, 0, s>>>(kb[cur], &sc->stats, shift, sort_blocks, sc->hist);
-        k_radix_colscan<<<kRadix, kColThreads, 0, s>>>(sc->hist, sort_blocks, sc->totals);
-        k_radix_scatter<<<sort_blocks, kSortThreads, sizeof(ScatterSmem), s>>>(
-            kb[cur], vb[cur], kb[cur ^ 1], vb[cur ^ 1], &sc->stats, shift, sort_blocks, sc->hist, sc->totals);
+        e = radix_pass(kb[cur], vb[cur], kb[cur ^ 1], vb[cur ^ 1], &sc->stats.num_pairs, p * kRadixBits,
+                       sort_blocks, sc->hist, s);
         cur ^= 1;
-        e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaMemsetAsync(ranges, 0, sizeof(uint32_t) * 2 * (size_t)b->num_tiles, s);
     if (e == cudaSuccess) {
-        k_tile_ranges<<<1216, 256, 0, s>>>(kb[0], &sc->stats, reinterpret_cast<uint2 *>(ranges));
+        k_tile_ranges<<<1216, 256, 0, s>>>(kb[0], &sc->stats.num_pairs, reinterpret_cast<uint2 *>(ranges));
         k_noalloc_counts<<<1, 1, 0, s>>>(&sc->stats, reinterpret_cast<unsigned long long *>(out_pairs));
         e = cudaGetLastError();
     }

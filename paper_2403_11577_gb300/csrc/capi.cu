@@ -37,6 +37,8 @@ bool make_layout(const gs_batch *b, Layout *L) {
     L->emit_blocks = (int)((R + kEmitItems - 1) / kEmitItems);
     long long st = ((long long)cap + kSortTile - 1) / kSortTile;
     L->sort_blocks = (int)std::max(1ll, std::min(st, (long long)kSortBlocksMax));
+    long long rt = ((long long)R + kSortTile - 1) / kSortTile;
+    L->rec_sort_blocks = (int)std::max(1ll, std::min(rt, (long long)kSortBlocksMax));
     L->twist_blocks = std::max(1, project_bwd_blocks(b));
     L->passes = radix_passes(b->num_tiles);
     L->first_buffer = L->passes & 1;
@@ -53,10 +55,14 @@ bool make_layout(const gs_batch *b, Layout *L) {
     L->vals[0] = take(cap * 4);
     L->keys[1] = take(cap * 8);
     L->vals[1] = take(cap * 4);
+    L->rec_keys[0] = take(R * 8);
+    L->rec_vals[0] = take(R * 4);
+    L->rec_keys[1] = take(R * 8);
+    L->rec_vals[1] = take(R * 4);
     L->ranges = take(T * 8);
     L->order = take(T * 4);
     L->emit_sums = take((size_t)std::max(1, L->emit_blocks) * 8);
-    L->sort_hist = take((size_t)kRadix * (L->sort_blocks + 1) * 4);  // counts + digit totals
+    L->sort_hist = take((size_t)kRadix * (std::max(L->sort_blocks, L->rec_sort_blocks) + 1) * 4);  // counts + totals
     L->twist_part = take(F * (size_t)L->twist_blocks * 6 * 8);
     L->twist_frame = take(F * 6 * 8);
     L->loss_part = take((size_t)kLossBlocks * 8);

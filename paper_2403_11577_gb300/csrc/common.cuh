@@ -31,22 +31,25 @@ struct Stats {
     unsigned long long eval_fwd;
     unsigned long long eval_bwd;
     unsigned long long raw_pairs;   // pairs requested before the capacity check
-    unsigned long long pad[3];
+    unsigned long long num_records; // records of the batch (count of the record sort)
+    unsigned long long pad[2];
 };
 
 struct Layout {
-    size_t stats, pose32, pose64, rect, depth, splat, grad2d, keys[2], vals[2], ranges,
+    size_t stats, pose32, pose64, rect, depth, splat, grad2d, keys[2], vals[2], rec_keys[2], rec_vals[2], ranges,
         order, emit_sums, sort_hist, twist_part, twist_frame, loss_part, total;
     int emit_blocks;     // blocks of the pair count / emit kernels
-    int sort_blocks;     // blocks of the radix sort kernels
+    int sort_blocks;     // blocks of the radix passes over pairs
+    int rec_sort_blocks; // blocks of the radix passes over records
     int twist_blocks;    // blocks of the projection backward
-    int passes;          // radix passes
+    int passes;          // radix passes over the tile bits of the pairs
     int first_buffer;    // buffer the emission writes (the last pass ends in 0)
 };
 
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 int radix_passes(int num_tiles);
+int full_key_passes(int num_tiles);
 bool make_layout(const gs_batch *b, Layout *L);
 
 // ------------------------------------------------------------ device side
