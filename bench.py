@@ -354,8 +354,12 @@ def run_ours(args, world, rank, local):
     e2e_t = max_over_ranks(max(e0.elapsed_time(e1) / 1e3, e2e_wall), world)
     e2e = world * args.steps / e2e_t
 
-    passes = int(math.ceil((32 + max(1, math.ceil(math.log2(max(plan.batch.num_tiles, 2))))) / 8))
-    launches_per_step = 1 + 1 + (3 + 3 * passes + 1) + 1 + 2 + 2 + 1
+    # kernels per iteration: pose 1, project 1, bin_sort (record keys 1, 4 record
+    # passes x 3, count/scan/emit 3, tile passes x 3, ranges 1, order 1),
+    # render fwd 1, L1 2, render bwd 1, projection bwd 1, pose grad 2
+    tile_bits = max(0, math.ceil(math.log2(max(plan.batch.num_tiles, 1))))
+    tile_passes = (tile_bits + 7) // 8
+    launches_per_step = 1 + 1 + (1 + 12 + 3 + 3 * tile_passes + 2) + 1 + 2 + 1 + 1 + 2
     out = {
         "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max * 1e3 / args.steps, "higher_is_better": True,
