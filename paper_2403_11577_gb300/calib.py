@@ -46,10 +46,12 @@ def errors(ext, delta, ext_true, delta_true):
 
 
 def run_calibration(problem, iters=3000, warmup=500, lr_rot=1e-4, lr_trans=5e-3, lr_delta=1e-3,
-                    lambda_scale=1e-3, opts=None, seed=0, log_every=250, reinit=True, device="cuda"):
+                    lambda_scale=1e-3, opts=None, seed=0, log_every=250, reinit=True, train_scene=True,
+                    scene_lr_scale=1.0, device="cuda"):
     """Calibrate camera 0 of `problem` (its ext/delta are the start,
-    ext_target/delta_target the truth).  Returns a dict with the error
-    history, the final errors and the wall time."""
+    ext_target/delta_target the truth).  train_scene=False keeps the
+    Gaussian attributes fixed (calibration only).  Returns a dict with the
+    error history, the final errors and the wall time."""
     build.build()
     dev = torch.device(device)
     gen = torch.Generator(device="cpu").manual_seed(seed)
@@ -80,7 +82,8 @@ def run_calibration(problem, iters=3000, warmup=500, lr_rot=1e-4, lr_trans=5e-3,
     delta_p = delta.clone()
     delta_p.grad = torch.zeros_like(delta_p)
     log_s = scene.log_scale
-    opt_scene = torch.optim.Adam([{"params": [params[k]], "lr": GAUSS_LR[k]} for k in GAUSS_LR], eps=1e-15)
+    opt_scene = torch.optim.Adam([{"params": [params[k]], "lr": GAUSS_LR[k] * scene_lr_scale} for k in GAUSS_LR],
+                                 eps=1e-15)
     opt_cal = torch.optim.Adam([{"params": [rot], "lr": lr_rot}, {"params": [trans], "lr": lr_trans},
                                 {"params": [delta_p], "lr": lr_delta}], eps=1e-15)
     base_lrs = [g["lr"] for g in opt_cal.param_groups]
@@ -94,17 +97,18 @@ def run_calibration(problem, iters=3000, warmup=500, lr_rot=1e-4, lr_trans=5e-3,
         ext[:, 3:].copy_(trans)
         delta.copy_(delta_p)
         loss = step()
-        for k in GAUSS_LR:
-            params[k].grad.copy_(step.grads[k])
-        # L_scale on the activated scales (Eq. 7)
-        if lambda_scale > 0:
-            with torch.enable_grad():
-                ls = log_s.detach().requires_grad_(True)
-                s = torch.exp(ls)
-                reg = lambda_scale * (s - s.mean(dim=1, keepdim=True)).abs().sum()
-                (g_ls,) = torch.autograd.grad(reg, ls)
-            params["log_scale"].grad.add_(g_ls)
-        opt_scene.step()
+        if train_scene:
+            for k in GAUSS_LR:
+                params[k].grad.copy_(step.grads[k])
+            # L_scale on the activated scales (Eq. 7)
+            if lambda_scale > 0:
+                with torch.enable_grad():
+                    ls = log_s.detach().requires_grad_(True)
+                    s = torch.exp(ls)
+                    reg = lambda_scale * (s - s.mean(dim=1, keepdim=True)).abs().sum()
+                    (g_ls,) = torch.autograd.grad(reg, ls)
+                params["log_scale"].grad.add_(g_ls)
+            opt_scene.step()
         if it >= warmup:
             frac = (it - warmup) / max(1, iters - warmup)
             for g, lr0 in zip(opt_cal.param_groups, base_lrs):
@@ -114,7 +118,7 @@ def run_calibration(problem, iters=3000, warmup=500, lr_rot=1e-4, lr_trans=5e-3,
             delta_p.grad.copy_(step.grads["delta"])
             opt_cal.step()
         # keep quaternions away from zero norm
-        if it % 100 == 99:
+        if train_scene and it % 100 == 99:
             with torch.no_grad():
                 q = params["quat"]
                 q.div_(q.norm(dim=1, keepdim=True).clamp_min(1e-8))
