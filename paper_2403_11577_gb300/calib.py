@@ -142,10 +142,17 @@ def main():
     ap.add_argument("--warmup", type=int, default=500)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--gaussians", type=int, default=1_000_000)
-    ap.add_argument("--no-reinit", action="store_true")
+    ap.add_argument("--trajectory", choices=["straight", "zigzag"], default="zigzag")
+    ap.add_argument("--mode", choices=["joint", "pose"], default="joint",
+                    help="joint: re-initialised scene trained with the calibration; "
+                         "pose: the scene's attributes fixed at their true values")
     a = ap.parse_args()
-    p = scenes.calibration_problem(seed=a.seed, n=a.gaussians)
-    res = run_calibration(p, iters=a.iters, warmup=a.warmup, seed=a.seed, reinit=not a.no_reinit)
+    p = scenes.calibration_problem(seed=a.seed, n=a.gaussians, trajectory=a.trajectory)
+    if a.mode == "pose":
+        res = run_calibration(p, iters=a.iters, warmup=0, seed=a.seed, reinit=False, train_scene=False)
+    else:
+        res = run_calibration(p, iters=a.iters, warmup=a.warmup, seed=a.seed, reinit=True)
+    res.update(trajectory=a.trajectory, mode=a.mode, seed=a.seed, gaussians=a.gaussians)
     print(json.dumps(res))
 
 

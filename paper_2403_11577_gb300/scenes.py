@@ -301,20 +301,42 @@ def lidar_frame_problem(seed: int = 1, n: int = 200_000) -> Problem:
                    tile=16, meta={"hit_ids": ids})
 
 
-def _drive_scene(rng, n, sweeps=50, speed=10.0, rate=10.0, smooth=True):
+def _yaw_rotate(dirs, yaw):
+    c, s = math.cos(yaw), math.sin(yaw)
+    out = dirs.copy()
+    out[..., 0] = c * dirs[..., 0] - s * dirs[..., 1]
+    out[..., 1] = s * dirs[..., 0] + c * dirs[..., 1]
+    return out
+
+
+def _drive_scene(rng, n, sweeps=50, speed=10.0, rate=10.0, smooth=True, trajectory="straight"):
+    """Points from LiDAR sweeps along a drive.  'straight': 10 m/s along x
+    with a constant heading.  'zigzag': the same forward speed with a lateral
+    swing y = 3 sin(2 pi t / 2.5) m and the heading following the path (so
+    velocity and orientation change over time)."""
     world = _make_world(rng, 60, (-30.0, 120.0))
     traj_t = np.arange(sweeps) / rate
-    traj_p = np.stack([speed * traj_t, np.zeros(sweeps), np.full(sweeps, LIDAR_HEIGHT)], axis=1)
+    if trajectory == "straight":
+        y = np.zeros(sweeps)
+        yaw = np.zeros(sweeps)
+    elif trajectory == "zigzag":
+        w = 2.0 * math.pi / 2.5
+        y = 3.0 * np.sin(w * traj_t)
+        yaw = np.arctan2(3.0 * w * np.cos(w * traj_t), speed)
+    else:
+        raise ValueError(trajectory)
+    traj_p = np.stack([speed * traj_t, y, np.full(sweeps, LIDAR_HEIGHT)], axis=1)
+    traj_q = np.stack([np.cos(yaw / 2), np.zeros(sweeps), np.zeros(sweeps), np.sin(yaw / 2)], axis=1)
     pts, ids = [], []
     for k in range(sweeps):
-        p, i = _cast(world, traj_p[k], _beam_dirs(rng, k > 0))
+        p, i = _cast(world, traj_p[k], _yaw_rotate(_beam_dirs(rng, k > 0), yaw[k]))
         pts.append(p)
         ids.append(i)
     pts = np.concatenate(pts)
     ids = np.concatenate(ids)
     while len(pts) < n:  # extra jittered sweeps if the quota is not reached
         k = int(rng.integers(sweeps))
-        p, i = _cast(world, traj_p[k], _beam_dirs(rng, True))
+        p, i = _cast(world, traj_p[k], _yaw_rotate(_beam_dirs(rng, True), yaw[k]))
         pts = np.concatenate([pts, p])
         ids = np.concatenate([ids, i])
     sel = rng.choice(len(pts), size=n, replace=False)
@@ -326,14 +348,15 @@ def _drive_scene(rng, n, sweeps=50, speed=10.0, rate=10.0, smooth=True):
     else:
         rgb = rng.uniform(0, 1, size=(n, 3))
     return Scene(pts.astype(np.float32), q, log_s, logit_o, rgb.astype(np.float32),
-                 traj_t, traj_p, _identity_quats(sweeps))
+                 traj_t, traj_p, traj_q)
 
 
-def batched_problem(seed: int = 2, n: int = 1_000_000, frames: int = 8) -> Problem:
-    """1M Gaussians from 50 sweeps along a straight 10 m/s drive sampled at
-    10 Hz; eight 1408x376 frames at t = 0.5, 1.0, ..., 4.0 s; true delta 40 ms."""
+def batched_problem(seed: int = 2, n: int = 1_000_000, frames: int = 8, trajectory: str = "straight") -> Problem:
+    """1M Gaussians from 50 sweeps along a 10 m/s drive sampled at 10 Hz
+    (straight by default); eight 1408x376 frames at t = 0.5, 1.0, ..., 4.0 s;
+    true delta 40 ms."""
     rng = np.random.default_rng(seed)
-    scene = _drive_scene(rng, n)
+    scene = _drive_scene(rng, n, trajectory=trajectory)
     ext = _true_extrinsic(rng)[None]
     fr = [Frame(CAM_KITTI, 0.5 * (i + 1)) for i in range(frames)]
     return Problem("batched", [scene], fr, ext, np.array([0.04]), tile=16)
@@ -356,11 +379,13 @@ def uneven_problem(seed: int = 3, sizes=(300_000, 1_000_000, 3_000_000),
 
 def calibration_problem(seed: int = 0, n: int = 1_000_000, frames: int = 8,
                         rot_deg: float = 5.0, trans_m: float = 0.5,
-                        delta0: float = 0.05, scene_seed: int = 2) -> Problem:
+                        delta0: float = 0.05, scene_seed: int = 2, trajectory: str = "straight") -> Problem:
     """The batched scene; targets at the true extrinsic and delta = 0, start
     from the extrinsic perturbed by rot_deg about a seeded axis and trans_m
-    along a seeded direction, and delta = delta0."""
-    base = batched_problem(scene_seed, n, frames)
+    along a seeded direction, and delta = delta0.  On the straight drive a
+    time offset and a translation along the motion are interchangeable; the
+    zigzag drive makes both observable."""
+    base = batched_problem(scene_seed, n, frames, trajectory=trajectory)
     rng = np.random.default_rng(1000 + seed)
     true = base.ext[0]
     omega0 = _perturb_rotvec(rng, true[:3], rot_deg)
