@@ -2,15 +2,16 @@
 // each tile, and its backward (Sec. III-B).
 //
 // One block per (frame, tile) work item of the whole batch, taken in the
-// heavy-first order gs_bin_sort computes (longest lists start first).  Per round the
-// block stages BATCH Gaussians of the tile's sorted range in shared memory
-// (mean, exponent coefficients, colour, alpha box).  Each warp owns a compact
-// full-width band of the tile; it ballots which staged Gaussians' alpha >=
-// alpha_min boxes meet its band and walks only those (in depth order, for
-// its PPT pixels per thread): outside the box alpha is below alpha_min, so
-// the cull is exact, and it is the same in both directions.  A pixel stops when compositing the next Gaussian would
-// bring its transmittance below t_min; the block stops when all its pixels
-// have stopped (checked once per round with a block vote).
+// heavy-first order gs_bin_sort computes (longest lists start first).  Each
+// warp owns a compact full-width band of the tile and walks the tile's
+// depth-sorted list on its own (no block-wide barrier inside the loop): it
+// loads chunks of batch/2 entries (prefetching the next chunk into registers
+// while it uses the current one), keeps the entries whose alpha >= alpha_min
+// box meets its band -- outside the box alpha is below alpha_min at every
+// pixel, so the cull is exact and identical in both directions -- compacts
+// them in order into its own shared-memory slot and composites them for its
+// PPT pixels per thread.  A warp stops as soon as all its pixels have
+// stopped.
 //
 // Per pixel and Gaussian (both directions use the same arithmetic):
 //   dx = u - mean_x, dy = v - mean_y
@@ -79,6 +80,29 @@ __device__ __forceinline__ bool box_hits(float4 a, float2 e, float xlo, float xh
     return (a.x + e.x >= xlo) && (a.x - e.x <= xhi) && (a.y + e.y >= ylo) && (a.y - e.y <= yhi);
 }
 
+// One staged Gaussian of a warp's chunk, as loaded from global memory.
+struct Entry {
+    float4 a;       // mean_x, mean_y, A, B
+    float4 b;       // C, F, rx, ry
+    float cr, cg, cb;
+    uint32_t g;     // Gaussian index within the scene
+    bool valid;
+};
+
+__device__ __forceinline__ void load_entry(Entry &e, bool valid, const uint32_t *__restrict__ vals, uint32_t at,
+                                           long long rec0, const float4 *__restrict__ splat,
+                                           const float *__restrict__ col) {
+    e.valid = valid;
+    if (!valid) return;
+    e.g = vals[at];
+    const long long r = rec0 + e.g;
+    e.a = splat[2 * r];
+    e.b = splat[2 * r + 1];
+    e.cr = __ldg(col + 3 * e.g);
+    e.cg = __ldg(col + 3 * e.g + 1);
+    e.cb = __ldg(col + 3 * e.g + 2);
+}
+
 template <int TILE, int BATCH>
 __global__ void __launch_bounds__(Cfg<TILE>::NT)
 k_render_fwd(const gs_frame *__restrict__ frames, int F, const uint32_t *__restrict__ order,
@@ -87,10 +111,11 @@ k_render_fwd(const gs_frame *__restrict__ frames, int F, const uint32_t *__restr
              Stats *__restrict__ stats, float *__restrict__ out_rgb, float *__restrict__ out_T,
              int32_t *__restrict__ out_last) {
     constexpr int NT = Cfg<TILE>::NT, PPT = Cfg<TILE>::PPT, RPW = Cfg<TILE>::RPW;
-    __shared__ float4 s0[BATCH];  // mean_x, mean_y, A, B
-    __shared__ float4 s1[BATCH];  // C, F, r, g
-    __shared__ float s2[BATCH];   // b
-    __shared__ float2 s3[BATCH];  // box half-widths
+    constexpr int NW = NT / 32, CH = BATCH / 2, PER = CH / 32;
+    __shared__ float4 s0[NW][CH];  // mean_x, mean_y, A, B
+    __shared__ float4 s1[NW][CH];  // C, F, r, g
+    __shared__ float s2[NW][CH];   // b
+    __shared__ int spos[NW][CH];   // position in the tile's sorted range
     __shared__ unsigned long long s_eval;
     const int t = (int)order[blockIdx.x];  // heavy tiles first
     const int f = frame_of_tile(frames, F, t);
@@ -99,6 +124,7 @@ k_render_fwd(const gs_frame *__restrict__ frames, int F, const uint32_t *__restr
     const int lt = t - fr.tile_offset;
     const int tx = lt % fr.tiles_x, ty = lt / fr.tiles_x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t lt_mask = (1u << lane) - 1u;
     const float xlo = (float)(tx * TILE), xhi = xlo + (float)(TILE - 1);
     const float ylo = (float)(ty * TILE + warp * RPW), yhi = ylo + (float)(RPW - 1);
     float px[PPT], py[PPT], T[PPT], c0[PPT], c1[PPT], c2[PPT];
@@ -123,68 +149,79 @@ k_render_fwd(const gs_frame *__restrict__ frames, int F, const uint32_t *__restr
     const long long rec0 = fr.record_offset;
     const float *col = colors + 3 * (size_t)fr.gauss_offset;
     unsigned evals = 0;
-    for (int b0 = 0; b0 < n; b0 += BATCH) {
+    // each warp walks the tile's list on its own: it loads a chunk of CH
+    // entries (the next one is prefetched while the current one is used),
+    // keeps those whose alpha box meets its band, compacts them in order into
+    // its shared-memory slot and composites them
+    Entry nx[PER];
+#pragma unroll
+    for (int p = 0; p < PER; p++) load_entry(nx[p], p * 32 + lane < n, vals, range.x + p * 32 + lane, rec0, splat, col);
+    for (int cb0 = 0; cb0 < n; cb0 += CH) {
         bool mine_done = true;
 #pragma unroll
         for (int k = 0; k < PPT; k++) mine_done &= done[k];
-        if (__syncthreads_and(mine_done)) break;
-        for (int i = threadIdx.x; i < BATCH; i += NT) {
-            const int j = b0 + i;
-            if (j < n) {
-                const uint32_t g = vals[range.x + j];
-                const long long r = rec0 + g;
-                const float4 a = splat[2 * r], b = splat[2 * r + 1];
-                s0[i] = a;
-                s1[i] = make_float4(b.x, b.y, __ldg(col + 3 * g), __ldg(col + 3 * g + 1));
-                s2[i] = __ldg(col + 3 * g + 2);
-                s3[i] = make_float2(b.z, b.w);
+        if (__all_sync(0xffffffffu, mine_done)) break;
+        Entry cu[PER];
+#pragma unroll
+        for (int p = 0; p < PER; p++) cu[p] = nx[p];
+        if (cb0 + CH < n) {
+#pragma unroll
+            for (int p = 0; p < PER; p++) {
+                const int i = cb0 + CH + p * 32 + lane;
+                load_entry(nx[p], i < n, vals, range.x + i, rec0, splat, col);
             }
         }
-        __syncthreads();
-        const int m = min(BATCH, n - b0);
-        if (!__all_sync(0xffffffffu, mine_done)) {
-            for (int q = 0; q * 32 < m; q++) {
-                const int i = q * 32 + lane;
-                uint32_t msk = __ballot_sync(0xffffffffu, i < m && box_hits(s0[i], s3[i], xlo, xhi, ylo, yhi));
-                while (msk) {
-                    const int j = q * 32 + __ffs(msk) - 1;
-                    msk &= msk - 1;
-                    const float4 a = s0[j], b = s1[j];
-                    const float cb = s2[j];
-                    // every lane evaluates the exponent; one warp vote decides
-                    // whether any pixel composites this Gaussian, and the
-                    // compositing itself runs predicated (no divergence)
-                    float e[PPT];
-                    bool ct[PPT];
-                    bool anyc = false;
+        int cnt = 0;
 #pragma unroll
-                    for (int k = 0; k < PPT; k++) {
-                        evals += !done[k];
-                        const float dx = px[k] - a.x, dy = py[k] - a.y;
-                        const float e2 = exponent2(dx, dy, a.z, a.w, b.x);
-                        e[k] = e2 + b.y;
-                        ct[k] = !done[k] && !(e2 > 0.f) && !(e[k] < rp.lmin);
-                        anyc |= ct[k];
-                    }
-                    if (!__any_sync(0xffffffffu, anyc)) continue;
+        for (int p = 0; p < PER; p++) {
+            const bool hit = cu[p].valid && box_hits(cu[p].a, make_float2(cu[p].b.z, cu[p].b.w), xlo, xhi, ylo, yhi);
+            const uint32_t msk = __ballot_sync(0xffffffffu, hit);
+            if (hit) {
+                const int at = cnt + __popc(msk & lt_mask);
+                s0[warp][at] = cu[p].a;
+                s1[warp][at] = make_float4(cu[p].b.x, cu[p].b.y, cu[p].cr, cu[p].cg);
+                s2[warp][at] = cu[p].cb;
+                spos[warp][at] = cb0 + p * 32 + lane;
+            }
+            cnt += __popc(msk);
+        }
+        __syncwarp();
+        for (int j = 0; j < cnt; j++) {
+            const float4 a = s0[warp][j], b = s1[warp][j];
+            const float cb = s2[warp][j];
+            const int pos = spos[warp][j];
+            // every lane evaluates the exponent; one warp vote decides
+            // whether any pixel composites this Gaussian, and the
+            // compositing itself runs predicated (no divergence)
+            float e[PPT];
+            bool ct[PPT];
+            bool anyc = false;
 #pragma unroll
-                    for (int k = 0; k < PPT; k++) {
-                        const float alpha = fminf(rp.amax, ex2_approx(e[k]));
-                        const float nT = T[k] * (1.f - alpha);
-                        const bool stop = ct[k] && nT < rp.tmin;
-                        const bool blend = ct[k] && !stop;
-                        done[k] = done[k] || stop;
-                        const float w = blend ? alpha * T[k] : 0.f;
-                        c0[k] = fmaf(b.z, w, c0[k]);
-                        c1[k] = fmaf(b.w, w, c1[k]);
-                        c2[k] = fmaf(cb, w, c2[k]);
-                        T[k] = blend ? nT : T[k];
-                        last[k] = blend ? b0 + j + 1 : last[k];
-                    }
-                }
+            for (int k = 0; k < PPT; k++) {
+                evals += !done[k];
+                const float dx = px[k] - a.x, dy = py[k] - a.y;
+                const float e2 = exponent2(dx, dy, a.z, a.w, b.x);
+                e[k] = e2 + b.y;
+                ct[k] = !done[k] && !(e2 > 0.f) && !(e[k] < rp.lmin);
+                anyc |= ct[k];
+            }
+            if (!__any_sync(0xffffffffu, anyc)) continue;
+#pragma unroll
+            for (int k = 0; k < PPT; k++) {
+                const float alpha = fminf(rp.amax, ex2_approx(e[k]));
+                const float nT = T[k] * (1.f - alpha);
+                const bool stop = ct[k] && nT < rp.tmin;
+                const bool blend = ct[k] && !stop;
+                done[k] = done[k] || stop;
+                const float w = blend ? alpha * T[k] : 0.f;
+                c0[k] = fmaf(b.z, w, c0[k]);
+                c1[k] = fmaf(b.w, w, c1[k]);
+                c2[k] = fmaf(cb, w, c2[k]);
+                T[k] = blend ? nT : T[k];
+                last[k] = blend ? pos + 1 : last[k];
             }
         }
-        __syncthreads();
+        __syncwarp();
     }
 #pragma unroll
     for (int k = 0; k < PPT; k++) {
@@ -248,12 +285,12 @@ k_render_bwd(const gs_frame *__restrict__ frames, int F, const uint32_t *__restr
              Stats *__restrict__ stats, const float *__restrict__ in_T, const int32_t *__restrict__ in_last,
              const float *__restrict__ dL_drgb, float4 *__restrict__ grad2d) {
     constexpr int NT = Cfg<TILE>::NT, PPT = Cfg<TILE>::PPT, RPW = Cfg<TILE>::RPW;
-    __shared__ float4 s0[BATCH];
-    __shared__ float4 s1[BATCH];
-    __shared__ float s2[BATCH];
-    __shared__ float2 s3[BATCH];
-    __shared__ long long s_rec[BATCH];
-    __shared__ int s_maxlast;
+    constexpr int NW = NT / 32, CH = BATCH / 2, PER = CH / 32;
+    __shared__ float4 s0[NW][CH];
+    __shared__ float4 s1[NW][CH];
+    __shared__ float s2[NW][CH];
+    __shared__ int spos[NW][CH];
+    __shared__ uint32_t sg[NW][CH];
     __shared__ unsigned long long s_eval;
     const int t = (int)order[blockIdx.x];  // heavy tiles first
     const int f = frame_of_tile(frames, F, t);
@@ -262,16 +299,13 @@ k_render_bwd(const gs_frame *__restrict__ frames, int F, const uint32_t *__restr
     const int lt = t - fr.tile_offset;
     const int tx = lt % fr.tiles_x, ty = lt / fr.tiles_x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t lt_mask = (1u << lane) - 1u;
     const float xlo = (float)(tx * TILE), xhi = xlo + (float)(TILE - 1);
     const float ylo = (float)(ty * TILE + warp * RPW), yhi = ylo + (float)(RPW - 1);
     float px[PPT], py[PPT], T[PPT], Tf[PPT], g0[PPT], g1[PPT], g2[PPT], bgd[PPT];
     float a0[PPT], a1[PPT], a2[PPT];
     int last[PPT];
-    if (threadIdx.x == 0) {
-        s_maxlast = 0;
-        s_eval = 0;
-    }
-    __syncthreads();
+    if (threadIdx.x == 0) s_eval = 0;
     // the range of this tile; a pixel's start position never exceeds it
     const uint2 range = ranges[t];
     const int n = (int)(range.y - range.x);
@@ -300,97 +334,110 @@ k_render_bwd(const gs_frame *__restrict__ frames, int F, const uint32_t *__restr
         bgd[k] = rp.bg0 * g0[k] + rp.bg1 * g1[k] + rp.bg2 * g2[k];
         mylast = max(mylast, last[k]);
     }
+    // each warp walks its own part of the list backwards, from the largest
+    // start position of its pixels, in chunks of CH (the next one prefetched)
     const int warp_last = __reduce_max_sync(0xffffffffu, mylast);
-    if (lane == 0) atomicMax(&s_maxlast, warp_last);
-    __syncthreads();
-    const int maxlast = s_maxlast;
     const long long rec0 = fr.record_offset;
     const float *col = colors + 3 * (size_t)fr.gauss_offset;
     unsigned evals = 0;
-    for (int b_end = maxlast; b_end > 0; b_end -= BATCH) {
-        const int b0 = max(0, b_end - BATCH);
-        const int m = b_end - b0;
-        for (int i = threadIdx.x; i < m; i += NT) {
-            const uint32_t g = vals[range.x + b0 + i];
-            const long long r = rec0 + g;
-            const float4 a = splat[2 * r], b = splat[2 * r + 1];
-            s0[i] = a;
-            s1[i] = make_float4(b.x, b.y, __ldg(col + 3 * g), __ldg(col + 3 * g + 1));
-            s2[i] = __ldg(col + 3 * g + 2);
-            s3[i] = make_float2(b.z, b.w);
-            s_rec[i] = r;
+    Entry nx[PER];
+    {
+        const int c0 = max(0, warp_last - CH);
+#pragma unroll
+        for (int p = 0; p < PER; p++) {
+            const int i = c0 + p * 32 + lane;
+            load_entry(nx[p], i < warp_last, vals, range.x + i, rec0, splat, col);
         }
-        __syncthreads();
-        // entries at or beyond the warp's largest start position concern none of its pixels
-        const int mw = min(m, warp_last - b0);
-        for (int q = (mw - 1) >> 5; q >= 0; q--) {
-            const int i = q * 32 + lane;
-            uint32_t msk = __ballot_sync(0xffffffffu, i < mw && box_hits(s0[i], s3[i], xlo, xhi, ylo, yhi));
-            while (msk) {
-                const int bit = 31 - __clz(msk);
-                msk &= ~(1u << bit);
-                const int j = q * 32 + bit;
-                const int pos = b0 + j;
-                const float4 a = s0[j], b = s1[j];
-                const float cb = s2[j];
-                // every lane evaluates the exponent; one warp vote decides
-                // whether any pixel composited this Gaussian; the gradient
-                // math then runs predicated (zero where a pixel did not)
-                float e[PPT], dxs[PPT], dys[PPT];
-                bool ct[PPT];
-                bool anyc = false;
+    }
+    for (int c_end = warp_last; c_end > 0; c_end -= CH) {
+        const int c0 = max(0, c_end - CH);
+        Entry cu[PER];
 #pragma unroll
-                for (int k = 0; k < PPT; k++) {
-                    const bool act = pos < last[k];
-                    evals += act;
-                    dxs[k] = px[k] - a.x;
-                    dys[k] = py[k] - a.y;
-                    const float e2 = exponent2(dxs[k], dys[k], a.z, a.w, b.x);
-                    e[k] = e2 + b.y;
-                    ct[k] = act && !(e2 > 0.f) && !(e[k] < rp.lmin);
-                    anyc |= ct[k];
-                }
-                if (!__any_sync(0xffffffffu, anyc)) continue;
-                float dmx = 0.f, dmy = 0.f, dA = 0.f, dB = 0.f, dC = 0.f, dF = 0.f, dr = 0.f, dg = 0.f, db = 0.f;
+        for (int p = 0; p < PER; p++) cu[p] = nx[p];
+        if (c0 > 0) {
+            const int n0 = max(0, c0 - CH);
 #pragma unroll
-                for (int k = 0; k < PPT; k++) {
-                    const float G = ex2_approx(e[k]);
-                    const float alpha = ct[k] ? fminf(rp.amax, G) : 0.f;
-                    const float inv = rcp_approx(1.f - alpha);
-                    T[k] = ct[k] ? T[k] * inv : T[k];  // T before this Gaussian
-                    const float w = alpha * T[k];
-                    dr = fmaf(w, g0[k], dr);
-                    dg = fmaf(w, g1[k], dg);
-                    db = fmaf(w, g2[k], db);
-                    const float dalpha = T[k] * ((b.z - a0[k]) * g0[k] + (b.w - a1[k]) * g1[k] + (cb - a2[k]) * g2[k]) -
-                                         Tf[k] * bgd[k] * inv;
-                    a0[k] = fmaf(alpha, b.z - a0[k], a0[k]);
-                    a1[k] = fmaf(alpha, b.w - a1[k], a1[k]);
-                    a2[k] = fmaf(alpha, cb - a2[k], a2[k]);
-                    const float de = (ct[k] && !(G > rp.amax)) ? dalpha * alpha * kLn2 : 0.f;
-                    const float dx = dxs[k], dy = dys[k];
-                    dF += de;
-                    dA = fmaf(de * dx, dx, dA);
-                    dB = fmaf(de * dx, dy, dB);
-                    dC = fmaf(de * dy, dy, dC);
-                    dmx -= de * (2.f * a.z * dx + a.w * dy);
-                    dmy -= de * (a.w * dx + 2.f * b.x * dy);
-                }
-                {
-                    // record layout: (dmx, dmy, dA, dB), (dC, dF, dr, dg), (db, -, -, -)
-                    const float v8[8] = {dmx, dmy, dA, dB, dC, dF, dr, dg};
-                    const float tot = warp_sum8_transposed(v8, lane);
-                    db = warp_sum_f(db);
-                    float *rec = reinterpret_cast<float *>(grad2d + 3 * s_rec[j]);
-                    if ((lane & 3) == 0) atomicAdd(rec + (lane >> 2), tot);
-                    if (lane == 0) atomicAdd(rec + 8, db);
-                }
+            for (int p = 0; p < PER; p++) {
+                const int i = n0 + p * 32 + lane;
+                load_entry(nx[p], i < c0, vals, range.x + i, rec0, splat, col);
             }
         }
-        __syncthreads();
+        int cnt = 0;
+#pragma unroll
+        for (int p = 0; p < PER; p++) {
+            const bool hit = cu[p].valid && box_hits(cu[p].a, make_float2(cu[p].b.z, cu[p].b.w), xlo, xhi, ylo, yhi);
+            const uint32_t msk = __ballot_sync(0xffffffffu, hit);
+            if (hit) {
+                const int at = cnt + __popc(msk & lt_mask);
+                s0[warp][at] = cu[p].a;
+                s1[warp][at] = make_float4(cu[p].b.x, cu[p].b.y, cu[p].cr, cu[p].cg);
+                s2[warp][at] = cu[p].cb;
+                spos[warp][at] = c0 + p * 32 + lane;
+                sg[warp][at] = cu[p].g;
+            }
+            cnt += __popc(msk);
+        }
+        __syncwarp();
+        for (int j = cnt - 1; j >= 0; j--) {
+            const float4 a = s0[warp][j], b = s1[warp][j];
+            const float cb = s2[warp][j];
+            const int pos = spos[warp][j];
+            // every lane evaluates the exponent; one warp vote decides
+            // whether any pixel composited this Gaussian; the gradient
+            // math then runs predicated (zero where a pixel did not)
+            float e[PPT], dxs[PPT], dys[PPT];
+            bool ct[PPT];
+            bool anyc = false;
+#pragma unroll
+            for (int k = 0; k < PPT; k++) {
+                const bool act = pos < last[k];
+                evals += act;
+                dxs[k] = px[k] - a.x;
+                dys[k] = py[k] - a.y;
+                const float e2 = exponent2(dxs[k], dys[k], a.z, a.w, b.x);
+                e[k] = e2 + b.y;
+                ct[k] = act && !(e2 > 0.f) && !(e[k] < rp.lmin);
+                anyc |= ct[k];
+            }
+            if (!__any_sync(0xffffffffu, anyc)) continue;
+            float dmx = 0.f, dmy = 0.f, dA = 0.f, dB = 0.f, dC = 0.f, dF = 0.f, dr = 0.f, dg = 0.f, db = 0.f;
+#pragma unroll
+            for (int k = 0; k < PPT; k++) {
+                const float G = ex2_approx(e[k]);
+                const float alpha = ct[k] ? fminf(rp.amax, G) : 0.f;
+                const float inv = rcp_approx(1.f - alpha);
+                T[k] = ct[k] ? T[k] * inv : T[k];  // T before this Gaussian
+                const float w = alpha * T[k];
+                dr = fmaf(w, g0[k], dr);
+                dg = fmaf(w, g1[k], dg);
+                db = fmaf(w, g2[k], db);
+                const float dalpha = T[k] * ((b.z - a0[k]) * g0[k] + (b.w - a1[k]) * g1[k] + (cb - a2[k]) * g2[k]) -
+                                     Tf[k] * bgd[k] * inv;
+                a0[k] = fmaf(alpha, b.z - a0[k], a0[k]);
+                a1[k] = fmaf(alpha, b.w - a1[k], a1[k]);
+                a2[k] = fmaf(alpha, cb - a2[k], a2[k]);
+                const float de = (ct[k] && !(G > rp.amax)) ? dalpha * alpha * kLn2 : 0.f;
+                const float dx = dxs[k], dy = dys[k];
+                dF += de;
+                dA = fmaf(de * dx, dx, dA);
+                dB = fmaf(de * dx, dy, dB);
+                dC = fmaf(de * dy, dy, dC);
+                dmx -= de * (2.f * a.z * dx + a.w * dy);
+                dmy -= de * (a.w * dx + 2.f * b.x * dy);
+            }
+            // record layout: (dmx, dmy, dA, dB), (dC, dF, dr, dg), (db, -, -, -)
+            const float v8[8] = {dmx, dmy, dA, dB, dC, dF, dr, dg};
+            const float tot = warp_sum8_transposed(v8, lane);
+            db = warp_sum_f(db);
+            float *rec = reinterpret_cast<float *>(grad2d + 3 * (rec0 + sg[warp][j]));
+            if ((lane & 3) == 0) atomicAdd(rec + (lane >> 2), tot);
+            if (lane == 0) atomicAdd(rec + 8, db);
+        }
+        __syncwarp();
     }
     unsigned long long ev = evals;
     for (int s = 16; s > 0; s >>= 1) ev += __shfl_xor_sync(0xffffffffu, ev, s);
+    __syncthreads();
     if (lane == 0) atomicAdd(&s_eval, ev);
     __syncthreads();
     if (threadIdx.x == 0) atomicAdd(&stats->eval_bwd, s_eval);
