@@ -36,7 +36,7 @@ sys.path.insert(0, ROOT)
 import numpy as np  # noqa: E402
 
 METRIC = "calib iters/s (fwd+bwd, 8×1408×376, 1M Gaussians) batched vs per-frame"
-WORKLOAD = "1M LiDAR-anchored Gaussians (50 synthetic 64-beam sweeps, 10 m/s drive), 8 frames 1408x376, tile 16"
+WORKLOAD = "1M LiDAR-anchored Gaussians (50 synthetic 64-beam sweeps, 10 m/s drive), 8 frames 1408x376"
 FLOP_PER_EVAL_FWD = 20.0   # per evaluated (pixel, Gaussian) pair, forward
 FLOP_PER_EVAL_BWD = 60.0   # backward: about three times the forward
 KERNEL_NAMES = {1: "project", 2: "bin_sort", 3: "render_fwd", 4: "render_bwd", 5: "project_bwd"}
@@ -50,7 +50,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--tile", type=int, default=16)
-    ap.add_argument("--batch", type=int, default=128)
+    ap.add_argument("--batch", type=int, default=64)
     ap.add_argument("--gaussians", type=int, default=1_000_000)
     ap.add_argument("--frames", type=int, default=8)
     ap.add_argument("--per-frame-steps", type=int, default=20)

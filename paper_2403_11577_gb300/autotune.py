@@ -42,9 +42,22 @@ def _save(d):
     os.replace(tmp, CACHE)
 
 
+def plan_with_capacity(problem, scene, opts, ext, delta, cap=None):
+    """A plan whose pair capacity holds the batch at (ext, delta): the
+    capacity is doubled until the binning reports no overflow."""
+    frames = render.Plan.frames_from_problem(problem, scene)
+    cap = cap or render.default_pair_capacity(frames, opts.tile)
+    while True:
+        plan = render.Plan(frames, scene.n, problem.num_cameras, len(problem.scenes), opts, cap, scene.X.device)
+        plan.forward(scene, ext, delta)
+        if not plan.stats().status & 1 or cap >= (1 << 32) - 1:
+            return plan
+        cap = int(min(2 * cap, (1 << 32) - 1))
+
+
 def time_setting(problem, scene, target, ext, delta, tile, batch, reps=5, base=None):
     opts = render.RenderOptions(tile=tile, batch=batch, **(base or {}))
-    plan = render.Plan.for_problem(problem, scene, opts)
+    plan = plan_with_capacity(problem, scene, opts, ext, delta)
     step = render.CalibStep(plan, scene, target, ext, delta, graph=True)
     for _ in range(2):
         step()

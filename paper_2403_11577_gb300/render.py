@@ -28,7 +28,7 @@ class RenderOptions:
     scale_max: float = float("inf")
     bg: tuple = (0.0, 0.0, 0.0)
     tile: int = 16
-    batch: int = 128
+    batch: int = 64
     frustum_margin: float = 0.15
 
     def c(self) -> capi.GsOpts:
