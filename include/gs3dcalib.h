@@ -60,7 +60,8 @@ enum {
 enum {
     GS_DEV_PAIR_OVERFLOW = 1u,  /* more tile-Gaussian pairs than pair_capacity:
                                    the batch was rendered with no Gaussians */
-    GS_DEV_NONFINITE = 2u       /* a non-finite projected value was culled */
+    GS_DEV_NONFINITE = 2u       /* a Gaussian with non-finite parameters or
+                                   projection was culled */
 };
 
 /* One camera frame n_i (Sec. III-A notation table). */

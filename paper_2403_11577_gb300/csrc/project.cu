@@ -157,9 +157,11 @@ k_project(const gs_frame *__restrict__ frames, int F, int N, const float *__rest
     if (g >= N) return;
     GaussParams G;
     load_gauss(g, X, quat, log_s, logit_o, o, G);
-    const bool opaque_enough = G.o >= o.alpha_min;
+    // non-finite parameters: cull the Gaussian and report it
+    bool nonfinite = !(isfinite(G.X[0]) && isfinite(G.X[1]) && isfinite(G.X[2]) && isfinite(G.Sig[0]) &&
+                       isfinite(G.Sig[3]) && isfinite(G.Sig[5]) && isfinite(G.F));
+    const bool opaque_enough = !nonfinite && G.o >= o.alpha_min;
     const float tile = (float)o.tile, itile = 1.f / tile;
-    bool nonfinite = false;
     for (int f = 0; f < F; f++) {
         const gs_frame &fr = frames[f];
         if (g < fr.gauss_offset || g >= fr.gauss_offset + fr.gauss_count) continue;
