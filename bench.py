@@ -37,8 +37,16 @@ import numpy as np  # noqa: E402
 
 METRIC = "calib iters/s (fwd+bwd, 8×1408×376, 1M Gaussians) batched vs per-frame"
 WORKLOAD = "1M LiDAR-anchored Gaussians (50 synthetic 64-beam sweeps, 10 m/s drive), 8 frames 1408x376"
-FLOP_PER_EVAL_FWD = 20.0   # per evaluated (pixel, Gaussian) pair, forward
-FLOP_PER_EVAL_BWD = 60.0   # backward: about three times the forward
+# Arithmetic per composited (pixel, Gaussian) pair, i.e. per pair with
+# alpha >= alpha_min before the pixel stops (Eq. 5), comparisons not counted.
+# Forward: dx, dy (2), exponent (7), + log2 o (1), 2^e and the alpha clamp (2),
+# 1 - alpha (1), T (1 - alpha) (1), alpha T (1), colour (3 fma = 6): 21.
+# Backward: the same exponent and alpha (12), 1 - alpha, 1/(1 - alpha), T
+# recovery (3), alpha T (1), c . g (5), dL/dalpha (3), light behind (2),
+# dL/de (1), de dx, de dy (2), dA, dB, dC (6), sums for the mean and F (3),
+# colour gradient (6): 44.
+FLOP_PER_EVAL_FWD = 21.0
+FLOP_PER_EVAL_BWD = 44.0
 KERNEL_NAMES = {1: "project", 2: "bin_sort", 3: "render_fwd", 4: "render_bwd", 5: "project_bwd"}
 KERNEL_SOURCES = {1: "project.cu", 2: "binsort.cu", 3: "render.cu", 4: "render.cu", 5: "project.cu"}
 
@@ -334,7 +342,7 @@ def run_ours(args, world, rank, local):
         peak = sms * 128 * 2 * clock_mhz * 1e6 / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": load_traffic(dom), "kernel": KERNEL_NAMES[dom], "launch_ms": dom_ms,
-                "units_per_launch": int(evals), "unit_work": "%g flop per evaluated (pixel, Gaussian) pair" %
+                "units_per_launch": int(evals), "unit_work": "%g flop per composited (pixel, Gaussian) pair" %
                 (FLOP_PER_EVAL_FWD if dom == 3 else FLOP_PER_EVAL_BWD),
                 "peak_basis": "FP32: %d SMs x 128 lanes x 2 flop x %.0f MHz (median SM clock in the timed region)"
                 % (sms, clock_mhz)}
@@ -390,7 +398,7 @@ def run_ours(args, world, rank, local):
                    "l2": "inputs larger than L2 (%.1f GB workspace per iteration)" % (plan.ws_bytes / 1e9)},
         "per_frame": {"value": per_frame, "unit": "iters/s", "speedup_batched": value / world / per_frame},
         "kernel_ms": kernel_ms,
-        "evaluations": {"fwd": int(st.eval_fwd), "bwd": int(st.eval_bwd)},
+        "composited_pairs": {"fwd": int(st.eval_fwd), "bwd": int(st.eval_bwd)},
         "roofline": roof,
         "e2e": {"value": e2e, "unit": "iters/s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": launches_per_step * args.steps,

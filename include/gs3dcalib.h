@@ -124,8 +124,8 @@ typedef struct {
     uint32_t status;            /* GS_DEV_* bits, sticky until gs_reset_status */
     uint32_t reserved;
     uint64_t num_pairs;         /* tile-Gaussian pairs of the last gs_bin_sort */
-    uint64_t eval_fwd;          /* (pixel, pair) evaluations, last gs_render_fwd */
-    uint64_t eval_bwd;          /* (pixel, pair) evaluations, last gs_render_bwd */
+    uint64_t eval_fwd;          /* composited (pixel, Gaussian) pairs, last gs_render_fwd */
+    uint64_t eval_bwd;          /* composited (pixel, Gaussian) pairs, last gs_render_bwd */
 } gs_stats;
 
 /* ------------------------------------------------------------ planning -- */

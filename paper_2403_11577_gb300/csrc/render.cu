@@ -2,16 +2,31 @@
 // each tile, and its backward (Sec. III-B).
 //
 // One block per (frame, tile) work item of the whole batch, taken in the
-// heavy-first order gs_bin_sort computes (longest lists start first).  Each
-// warp owns a compact full-width band of the tile and walks the tile's
+// heavy-first order gs_bin_sort computes (longest lists first).  Each warp
+// owns a compact full-width band of the tile and walks the tile's
 // depth-sorted list on its own (no block-wide barrier inside the loop): it
 // loads chunks of batch/2 entries (prefetching the next chunk into registers
-// while it uses the current one), keeps the entries whose alpha >= alpha_min
-// box meets its band -- outside the box alpha is below alpha_min at every
-// pixel, so the cull is exact and identical in both directions -- compacts
-// them in order into its own shared-memory slot and composites them for its
-// PPT pixels per thread.  A warp stops as soon as all its pixels have
-// stopped.
+// while it uses the current one), keeps the entries that can reach
+// alpha >= alpha_min somewhere in its band, compacts them in order into its
+// own shared-memory slot and composites them.  A warp stops as soon as all
+// its pixels have stopped.
+//
+// The heaviest tiles (up to two per SM, the head of the heavy-first order)
+// bound the kernel's duration: a band of a tile near the vanishing point
+// walks tens of thousands of entries alone.  Each of them is split into two
+// work items (upper and lower half) with bands of half the height and half
+// the pixels per thread, which halves the Gaussians a warp composites and so
+// that tile's critical path.  The work items of one launch are: the halves
+// of the heavy tiles first (blocks are dispatched in index order, so they
+// start first), then every other tile whole.  The image does not depend on
+// the band shape (see the culling below).
+//
+// Culling per band is exact: a Gaussian is kept when its alpha box meets the
+// band and the minimum of its quadratic form over the band rectangle is
+// within reach of alpha_min (the minimum of a convex quadratic over a
+// rectangle lies at the centre or on a side the centre is outside of; a
+// margin above the rounding of both this test and the per-pixel exponent
+// keeps it conservative).
 //
 // Per pixel and Gaussian (both directions use the same arithmetic):
 //   dx = u - mean_x, dy = v - mean_y
@@ -21,31 +36,45 @@
 //
 // Backward: walks the pixel's range from its last composited Gaussian back
 // to the first, recovering T_i = T_{i+1} / (1 - alpha_i) from the final
-// transmittance instead of storing it, with accum = colour composited behind:
+// transmittance instead of storing it, with S = light composited behind,
+// projected on the pixel's colour gradient g:
+//   S_i = sum_{j>i} alpha_j T_j (c_j . g) + T_final (bg . g)
 //   dL/dc_i     = alpha_i T_i g
-//   dL/dalpha_i = T_i (c_i - accum) . g - T_final (bg . g) / (1 - alpha_i)
+//   dL/dalpha_i = T_i (c_i . g) - S_i / (1 - alpha_i)
 //   dL/de       = dL/dalpha_i * alpha_i * ln 2   (0 where alpha is clamped)
 // giving dL/dF = dL/de, dL/dA = dL/de dx^2, dL/dB = dL/de dx dy,
-// dL/dC = dL/de dy^2, dL/dmean = -dL/de (2A dx + B dy, B dx + 2C dy).
-// The nine per-pixel values are summed over the thread's pixels, then over
-// the warp (skipped when no lane contributes): eight of them by a transposed
+// dL/dC = dL/de dy^2, and, as A, B, C are per Gaussian,
+// dL/dmean = -(2A sum(dL/de dx) + B sum(dL/de dy), B sum(dL/de dx) + 2C sum(dL/de dy)).
+// The nine per-pixel sums are added over the thread's pixels, then over the
+// warp (skipped when no lane contributes): eight of them by a transposed
 // halving exchange that leaves one total per group of four lanes, which the
 // group's first lane adds to the record (eight lanes, contiguous addresses),
-// the ninth by a plain shuffle reduction.
+// the ninth by a plain shuffle reduction.  The factor ln 2 is applied to the
+// warp totals.
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace gs {
 
 namespace {
 
-// Threads per block: 64 for 8x8 tiles (a pixel each), 128 for 16x16 (two
-// vertically adjacent pixels each), 256 for 32x32 (four each).
-template <int TILE>
+// Pixels per thread: 2 at tiles 8 and 16 (bands 8x8 and 16x4), 4 at 32
+// (32x4); half of that in the halves of heavy tiles (bands 8x4, 16x2, 32x2).
+__host__ __device__ constexpr int pix_per_thread(int tile) { return tile == 32 ? 4 : 2; }
+
+// A work item of TILE-wide rows for NT threads at PPT pixels per thread.
+template <int TILE, int PPT, int NT>
 struct Cfg {
-    static constexpr int NPIX = TILE * TILE;
-    static constexpr int PPT = TILE == 8 ? 1 : (TILE == 16 ? 2 : 4);  // pixels per thread
-    static constexpr int NT = NPIX / PPT;
-    static constexpr int RPW = 32 * PPT / TILE;    // pixel rows per warp (full tile width)
+    static constexpr int NW = NT / 32;            // warps per block
+    static constexpr int RPW = 32 * PPT / TILE;   // pixel rows of a warp's band
+    static constexpr int ROWS = NW * RPW;         // pixel rows of the item
+    static_assert(NT % 32 == 0 && (32 * PPT) % TILE == 0 && ROWS <= TILE, "a warp owns full-width rows");
+};
+
+template <int TILE>
+struct Threads {
+    static constexpr int NT = TILE * TILE / pix_per_thread(TILE);
 };
 
 struct RenderParams {
@@ -54,8 +83,9 @@ struct RenderParams {
     float bg0, bg1, bg2;
 };
 
-// Exponent e2 = A dx^2 + B dx dy + C dy^2 with a fixed operation order
-// (no contraction freedom), shared by the forward and the backward.
+// Exponent e2 = A dx^2 + B dx dy + C dy^2 with a fixed operation order (no
+// contraction freedom), shared by the forward and the backward and by every
+// band shape.
 __device__ __forceinline__ float exponent2(float dx, float dy, float A, float B, float C) {
     const float bdy = __fmul_rn(B, dy);
     const float t = __fmaf_rn(A, dx, bdy);
@@ -64,23 +94,45 @@ __device__ __forceinline__ float exponent2(float dx, float dy, float A, float B,
     return __fmaf_rn(dx, t, q);
 }
 
-// Pixel (lx, ly) of the tile handled by thread `tid` as its k-th pixel.  A
-// warp covers RPW consecutive full-width rows, so its pixels form a compact
-// TILE x RPW region (used to cull Gaussians per warp).
-template <int TILE>
-__device__ __forceinline__ void pixel_of(int tid, int k, int &lx, int &ly) {
-    lx = tid % TILE;
-    ly = (tid / TILE) * Cfg<TILE>::PPT + k;
+// Whether a Gaussian with centre m, exponent coefficients (A, B, C), F =
+// log2 opacity and alpha box half-widths (rx, ry) can reach alpha >=
+// alpha_min at some point of the band [xlo, xhi] x [ylo, yhi].
+// With P(d) = -(A dx^2 + B dx dy + C dy^2) (positive definite), a pixel can
+// pass only where P <= F - lmin.  The minimum of P over the band is 0 with
+// the centre inside; otherwise it lies on a side that the centre is outside
+// of, where P restricted to the side is a parabola minimised at a clamped
+// point.  The margin 2^-10 (F - lmin) + 2^-16 (|A| Dx^2 + |B| Dx Dy + |C| Dy^2)
+// (Dx, Dy the largest offsets within the band) exceeds the rounding error
+// of this test and of exponent2 by more than an order of magnitude, so a
+// Gaussian that the per-pixel test would composite is never dropped.
+__device__ __forceinline__ bool band_hits(float mx, float my, float A, float B, float C, float F, float rx,
+                                          float ry, float lmin, float xlo, float xhi, float ylo, float yhi) {
+    if (!((mx + rx >= xlo) && (mx - rx <= xhi) && (my + ry >= ylo) && (my - ry <= yhi))) return false;
+    const float a = -A, b = -B, c = -C;
+    const float x0 = xlo - mx, x1 = xhi - mx, y0 = ylo - my, y1 = yhi - my;
+    const bool out_x = x0 > 0.f || x1 < 0.f, out_y = y0 > 0.f || y1 < 0.f;
+    float pmin = 0.f;
+    if (out_x || out_y) {
+        float px = INFINITY, py = INFINITY;
+        if (out_x) {
+            const float dx = x0 > 0.f ? x0 : x1;
+            const float dy = fminf(fmaxf(__fdividef(-b * dx, 2.f * c), y0), y1);
+            px = dx * (a * dx + b * dy) + c * dy * dy;
+        }
+        if (out_y) {
+            const float dy = y0 > 0.f ? y0 : y1;
+            const float dx = fminf(fmaxf(__fdividef(-b * dy, 2.f * a), x0), x1);
+            py = dx * (a * dx + b * dy) + c * dy * dy;
+        }
+        pmin = fminf(px, py);
+    }
+    const float lim = F - lmin;
+    const float Dx = fmaxf(fabsf(x0), fabsf(x1)), Dy = fmaxf(fabsf(y0), fabsf(y1));
+    const float mag = a * Dx * Dx + fabsf(b) * Dx * Dy + c * Dy * Dy;
+    return pmin <= lim + fabsf(lim) * 0x1p-10f + mag * 0x1p-16f;
 }
 
-// Whether the Gaussian's alpha >= alpha_min box (centre m, half-widths e)
-// meets the warp's pixel region.  Outside that box alpha < alpha_min at
-// every pixel, so skipping is exact; forward and backward use this same test.
-__device__ __forceinline__ bool box_hits(float4 a, float2 e, float xlo, float xhi, float ylo, float yhi) {
-    return (a.x + e.x >= xlo) && (a.x - e.x <= xhi) && (a.y + e.y >= ylo) && (a.y - e.y <= yhi);
-}
-
-// One staged Gaussian of a warp's chunk, as loaded from global memory.
+// One Gaussian of a warp's chunk, as loaded from global memory.
 struct Entry {
     float4 a;       // mean_x, mean_y, A, B
     float4 b;       // C, F, rx, ry
@@ -103,42 +155,78 @@ __device__ __forceinline__ void load_entry(Entry &e, bool valid, const uint32_t 
     e.cb = __ldg(col + 3 * e.g + 2);
 }
 
-template <int TILE, int BATCH>
-__global__ void __launch_bounds__(Cfg<TILE>::NT)
-k_render_fwd(const gs_frame *__restrict__ frames, int F, const uint32_t *__restrict__ order,
-             const uint2 *__restrict__ ranges, const uint32_t *__restrict__ vals,
-             const float4 *__restrict__ splat, const float *__restrict__ colors, RenderParams rp,
-             Stats *__restrict__ stats, float *__restrict__ out_rgb, float *__restrict__ out_T,
-             int32_t *__restrict__ out_last) {
-    constexpr int NT = Cfg<TILE>::NT, PPT = Cfg<TILE>::PPT, RPW = Cfg<TILE>::RPW;
-    constexpr int NW = NT / 32, CH = BATCH / 2, PER = CH / 32;
-    __shared__ float4 s0[NW][CH];  // mean_x, mean_y, A, B
-    __shared__ float4 s1[NW][CH];  // C, F, r, g
-    __shared__ float s2[NW][CH];   // b
-    __shared__ int spos[NW][CH];   // position in the tile's sorted range
-    __shared__ unsigned long long s_eval;
-    const int t = (int)order[blockIdx.x];  // heavy tiles first
+// A kept Gaussian in the warp's shared-memory slot.
+struct alignas(16) Staged {
+    float4 a;  // mean_x, mean_y, A, B
+    float4 b;  // C, F, r, g
+    uint4 z;   // bits of b, position in the tile's range, Gaussian index, 0
+};
+
+// Band of warp `warp` in the work item starting at row row0 of tile (tx, ty),
+// clipped to the image.
+template <int TILE, int RPW>
+__device__ __forceinline__ void band_of(int tx, int ty, int row0, int warp, int W, int H, float &xlo, float &xhi,
+                                        float &ylo, float &yhi) {
+    xlo = (float)(tx * TILE);
+    xhi = (float)min(tx * TILE + TILE - 1, W - 1);
+    ylo = (float)(ty * TILE + row0 + warp * RPW);
+    yhi = (float)min(ty * TILE + row0 + warp * RPW + RPW - 1, H - 1);
+}
+
+// Compact the chunk's kept entries, in order, into the warp's slot; returns
+// how many were kept.  pos0 + p * 32 + lane is entry p's position.
+template <int PER>
+__device__ __forceinline__ int compact(Staged *st, const Entry (&cu)[PER], int pos0, int lane, float lmin, float xlo,
+                                       float xhi, float ylo, float yhi) {
+    const uint32_t lt_mask = (1u << lane) - 1u;
+    int cnt = 0;
+#pragma unroll
+    for (int p = 0; p < PER; p++) {
+        const Entry &e = cu[p];
+        const bool hit = e.valid && band_hits(e.a.x, e.a.y, e.a.z, e.a.w, e.b.x, e.b.y, e.b.z, e.b.w, lmin, xlo, xhi,
+                                              ylo, yhi);
+        const uint32_t msk = __ballot_sync(0xffffffffu, hit);
+        if (hit) {
+            Staged &s = st[cnt + __popc(msk & lt_mask)];
+            s.a = e.a;
+            s.b = make_float4(e.b.x, e.b.y, e.cr, e.cg);
+            s.z = make_uint4(__float_as_uint(e.cb), (uint32_t)(pos0 + p * 32 + lane), e.g, 0u);
+        }
+        cnt += __popc(msk);
+    }
+    __syncwarp();
+    return cnt;
+}
+
+// Forward of one work item: rows [row0, row0 + ROWS) of tile t.
+template <int TILE, int PPT, int NT, int BATCH>
+__device__ __forceinline__ void fwd_item(int t, int row0, Staged *st_all, unsigned long long &s_eval,
+                                         const gs_frame *__restrict__ frames, int F,
+                                         const uint2 *__restrict__ ranges, const uint32_t *__restrict__ vals,
+                                         const float4 *__restrict__ splat, const float *__restrict__ colors,
+                                         const RenderParams &rp, Stats *__restrict__ stats,
+                                         float *__restrict__ out_rgb, float *__restrict__ out_T,
+                                         int32_t *__restrict__ out_last) {
+    constexpr int RPW = Cfg<TILE, PPT, NT>::RPW, CH = BATCH / 2, PER = CH / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    Staged *st = st_all + warp * CH;
     const int f = frame_of_tile(frames, F, t);
     const gs_frame &fr = frames[f];
     const int W = fr.width, H = fr.height;
     const int lt = t - fr.tile_offset;
     const int tx = lt % fr.tiles_x, ty = lt / fr.tiles_x;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint32_t lt_mask = (1u << lane) - 1u;
-    const float xlo = (float)(tx * TILE), xhi = xlo + (float)(TILE - 1);
-    const float ylo = (float)(ty * TILE + warp * RPW), yhi = ylo + (float)(RPW - 1);
-    float px[PPT], py[PPT], T[PPT], c0[PPT], c1[PPT], c2[PPT];
+    float xlo, xhi, ylo, yhi;
+    band_of<TILE, RPW>(tx, ty, row0, warp, W, H, xlo, xhi, ylo, yhi);
+    const int u = tx * TILE + (int)threadIdx.x % TILE;
+    const int v0 = ty * TILE + row0 + ((int)threadIdx.x / TILE) * PPT;  // first row of the thread's pixels
+    const float px = (float)u;
+    float py[PPT], T[PPT], c0[PPT], c1[PPT], c2[PPT];
     int last[PPT];
-    bool done[PPT], inside[PPT];
+    bool done[PPT];
 #pragma unroll
     for (int k = 0; k < PPT; k++) {
-        int lx, ly;
-        pixel_of<TILE>(threadIdx.x, k, lx, ly);
-        const int u = tx * TILE + lx, v = ty * TILE + ly;
-        px[k] = (float)u;
-        py[k] = (float)v;
-        inside[k] = u < W && v < H;
-        done[k] = !inside[k];
+        py[k] = (float)(v0 + k);
+        done[k] = !(u < W && v0 + k < H);
         T[k] = 1.f;
         c0[k] = c1[k] = c2[k] = 0.f;
         last[k] = 0;
@@ -148,11 +236,7 @@ k_render_fwd(const gs_frame *__restrict__ frames, int F, const uint32_t *__restr
     const int n = (int)(range.y - range.x);
     const long long rec0 = fr.record_offset;
     const float *col = colors + 3 * (size_t)fr.gauss_offset;
-    unsigned evals = 0;
-    // each warp walks the tile's list on its own: it loads a chunk of CH
-    // entries (the next one is prefetched while the current one is used),
-    // keeps those whose alpha box meets its band, compacts them in order into
-    // its shared-memory slot and composites them
+    unsigned evals = 0;  // composited (pixel, Gaussian) pairs
     Entry nx[PER];
 #pragma unroll
     for (int p = 0; p < PER; p++) load_entry(nx[p], p * 32 + lane < n, vals, range.x + p * 32 + lane, rec0, splat, col);
@@ -171,41 +255,27 @@ k_render_fwd(const gs_frame *__restrict__ frames, int F, const uint32_t *__restr
                 load_entry(nx[p], i < n, vals, range.x + i, rec0, splat, col);
             }
         }
-        int cnt = 0;
-#pragma unroll
-        for (int p = 0; p < PER; p++) {
-            const bool hit = cu[p].valid && box_hits(cu[p].a, make_float2(cu[p].b.z, cu[p].b.w), xlo, xhi, ylo, yhi);
-            const uint32_t msk = __ballot_sync(0xffffffffu, hit);
-            if (hit) {
-                const int at = cnt + __popc(msk & lt_mask);
-                s0[warp][at] = cu[p].a;
-                s1[warp][at] = make_float4(cu[p].b.x, cu[p].b.y, cu[p].cr, cu[p].cg);
-                s2[warp][at] = cu[p].cb;
-                spos[warp][at] = cb0 + p * 32 + lane;
-            }
-            cnt += __popc(msk);
-        }
-        __syncwarp();
+        const int cnt = compact<PER>(st, cu, cb0, lane, rp.lmin, xlo, xhi, ylo, yhi);
         for (int j = 0; j < cnt; j++) {
-            const float4 a = s0[warp][j], b = s1[warp][j];
-            const float cb = s2[warp][j];
-            const int pos = spos[warp][j];
+            const float4 a = st[j].a, b = st[j].b;
             // every lane evaluates the exponent; one warp vote decides
             // whether any pixel composites this Gaussian, and the
             // compositing itself runs predicated (no divergence)
+            const float dx = px - a.x;
             float e[PPT];
             bool ct[PPT];
             bool anyc = false;
 #pragma unroll
             for (int k = 0; k < PPT; k++) {
-                evals += !done[k];
-                const float dx = px[k] - a.x, dy = py[k] - a.y;
-                const float e2 = exponent2(dx, dy, a.z, a.w, b.x);
+                const float e2 = exponent2(dx, py[k] - a.y, a.z, a.w, b.x);
                 e[k] = e2 + b.y;
                 ct[k] = !done[k] && !(e2 > 0.f) && !(e[k] < rp.lmin);
                 anyc |= ct[k];
             }
             if (!__any_sync(0xffffffffu, anyc)) continue;
+            const uint4 z = st[j].z;
+            const float cb = __uint_as_float(z.x);
+            const int pos1 = (int)z.y + 1;
 #pragma unroll
             for (int k = 0; k < PPT; k++) {
                 const float alpha = fminf(rp.amax, ex2_approx(e[k]));
@@ -213,35 +283,57 @@ k_render_fwd(const gs_frame *__restrict__ frames, int F, const uint32_t *__restr
                 const bool stop = ct[k] && nT < rp.tmin;
                 const bool blend = ct[k] && !stop;
                 done[k] = done[k] || stop;
+                evals += blend;
                 const float w = blend ? alpha * T[k] : 0.f;
                 c0[k] = fmaf(b.z, w, c0[k]);
                 c1[k] = fmaf(b.w, w, c1[k]);
                 c2[k] = fmaf(cb, w, c2[k]);
                 T[k] = blend ? nT : T[k];
-                last[k] = blend ? pos + 1 : last[k];
+                last[k] = blend ? pos1 : last[k];
             }
         }
         __syncwarp();
     }
 #pragma unroll
     for (int k = 0; k < PPT; k++) {
-        if (!inside[k]) continue;
-        int lx, ly;
-        pixel_of<TILE>(threadIdx.x, k, lx, ly);
-        const long long pix = fr.pixel_offset + (long long)(ty * TILE + ly) * W + (tx * TILE + lx);
+        const int v = v0 + k;
+        if (!(u < W && v < H)) continue;
+        const long long pix = fr.pixel_offset + (long long)v * W + u;
         out_rgb[3 * pix] = c0[k] + T[k] * rp.bg0;
         out_rgb[3 * pix + 1] = c1[k] + T[k] * rp.bg1;
         out_rgb[3 * pix + 2] = c2[k] + T[k] * rp.bg2;
         out_T[pix] = T[k];
         out_last[pix] = last[k];
     }
-    // evaluation counter (for the roofline): warp sums, one atomic per warp
+    // composited-pair counter (the roofline's unit): warp sums, one atomic per warp
     unsigned long long ev = evals;
     for (int s = 16; s > 0; s >>= 1) ev += __shfl_xor_sync(0xffffffffu, ev, s);
     __syncthreads();
     if (lane == 0) atomicAdd(&s_eval, ev);
     __syncthreads();
     if (threadIdx.x == 0) atomicAdd(&stats->eval_fwd, s_eval);
+}
+
+// Work item i of a launch: the halves of the `heavy` first tiles of the
+// heavy-first order, then the other tiles whole.
+template <int TILE, int BATCH>
+__global__ void __launch_bounds__(Threads<TILE>::NT)
+k_render_fwd(const gs_frame *__restrict__ frames, int F, const uint32_t *__restrict__ order, int heavy,
+             const uint2 *__restrict__ ranges, const uint32_t *__restrict__ vals,
+             const float4 *__restrict__ splat, const float *__restrict__ colors, RenderParams rp,
+             Stats *__restrict__ stats, float *__restrict__ out_rgb, float *__restrict__ out_T,
+             int32_t *__restrict__ out_last) {
+    constexpr int NT = Threads<TILE>::NT, PL = pix_per_thread(TILE);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ unsigned long long s_eval;
+    Staged *st = reinterpret_cast<Staged *>(smem_raw);
+    const int i = (int)blockIdx.x;
+    if (i < 2 * heavy)
+        fwd_item<TILE, PL / 2, NT, BATCH>((int)order[i >> 1], (i & 1) * (TILE / 2), st, s_eval, frames, F, ranges,
+                                          vals, splat, colors, rp, stats, out_rgb, out_T, out_last);
+    else
+        fwd_item<TILE, PL, NT, BATCH>((int)order[i - heavy], 0, st, s_eval, frames, F, ranges, vals, splat, colors,
+                                      rp, stats, out_rgb, out_T, out_last);
 }
 
 __device__ __forceinline__ float warp_sum_f(float v) {
@@ -253,7 +345,7 @@ __device__ __forceinline__ float warp_sum_f(float v) {
 // a lane keeps half of its values and sends the other half to its partner,
 // so the exchanges shrink 4, 2, 1, 1, 1 (8 shuffles instead of 40).  On
 // return every lane holds the warp total of component
-// c = 4*bit4(lane) + 2*bit3(lane) + bit2(lane).
+// c = 4*bit4(lane) + 2*bit3(lane) + bit2(lane) = lane >> 2.
 __device__ __forceinline__ float warp_sum8_transposed(const float (&v)[8], int lane) {
     const bool u16 = lane & 16, u8 = lane & 8, u4 = lane & 4;
     float w[4];
@@ -277,61 +369,52 @@ __device__ __forceinline__ float warp_sum8_transposed(const float (&v)[8], int l
     return y;
 }
 
-template <int TILE, int BATCH>
-__global__ void __launch_bounds__(Cfg<TILE>::NT)
-k_render_bwd(const gs_frame *__restrict__ frames, int F, const uint32_t *__restrict__ order,
-             const uint2 *__restrict__ ranges, const uint32_t *__restrict__ vals,
-             const float4 *__restrict__ splat, const float *__restrict__ colors, RenderParams rp,
-             Stats *__restrict__ stats, const float *__restrict__ in_T, const int32_t *__restrict__ in_last,
-             const float *__restrict__ dL_drgb, float4 *__restrict__ grad2d) {
-    constexpr int NT = Cfg<TILE>::NT, PPT = Cfg<TILE>::PPT, RPW = Cfg<TILE>::RPW;
-    constexpr int NW = NT / 32, CH = BATCH / 2, PER = CH / 32;
-    __shared__ float4 s0[NW][CH];
-    __shared__ float4 s1[NW][CH];
-    __shared__ float s2[NW][CH];
-    __shared__ int spos[NW][CH];
-    __shared__ uint32_t sg[NW][CH];
-    __shared__ unsigned long long s_eval;
-    const int t = (int)order[blockIdx.x];  // heavy tiles first
+// Backward of one work item: rows [row0, row0 + ROWS) of tile t.
+template <int TILE, int PPT, int NT, int BATCH>
+__device__ __forceinline__ void bwd_item(int t, int row0, Staged *st_all, unsigned long long &s_eval,
+                                         const gs_frame *__restrict__ frames, int F,
+                                         const uint2 *__restrict__ ranges, const uint32_t *__restrict__ vals,
+                                         const float4 *__restrict__ splat, const float *__restrict__ colors,
+                                         const RenderParams &rp, Stats *__restrict__ stats,
+                                         const float *__restrict__ in_T, const int32_t *__restrict__ in_last,
+                                         const float *__restrict__ dL_drgb, float4 *__restrict__ grad2d) {
+    constexpr int RPW = Cfg<TILE, PPT, NT>::RPW, CH = BATCH / 2, PER = CH / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    Staged *st = st_all + warp * CH;
     const int f = frame_of_tile(frames, F, t);
     const gs_frame &fr = frames[f];
     const int W = fr.width, H = fr.height;
     const int lt = t - fr.tile_offset;
     const int tx = lt % fr.tiles_x, ty = lt / fr.tiles_x;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint32_t lt_mask = (1u << lane) - 1u;
-    const float xlo = (float)(tx * TILE), xhi = xlo + (float)(TILE - 1);
-    const float ylo = (float)(ty * TILE + warp * RPW), yhi = ylo + (float)(RPW - 1);
-    float px[PPT], py[PPT], T[PPT], Tf[PPT], g0[PPT], g1[PPT], g2[PPT], bgd[PPT];
-    float a0[PPT], a1[PPT], a2[PPT];
-    int last[PPT];
+    float xlo, xhi, ylo, yhi;
+    band_of<TILE, RPW>(tx, ty, row0, warp, W, H, xlo, xhi, ylo, yhi);
+    const int u = tx * TILE + (int)threadIdx.x % TILE;
+    const int v0 = ty * TILE + row0 + ((int)threadIdx.x / TILE) * PPT;
+    const float px = (float)u;
     if (threadIdx.x == 0) s_eval = 0;
     // the range of this tile; a pixel's start position never exceeds it
     const uint2 range = ranges[t];
     const int n = (int)(range.y - range.x);
+    float py[PPT], T[PPT], S[PPT], g0[PPT], g1[PPT], g2[PPT];
+    int last[PPT];
     int mylast = 0;
 #pragma unroll
     for (int k = 0; k < PPT; k++) {
-        int lx, ly;
-        pixel_of<TILE>(threadIdx.x, k, lx, ly);
-        const int u = tx * TILE + lx, v = ty * TILE + ly;
-        px[k] = (float)u;
+        const int v = v0 + k;
         py[k] = (float)v;
-        a0[k] = a1[k] = a2[k] = 0.f;
         if (u < W && v < H) {
             const long long pix = fr.pixel_offset + (long long)v * W + u;
-            Tf[k] = in_T[pix];
+            T[k] = in_T[pix];
             last[k] = min(max(in_last[pix], 0), n);
             g0[k] = dL_drgb[3 * pix];
             g1[k] = dL_drgb[3 * pix + 1];
             g2[k] = dL_drgb[3 * pix + 2];
         } else {
-            Tf[k] = 1.f;
+            T[k] = 1.f;
             last[k] = 0;
             g0[k] = g1[k] = g2[k] = 0.f;
         }
-        T[k] = Tf[k];
-        bgd[k] = rp.bg0 * g0[k] + rp.bg1 * g1[k] + rp.bg2 * g2[k];
+        S[k] = T[k] * (rp.bg0 * g0[k] + rp.bg1 * g1[k] + rp.bg2 * g2[k]);
         mylast = max(mylast, last[k]);
     }
     // each warp walks its own part of the list backwards, from the largest
@@ -339,7 +422,7 @@ k_render_bwd(const gs_frame *__restrict__ frames, int F, const uint32_t *__restr
     const int warp_last = __reduce_max_sync(0xffffffffu, mylast);
     const long long rec0 = fr.record_offset;
     const float *col = colors + 3 * (size_t)fr.gauss_offset;
-    unsigned evals = 0;
+    unsigned evals = 0;  // composited (pixel, Gaussian) pairs
     Entry nx[PER];
     {
         const int c0 = max(0, warp_last - CH);
@@ -362,76 +445,68 @@ k_render_bwd(const gs_frame *__restrict__ frames, int F, const uint32_t *__restr
                 load_entry(nx[p], i < c0, vals, range.x + i, rec0, splat, col);
             }
         }
-        int cnt = 0;
-#pragma unroll
-        for (int p = 0; p < PER; p++) {
-            const bool hit = cu[p].valid && box_hits(cu[p].a, make_float2(cu[p].b.z, cu[p].b.w), xlo, xhi, ylo, yhi);
-            const uint32_t msk = __ballot_sync(0xffffffffu, hit);
-            if (hit) {
-                const int at = cnt + __popc(msk & lt_mask);
-                s0[warp][at] = cu[p].a;
-                s1[warp][at] = make_float4(cu[p].b.x, cu[p].b.y, cu[p].cr, cu[p].cg);
-                s2[warp][at] = cu[p].cb;
-                spos[warp][at] = c0 + p * 32 + lane;
-                sg[warp][at] = cu[p].g;
-            }
-            cnt += __popc(msk);
-        }
-        __syncwarp();
+        const int cnt = compact<PER>(st, cu, c0, lane, rp.lmin, xlo, xhi, ylo, yhi);
         for (int j = cnt - 1; j >= 0; j--) {
-            const float4 a = s0[warp][j], b = s1[warp][j];
-            const float cb = s2[warp][j];
-            const int pos = spos[warp][j];
+            const float4 a = st[j].a, b = st[j].b;
+            const uint4 z = st[j].z;  // b, pos, g
+            const int pos = (int)z.y;
             // every lane evaluates the exponent; one warp vote decides
             // whether any pixel composited this Gaussian; the gradient
             // math then runs predicated (zero where a pixel did not)
-            float e[PPT], dxs[PPT], dys[PPT];
+            const float dx = px - a.x;
+            float e[PPT], dy[PPT];
             bool ct[PPT];
             bool anyc = false;
 #pragma unroll
             for (int k = 0; k < PPT; k++) {
-                const bool act = pos < last[k];
-                evals += act;
-                dxs[k] = px[k] - a.x;
-                dys[k] = py[k] - a.y;
-                const float e2 = exponent2(dxs[k], dys[k], a.z, a.w, b.x);
+                dy[k] = py[k] - a.y;
+                const float e2 = exponent2(dx, dy[k], a.z, a.w, b.x);
                 e[k] = e2 + b.y;
-                ct[k] = act && !(e2 > 0.f) && !(e[k] < rp.lmin);
+                ct[k] = pos < last[k] && !(e2 > 0.f) && !(e[k] < rp.lmin);
                 anyc |= ct[k];
             }
             if (!__any_sync(0xffffffffu, anyc)) continue;
-            float dmx = 0.f, dmy = 0.f, dA = 0.f, dB = 0.f, dC = 0.f, dF = 0.f, dr = 0.f, dg = 0.f, db = 0.f;
+            const float cb = __uint_as_float(z.x);
+            // per-thread sums: sum de dx, sum de dy, dA, dB, dC, dF, dr, dg, db
+            float sx = 0.f, sy = 0.f, dA = 0.f, dB = 0.f, dC = 0.f, dF = 0.f, dr = 0.f, dg = 0.f, db = 0.f;
 #pragma unroll
             for (int k = 0; k < PPT; k++) {
-                const float G = ex2_approx(e[k]);
-                const float alpha = ct[k] ? fminf(rp.amax, G) : 0.f;
-                const float inv = rcp_approx(1.f - alpha);
-                T[k] = ct[k] ? T[k] * inv : T[k];  // T before this Gaussian
+                // a pixel that does not composite this Gaussian gets alpha = 0
+                // (2^-inf), so every term below vanishes for it
+                const float G = ex2_approx(ct[k] ? e[k] : -INFINITY);
+                const float alpha = fminf(rp.amax, G);
+                const float inv = ct[k] ? rcp_approx(1.f - alpha) : 1.f;
+                T[k] *= inv;  // T before this Gaussian
                 const float w = alpha * T[k];
                 dr = fmaf(w, g0[k], dr);
                 dg = fmaf(w, g1[k], dg);
                 db = fmaf(w, g2[k], db);
-                const float dalpha = T[k] * ((b.z - a0[k]) * g0[k] + (b.w - a1[k]) * g1[k] + (cb - a2[k]) * g2[k]) -
-                                     Tf[k] * bgd[k] * inv;
-                a0[k] = fmaf(alpha, b.z - a0[k], a0[k]);
-                a1[k] = fmaf(alpha, b.w - a1[k], a1[k]);
-                a2[k] = fmaf(alpha, cb - a2[k], a2[k]);
-                const float de = (ct[k] && !(G > rp.amax)) ? dalpha * alpha * kLn2 : 0.f;
-                const float dx = dxs[k], dy = dys[k];
+                const float cd = fmaf(b.z, g0[k], fmaf(b.w, g1[k], cb * g2[k]));
+                const float dal = T[k] * cd - S[k] * inv;
+                S[k] = fmaf(w, cd, S[k]);
+                const float de = G > rp.amax ? 0.f : dal * alpha;  // dL/de / ln 2
+                const float tx_ = de * dx, ty_ = de * dy[k];
+                dA = fmaf(tx_, dx, dA);
+                dB = fmaf(tx_, dy[k], dB);
+                dC = fmaf(ty_, dy[k], dC);
+                sx += tx_;
+                sy += ty_;
                 dF += de;
-                dA = fmaf(de * dx, dx, dA);
-                dB = fmaf(de * dx, dy, dB);
-                dC = fmaf(de * dy, dy, dC);
-                dmx -= de * (2.f * a.z * dx + a.w * dy);
-                dmy -= de * (a.w * dx + 2.f * b.x * dy);
+                evals += ct[k];
             }
             // record layout: (dmx, dmy, dA, dB), (dC, dF, dr, dg), (db, -, -, -)
-            const float v8[8] = {dmx, dmy, dA, dB, dC, dF, dr, dg};
+            const float v8[8] = {sx, sy, dA, dB, dC, dF, dr, dg};
             const float tot = warp_sum8_transposed(v8, lane);
-            db = warp_sum_f(db);
-            float *rec = reinterpret_cast<float *>(grad2d + 3 * (rec0 + sg[warp][j]));
-            if ((lane & 3) == 0) atomicAdd(rec + (lane >> 2), tot);
-            if (lane == 0) atomicAdd(rec + 8, db);
+            const float dbt = warp_sum_f(db);
+            // lanes 0-3 hold sum de dx and lanes 4-7 sum de dy: the mean gradient
+            const float oth = __shfl_xor_sync(0xffffffffu, tot, 4);
+            const int comp = lane >> 2;
+            float val = comp < 6 ? tot * kLn2 : tot;
+            val = comp == 0 ? -kLn2 * (2.f * a.z * tot + a.w * oth) : val;
+            val = comp == 1 ? -kLn2 * (a.w * oth + 2.f * b.x * tot) : val;
+            float *rec = reinterpret_cast<float *>(grad2d + 3 * (rec0 + z.z));
+            if ((lane & 3) == 0) atomicAdd(rec + comp, val);
+            if (lane == 0) atomicAdd(rec + 8, dbt);
         }
         __syncwarp();
     }
@@ -444,22 +519,77 @@ k_render_bwd(const gs_frame *__restrict__ frames, int F, const uint32_t *__restr
 }
 
 template <int TILE, int BATCH>
+__global__ void __launch_bounds__(Threads<TILE>::NT)
+k_render_bwd(const gs_frame *__restrict__ frames, int F, const uint32_t *__restrict__ order, int heavy,
+             const uint2 *__restrict__ ranges, const uint32_t *__restrict__ vals,
+             const float4 *__restrict__ splat, const float *__restrict__ colors, RenderParams rp,
+             Stats *__restrict__ stats, const float *__restrict__ in_T, const int32_t *__restrict__ in_last,
+             const float *__restrict__ dL_drgb, float4 *__restrict__ grad2d) {
+    constexpr int NT = Threads<TILE>::NT, PL = pix_per_thread(TILE);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ unsigned long long s_eval;
+    Staged *st = reinterpret_cast<Staged *>(smem_raw);
+    const int i = (int)blockIdx.x;
+    if (i < 2 * heavy)
+        bwd_item<TILE, PL / 2, NT, BATCH>((int)order[i >> 1], (i & 1) * (TILE / 2), st, s_eval, frames, F, ranges,
+                                          vals, splat, colors, rp, stats, in_T, in_last, dL_drgb, grad2d);
+    else
+        bwd_item<TILE, PL, NT, BATCH>((int)order[i - heavy], 0, st, s_eval, frames, F, ranges, vals, splat, colors,
+                                      rp, stats, in_T, in_last, dL_drgb, grad2d);
+}
+
+// ---------------------------------------------------------------- launch
+
+// Heavy tiles split in halves: two per SM, at most a quarter of the tiles.
+int heavy_tiles(long long num_tiles) {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                   cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return (int)std::min<long long>(num_tiles / 4, 2ll * sms);
+}
+
+// Dynamic shared memory of a render kernel (the warps' staging slots), with
+// the opt-in for more than the default 48 KB per block (static shared memory
+// included) set before each launch that needs it (a per-device function
+// attribute; cheap and legal while capturing).
+template <typename K>
+cudaError_t smem_opt_in(K kern, size_t bytes) {
+    if (bytes + 1024 <= 48 * 1024) return cudaSuccess;
+    return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <int TILE, int BATCH>
+constexpr size_t stage_bytes() {
+    return (size_t)(Threads<TILE>::NT / 32) * (BATCH / 2) * sizeof(Staged);
+}
+
+template <int TILE, int BATCH>
 cudaError_t run_fwd(const gs_batch *b, const uint32_t *order, const uint2 *ranges, const uint32_t *vals,
-                    const float4 *splat,
-                    const float *colors, RenderParams rp, Stats *stats, float *out_rgb, float *out_T,
-                    int32_t *out_last, cudaStream_t s) {
-    k_render_fwd<TILE, BATCH><<<b->num_tiles, Cfg<TILE>::NT, 0, s>>>(
-        b->frames_dev, b->num_frames, order, ranges, vals, splat, colors, rp, stats, out_rgb, out_T, out_last);
+                    const float4 *splat, const float *colors, RenderParams rp, Stats *stats, float *out_rgb,
+                    float *out_T, int32_t *out_last, cudaStream_t s) {
+    constexpr size_t smem = stage_bytes<TILE, BATCH>();
+    const int heavy = heavy_tiles(b->num_tiles);
+    cudaError_t e = smem_opt_in(k_render_fwd<TILE, BATCH>, smem);
+    if (e != cudaSuccess) return e;
+    k_render_fwd<TILE, BATCH><<<(unsigned)(b->num_tiles + heavy), Threads<TILE>::NT, smem, s>>>(
+        b->frames_dev, b->num_frames, order, heavy, ranges, vals, splat, colors, rp, stats, out_rgb, out_T, out_last);
     return cudaGetLastError();
 }
 
 template <int TILE, int BATCH>
 cudaError_t run_bwd(const gs_batch *b, const uint32_t *order, const uint2 *ranges, const uint32_t *vals,
-                    const float4 *splat,
-                    const float *colors, RenderParams rp, Stats *stats, const float *in_T, const int32_t *in_last,
-                    const float *dL, float4 *grad2d, cudaStream_t s) {
-    k_render_bwd<TILE, BATCH><<<b->num_tiles, Cfg<TILE>::NT, 0, s>>>(
-        b->frames_dev, b->num_frames, order, ranges, vals, splat, colors, rp, stats, in_T, in_last, dL, grad2d);
+                    const float4 *splat, const float *colors, RenderParams rp, Stats *stats, const float *in_T,
+                    const int32_t *in_last, const float *dL, float4 *grad2d, cudaStream_t s) {
+    constexpr size_t smem = stage_bytes<TILE, BATCH>();
+    const int heavy = heavy_tiles(b->num_tiles);
+    cudaError_t e = smem_opt_in(k_render_bwd<TILE, BATCH>, smem);
+    if (e != cudaSuccess) return e;
+    k_render_bwd<TILE, BATCH><<<(unsigned)(b->num_tiles + heavy), Threads<TILE>::NT, smem, s>>>(
+        b->frames_dev, b->num_frames, order, heavy, ranges, vals, splat, colors, rp, stats, in_T, in_last, dL,
+        grad2d);
     return cudaGetLastError();
 }
 
