@@ -161,7 +161,8 @@ size_t gs_workspace_size(const gs_batch *batch);
  * base-2 exponent log2 alpha = A dx^2 + B dx dy + C dy^2 + F and the
  * half-widths of the box outside which alpha < alpha_min), [6] grad2d
  * (float4[R][3]: d/d(mean_x, mean_y, A, B), d/d(C, F, r, g), d/d(b)), [7] keys
- * (uint64[pair_capacity]), [8] vals (uint32[pair_capacity]), [9] ranges
+ * (uint32[pair_capacity]: the global tile of each sorted pair), [8] vals
+ * (uint32[pair_capacity]: Gaussian index within its scene), [9] ranges
  * (uint32[T][2]: [start, end) of each tile in keys/vals).  Returns the
  * number of offsets written (<= max_entries). */
 int32_t gs_workspace_offsets(const gs_batch *batch, size_t *offsets, int32_t max_entries);
@@ -228,10 +229,11 @@ gs_status gs_project(const gs_batch *batch, const float *X, const float *quat,
                      void *ws_dev, void *stream);
 
 /* Tile binning and depth ordering for Phi (Eq. 5): every record emits one
- * pair per tile of its rectangle, key = (global tile << 32) | float bits of
- * the depth, value = Gaussian index within its scene; the pairs are sorted
- * by key with a stable LSD radix sort (equal keys keep record order), and
- * each tile's [start, end) range is found.  If the pairs exceed
+ * pair per tile of its rectangle, value = Gaussian index within its scene;
+ * the pairs end up in the order of the key (global tile << 32) | float bits
+ * of the depth, equal keys in record order (a stable sort), and each tile's
+ * [start, end) range is found.  The workspace keys region holds each sorted
+ * pair's global tile (the high half of that key).  If the pairs exceed
  * pair_capacity, GS_DEV_PAIR_OVERFLOW is set and the batch is treated as
  * having no pairs. */
 gs_status gs_bin_sort(const gs_batch *batch, const gs_opts *opts, void *ws_dev, void *stream);
@@ -299,8 +301,10 @@ gs_status gs_pose_grad(const gs_batch *batch, const double *ext, void *ws_dev, d
  * acceptable.  Such a caller cannot provide the workspace gs_bin_sort needs.
  * The paper has no counterpart; it is a deployment convenience.
  *
- * Results are the same as gs_bin_sort's, bit for bit; the inputs and
- * outputs are the caller's buffers instead of workspace regions:
+ * vals and ranges are the same as gs_bin_sort's, bit for bit, and keys are
+ * the full 64-bit keys (global tile << 32 | float bits of the depth) whose
+ * high halves are gs_bin_sort's workspace keys; the inputs and outputs are
+ * the caller's buffers instead of workspace regions:
  *   rect[R][2]   uint32 rectangles (x0 | y0 << 16, x1 | y1 << 16, inclusive
  *                tiles; empty when x0 > x1), R = batch->num_records
  *   depth[R]     float camera depths (the key's low 32 bits)

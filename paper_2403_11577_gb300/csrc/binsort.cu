@@ -1,22 +1,25 @@
 // Tile binning and depth ordering for Phi (Eq. 5).
 //
 // The pairs must end up ordered by (global tile, depth, Gaussian index):
-// key = (global tile << 32) | float bits of the depth, value = Gaussian index
-// within its scene, stable in record order.  gs_bin_sort gets there in two
-// cheap stages instead of one wide sort:
+// the order of the 64-bit key (global tile << 32) | float bits of the depth,
+// value = Gaussian index within its scene, stable in record order.
+// gs_bin_sort gets there in two cheap stages instead of one wide sort, with
+// 32-bit keys throughout:
 // 1. k_rec_keys + 4 LSD passes over the per-(frame, Gaussian) records keyed
-//    by their 32-bit depth (culled records last): a stable depth order of the
-//    records (ties keep record order).
+//    by the float bits of their depth (culled records last): a stable depth
+//    order of the records (ties keep record order).
 // 2. k_pair_count / k_pair_scan / k_pair_emit over the records in that
 //    order: every record emits one pair per tile of its rectangle (emission
 //    is cooperative: threads stride over the block's output range and find
 //    their record by binary search).  The pairs are thus already in
-//    (depth, record) order.
-// 3. LSD passes over the tile bits only (2 for up to 65,536 tiles): a stable
-//    sort by tile keeps the depth order inside each tile, so the result is
-//    the full-key order bit for bit, with about a third of the traffic.
+//    (depth, record) order; their key is the global tile alone.
+// 3. LSD passes over the tile id (2 for up to 65,536 tiles): a stable sort
+//    by tile keeps the depth order inside each tile, so the result is the
+//    full-key order bit for bit, with a fraction of the traffic.
 // 4. k_tile_ranges: [start, end) of every tile; k_tile_order: the tiles
 //    sorted heavy-first for the render kernels.
+// gs_bin_sort_noalloc sorts 64-bit full keys over all their bits instead
+// (one stage, no record buffers).
 // Each radix pass: k_radix_hist (per-block digit counts) -> k_radix_colscan
 // (per-digit prefix over blocks, digit totals) -> k_radix_scatter (stable:
 // per-warp ranking with match_any in index order, per-tile prefix over
@@ -52,12 +55,11 @@ __device__ __forceinline__ unsigned long long block_sum_u64(unsigned long long v
 // (ordered like the depths, which are positive), culled records last; the
 // value is the record index.  Also stores the record count for the sort.
 __global__ void k_rec_keys(const uint2 *__restrict__ rect, const float *__restrict__ depth, long long R,
-                           unsigned long long *__restrict__ keys, uint32_t *__restrict__ vals,
-                           Stats *__restrict__ stats) {
+                           uint32_t *__restrict__ keys, uint32_t *__restrict__ vals, Stats *__restrict__ stats) {
     const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (r == 0) stats->num_records = (unsigned long long)R;
     if (r >= R) return;
-    keys[r] = rect_count(rect[r]) ? (unsigned long long)__float_as_uint(depth[r]) : 0xffffffffull;
+    keys[r] = rect_count(rect[r]) ? __float_as_uint(depth[r]) : 0xffffffffu;
     vals[r] = (uint32_t)r;
 }
 
@@ -117,11 +119,27 @@ k_pair_scan(unsigned long long *__restrict__ sums, int nb, long long capacity, S
     }
 }
 
+// Key of a pair: the global tile (K = uint32_t, pairs emitted in depth order)
+// or (global tile << 32) | depth bits (K = unsigned long long, full key).
+template <typename K>
+__device__ __forceinline__ K pair_key(uint32_t tile, uint32_t depth_bits);
+template <>
+__device__ __forceinline__ uint32_t pair_key<uint32_t>(uint32_t tile, uint32_t) { return tile; }
+template <>
+__device__ __forceinline__ unsigned long long pair_key<unsigned long long>(uint32_t tile, uint32_t depth_bits) {
+    return ((unsigned long long)tile << 32) | depth_bits;
+}
+
+// Global tile of a sorted key.
+__device__ __forceinline__ uint32_t key_tile(uint32_t k) { return k; }
+__device__ __forceinline__ uint32_t key_tile(unsigned long long k) { return (uint32_t)(k >> 32); }
+
+template <typename K>
 __global__ void __launch_bounds__(kEmitThreads)
 k_pair_emit(const gs_frame *__restrict__ frames, int F, const uint2 *__restrict__ rect,
             const float *__restrict__ depth, long long R, const uint32_t *__restrict__ perm,
-            const unsigned long long *__restrict__ sums, const Stats *__restrict__ stats,
-            unsigned long long *__restrict__ keys, uint32_t *__restrict__ vals) {
+            const unsigned long long *__restrict__ sums, const Stats *__restrict__ stats, K *__restrict__ keys,
+            uint32_t *__restrict__ vals) {
     __shared__ unsigned long long off[kEmitItems + 1];
     __shared__ uint32_t s_tile0[kEmitItems];   // global tile of the rect's first tile
     __shared__ uint32_t s_w[kEmitItems];       // rect width in tiles
@@ -186,7 +204,7 @@ k_pair_emit(const gs_frame *__restrict__ frames, int F, const uint2 *__restrict_
         const uint32_t k = (uint32_t)(o - off[lo]);
         const uint32_t w = s_w[lo];
         const uint32_t tile = s_tile0[lo] + (k / w) * s_stride[lo] + (k % w);
-        keys[gbase + o] = ((unsigned long long)tile << 32) | s_bits[lo];
+        keys[gbase + o] = pair_key<K>(tile, s_bits[lo]);
         vals[gbase + o] = s_val[lo];
     }
 }
@@ -203,9 +221,10 @@ __device__ __forceinline__ Chunk sort_chunk(unsigned long long P, int nb, int b)
     return {lo, hi};
 }
 
+template <typename K>
 __global__ void __launch_bounds__(kSortThreads)
-k_radix_hist(const unsigned long long *__restrict__ keys, const unsigned long long *__restrict__ count, int shift,
-             int nb, uint32_t *__restrict__ hist) {
+k_radix_hist(const K *__restrict__ keys, const unsigned long long *__restrict__ count, int shift, int nb,
+             uint32_t *__restrict__ hist) {
     __shared__ uint32_t h[kSortThreads / 32][kRadix];
     const int warp = threadIdx.x >> 5;
     for (int i = threadIdx.x; i < (kSortThreads / 32) * kRadix; i += kSortThreads) (&h[0][0])[i] = 0;
@@ -248,8 +267,9 @@ k_radix_colscan(uint32_t *__restrict__ hist, int nb, uint32_t *__restrict__ tota
 
 constexpr int kWarps = kSortThreads / 32;
 
+template <typename K>
 struct ScatterSmem {
-    unsigned long long skey[kSortTile];
+    K skey[kSortTile];
     uint32_t sval[kSortTile];
     uint32_t wcnt[kWarps][kRadix];   // per-warp digit counts, then exclusive prefix over warps
     uint32_t tcnt[kRadix];           // digit counts of the tile
@@ -258,13 +278,13 @@ struct ScatterSmem {
     uint32_t wtot[kRadix / 32];
 };
 
+template <typename K>
 __global__ void __launch_bounds__(kSortThreads, 2)
-k_radix_scatter(const unsigned long long *__restrict__ kin, const uint32_t *__restrict__ vin,
-                unsigned long long *__restrict__ kout, uint32_t *__restrict__ vout,
-                const unsigned long long *__restrict__ count, int shift, int nb, const uint32_t *__restrict__ hist,
-                const uint32_t *__restrict__ totals) {
+k_radix_scatter(const K *__restrict__ kin, const uint32_t *__restrict__ vin, K *__restrict__ kout,
+                uint32_t *__restrict__ vout, const unsigned long long *__restrict__ count, int shift, int nb,
+                const uint32_t *__restrict__ hist, const uint32_t *__restrict__ totals) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    ScatterSmem &S = *reinterpret_cast<ScatterSmem *>(smem_raw);
+    ScatterSmem<K> &S = *reinterpret_cast<ScatterSmem<K> *>(smem_raw);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const Chunk c = sort_chunk(*count, nb, blockIdx.x);
     // run[d] = (items of digits < d) + (items of digit d in earlier blocks)
@@ -289,14 +309,14 @@ k_radix_scatter(const unsigned long long *__restrict__ kin, const uint32_t *__re
     for (long long t0 = c.lo; t0 < c.hi; t0 += kSortTile) {
         for (int i = lane; i < kRadix; i += 32) S.wcnt[warp][i] = 0;
         __syncwarp();
-        unsigned long long k[kSortItems];
+        K k[kSortItems];
         uint32_t v[kSortItems], dg[kSortItems], rk[kSortItems];
         // warp w owns items [w*32*ITEMS, (w+1)*32*ITEMS) of the tile, in index order
 #pragma unroll
         for (int r = 0; r < kSortItems; r++) {
             const long long idx = t0 + (long long)warp * 32 * kSortItems + r * 32 + lane;
             const bool valid = idx < c.hi;
-            k[r] = valid ? kin[idx] : 0ull;
+            k[r] = valid ? kin[idx] : K(0);
             v[r] = valid ? vin[idx] : 0u;
             const uint32_t d = (uint32_t)(k[r] >> shift) & (kRadix - 1);
             dg[r] = valid ? d : kRadix;  // kRadix marks an empty slot
@@ -351,7 +371,7 @@ k_radix_scatter(const unsigned long long *__restrict__ kin, const uint32_t *__re
         __syncthreads();
         const int n = (int)min((long long)kSortTile, c.hi - t0);
         for (int i = threadIdx.x; i < n; i += kSortThreads) {
-            const unsigned long long key = S.skey[i];
+            const K key = S.skey[i];
             const uint32_t d = (uint32_t)(key >> shift) & (kRadix - 1);
             const uint32_t pos = S.run[d] + (uint32_t)i - S.tstart[d];
             kout[pos] = key;
@@ -363,14 +383,15 @@ k_radix_scatter(const unsigned long long *__restrict__ kin, const uint32_t *__re
     }
 }
 
-__global__ void k_tile_ranges(const unsigned long long *__restrict__ keys, const unsigned long long *__restrict__ count,
+template <typename K>
+__global__ void k_tile_ranges(const K *__restrict__ keys, const unsigned long long *__restrict__ count,
                               uint2 *__restrict__ ranges) {
     const long long P = (long long)*count;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < P;
          i += (long long)gridDim.x * blockDim.x) {
-        const uint32_t t = (uint32_t)(keys[i] >> 32);
-        if (i == 0 || (uint32_t)(keys[i - 1] >> 32) != t) ranges[t].x = (uint32_t)i;
-        if (i == P - 1 || (uint32_t)(keys[i + 1] >> 32) != t) ranges[t].y = (uint32_t)(i + 1);
+        const uint32_t t = key_tile(keys[i]);
+        if (i == 0 || key_tile(keys[i - 1]) != t) ranges[t].x = (uint32_t)i;
+        if (i == P - 1 || key_tile(keys[i + 1]) != t) ranges[t].y = (uint32_t)(i + 1);
     }
 }
 
@@ -418,34 +439,35 @@ k_tile_order(const uint2 *__restrict__ ranges, int T, uint32_t *__restrict__ ord
 
 }  // namespace
 
-// Radix passes over the tile bits of the pair keys (the depth order comes
-// from the record sort).
+// Radix passes over the tile id (the depth order comes from the record sort).
 int radix_passes(int num_tiles) {
     int tb = 0;
     while ((1ll << tb) < (long long)num_tiles) tb++;
     return (tb + kRadixBits - 1) / kRadixBits;
 }
 
-// Passes of a sort over the full 64-bit pair key (tile and depth bits).
+// Passes of a sort over the full 64-bit pair key (depth bits, then tile bits).
 int full_key_passes(int num_tiles) { return radix_passes(num_tiles) + 32 / kRadixBits; }
 
 
 namespace {
 
 // One LSD pass (histogram, column scan, scatter) over *count items.
-cudaError_t radix_pass(const unsigned long long *kin, const uint32_t *vin, unsigned long long *kout, uint32_t *vout,
-                       const unsigned long long *count, int shift, int nb, uint32_t *hist, cudaStream_t s) {
+template <typename K>
+cudaError_t radix_pass(const K *kin, const uint32_t *vin, K *kout, uint32_t *vout, const unsigned long long *count,
+                       int shift, int nb, uint32_t *hist, cudaStream_t s) {
     uint32_t *totals = hist + (size_t)kRadix * nb;
-    k_radix_hist<<<nb, kSortThreads, 0, s>>>(kin, count, shift, nb, hist);
+    k_radix_hist<K><<<nb, kSortThreads, 0, s>>>(kin, count, shift, nb, hist);
     k_radix_colscan<<<kRadix, kColThreads, 0, s>>>(hist, nb, totals);
-    k_radix_scatter<<<nb, kSortThreads, sizeof(ScatterSmem), s>>>(kin, vin, kout, vout, count, shift, nb, hist,
-                                                                  totals);
+    k_radix_scatter<K><<<nb, kSortThreads, sizeof(ScatterSmem<K>), s>>>(kin, vin, kout, vout, count, shift, nb, hist,
+                                                                        totals);
     return cudaGetLastError();
 }
 
+template <typename K>
 cudaError_t scatter_smem_attr() {
-    return cudaFuncSetAttribute(k_radix_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)sizeof(ScatterSmem));
+    return cudaFuncSetAttribute(k_radix_scatter<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)sizeof(ScatterSmem<K>));
 }
 
 }  // namespace
@@ -456,17 +478,16 @@ cudaError_t launch_bin_sort(const gs_batch *b, const Layout &L, unsigned char *w
     const uint2 *rect = reinterpret_cast<const uint2 *>(ws + L.rect);
     const float *depth = reinterpret_cast<const float *>(ws + L.depth);
     unsigned long long *sums = reinterpret_cast<unsigned long long *>(ws + L.emit_sums);
-    unsigned long long *keys[2] = {reinterpret_cast<unsigned long long *>(ws + L.keys[0]),
-                                   reinterpret_cast<unsigned long long *>(ws + L.keys[1])};
+    uint32_t *keys[2] = {reinterpret_cast<uint32_t *>(ws + L.keys[0]), reinterpret_cast<uint32_t *>(ws + L.keys[1])};
     uint32_t *vals[2] = {reinterpret_cast<uint32_t *>(ws + L.vals[0]), reinterpret_cast<uint32_t *>(ws + L.vals[1])};
-    unsigned long long *rkeys[2] = {reinterpret_cast<unsigned long long *>(ws + L.rec_keys[0]),
-                                    reinterpret_cast<unsigned long long *>(ws + L.rec_keys[1])};
+    uint32_t *rkeys[2] = {reinterpret_cast<uint32_t *>(ws + L.rec_keys[0]),
+                          reinterpret_cast<uint32_t *>(ws + L.rec_keys[1])};
     uint32_t *rvals[2] = {reinterpret_cast<uint32_t *>(ws + L.rec_vals[0]),
                           reinterpret_cast<uint32_t *>(ws + L.rec_vals[1])};
     uint32_t *hist = reinterpret_cast<uint32_t *>(ws + L.sort_hist);
     uint2 *ranges = reinterpret_cast<uint2 *>(ws + L.ranges);
     const long long R = b->num_records;
-    cudaError_t e = scatter_smem_attr();
+    cudaError_t e = scatter_smem_attr<uint32_t>();
     if (e != cudaSuccess) return e;
     if (L.emit_blocks > 0) {
         // stage 1: stable depth order of the records (4 passes, ends in buffer 0)
@@ -478,8 +499,9 @@ cudaError_t launch_bin_sort(const gs_batch *b, const Layout &L, unsigned char *w
         // stage 2: pairs emitted in that order
         k_pair_count<<<L.emit_blocks, kEmitThreads, 0, s>>>(rect, R, rvals[0], sums);
         k_pair_scan<<<1, 1024, 0, s>>>(sums, L.emit_blocks, b->pair_capacity, stats);
-        k_pair_emit<<<L.emit_blocks, kEmitThreads, 0, s>>>(b->frames_dev, b->num_frames, rect, depth, R, rvals[0],
-                                                           sums, stats, keys[L.first_buffer], vals[L.first_buffer]);
+        k_pair_emit<uint32_t><<<L.emit_blocks, kEmitThreads, 0, s>>>(b->frames_dev, b->num_frames, rect, depth, R,
+                                                                     rvals[0], sums, stats, keys[L.first_buffer],
+                                                                     vals[L.first_buffer]);
     } else {
         e = cudaMemsetAsync(&stats->num_pairs, 0, sizeof(unsigned long long), s);
     }
@@ -487,13 +509,13 @@ cudaError_t launch_bin_sort(const gs_batch *b, const Layout &L, unsigned char *w
     // stage 3: stable passes over the tile bits only (end in buffer 0)
     int cur = L.first_buffer;
     for (int p = 0; p < L.passes && e == cudaSuccess; p++) {
-        e = radix_pass(keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], &stats->num_pairs, 32 + 8 * p,
-                       L.sort_blocks, hist, s);
+        e = radix_pass(keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], &stats->num_pairs, 8 * p, L.sort_blocks,
+                       hist, s);
         cur ^= 1;
     }
     if (e != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(ranges, 0, sizeof(uint2) * (size_t)b->num_tiles, s)) != cudaSuccess) return e;
-    k_tile_ranges<<<1216, 256, 0, s>>>(keys[0], &stats->num_pairs, ranges);
+    k_tile_ranges<uint32_t><<<1216, 256, 0, s>>>(keys[0], &stats->num_pairs, ranges);
     k_tile_order<<<1, 1024, 0, s>>>(ranges, b->num_tiles, reinterpret_cast<uint32_t *>(ws + L.order));
     return cudaGetLastError();
 }
@@ -578,11 +600,12 @@ extern "C" gs_status gs_bin_sort_noalloc(const gs_batch *b, const gs_opts *o, co
     if (e == cudaSuccess && emit_blocks > 0) {
         k_pair_count<<<emit_blocks, kEmitThreads, 0, s>>>(r2, b->num_records, nullptr, sc->emit_sums);
         k_pair_scan<<<1, 1024, 0, s>>>(sc->emit_sums, emit_blocks, b->pair_capacity, &sc->stats);
-        k_pair_emit<<<emit_blocks, kEmitThreads, 0, s>>>(b->frames_dev, b->num_frames, r2, depth, b->num_records,
-                                                         nullptr, sc->emit_sums, &sc->stats, kb[cur], vb[cur]);
+        k_pair_emit<unsigned long long><<<emit_blocks, kEmitThreads, 0, s>>>(
+            b->frames_dev, b->num_frames, r2, depth, b->num_records, nullptr, sc->emit_sums, &sc->stats, kb[cur],
+            vb[cur]);
         e = cudaGetLastError();
     }
-    if (e == cudaSuccess) e = scatter_smem_attr();
+    if (e == cudaSuccess) e = scatter_smem_attr<unsigned long long>();
     for (int p = 0; e == cudaSuccess && p < passes; p++) {
         e = radix_pass(kb[cur], vb[cur], kb[cur ^ 1], vb[cur ^ 1], &sc->stats.num_pairs, p * kRadixBits,
                        sort_blocks, sc->hist, s);
@@ -590,7 +613,8 @@ extern "C" gs_status gs_bin_sort_noalloc(const gs_batch *b, const gs_opts *o, co
     }
     if (e == cudaSuccess) e = cudaMemsetAsync(ranges, 0, sizeof(uint32_t) * 2 * (size_t)b->num_tiles, s);
     if (e == cudaSuccess) {
-        k_tile_ranges<<<1216, 256, 0, s>>>(kb[0], &sc->stats.num_pairs, reinterpret_cast<uint2 *>(ranges));
+        k_tile_ranges<unsigned long long><<<1216, 256, 0, s>>>(kb[0], &sc->stats.num_pairs,
+                                                               reinterpret_cast<uint2 *>(ranges));
         k_noalloc_counts<<<1, 1, 0, s>>>(&sc->stats, reinterpret_cast<unsigned long long *>(out_pairs));
         e = cudaGetLastError();
     }

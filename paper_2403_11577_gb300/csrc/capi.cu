@@ -51,13 +51,13 @@ bool make_layout(const gs_batch *b, Layout *L) {
     L->depth = take(R * 4);
     L->splat = take(R * 32);
     L->grad2d = take(R * 48);
-    L->keys[0] = take(cap * 8);
+    L->keys[0] = take(cap * 4);
     L->vals[0] = take(cap * 4);
-    L->keys[1] = take(cap * 8);
+    L->keys[1] = take(cap * 4);
     L->vals[1] = take(cap * 4);
-    L->rec_keys[0] = take(R * 8);
+    L->rec_keys[0] = take(R * 4);
     L->rec_vals[0] = take(R * 4);
-    L->rec_keys[1] = take(R * 8);
+    L->rec_keys[1] = take(R * 4);
     L->rec_vals[1] = take(R * 4);
     L->ranges = take(T * 8);
     L->order = take(T * 4);

@@ -55,8 +55,9 @@ def test_workspace_size_is_host_only(lib):
     b.tile, b.num_tiles = 16, 8 * 88 * 24
     b.num_records, b.num_pixels, b.pair_capacity = 8_000_000, 8 * 1408 * 376, 100_000_000
     n = capi.gs_workspace_size(b)
-    # records (8+4+32+48 B) + pairs (2 x 12 B) dominate
-    assert n >= 8_000_000 * 92 + 100_000_000 * 24
+    # records (rect 8, depth 4, splat 32, grad2d 48, two key/value buffers of
+    # the record sort 2 x 8 B) and pairs (two key/value buffers, 2 x 8 B) dominate
+    assert n >= 8_000_000 * (92 + 16) + 100_000_000 * 16
     offs = capi.gs_workspace_offsets(b)
     assert len(offs) == 10 and offs == sorted(offs) and all(o % 256 == 0 for o in offs)
     b.num_frames = 0

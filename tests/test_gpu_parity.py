@@ -144,10 +144,12 @@ def test_bin_sort_bit_exact_synthetic(tile):
     keys, vals, ranges = oracle.bin_sort(tiles, counts, rect, depth)
     P = len(keys)
     assert st.num_pairs == P and st.status == 0
-    gk = plan.ws_view(capi.WS_KEYS, torch.int64, P).cpu().numpy().view(np.uint64)
+    # the workspace keys hold the global tile (the high half of the full key);
+    # the values carry the depth order within each tile
+    gk = plan.ws_view(capi.WS_KEYS, torch.int32, P).cpu().numpy().view(np.uint32)
     gv = plan.ws_view(capi.WS_VALS, torch.int32, P).cpu().numpy().view(np.uint32)
     gr = plan.ws_view(capi.WS_RANGES, torch.int32, 2 * plan.batch.num_tiles).cpu().numpy().view(np.uint32)
-    np.testing.assert_array_equal(gk, keys)
+    np.testing.assert_array_equal(gk, (keys >> np.uint64(32)).astype(np.uint32))
     np.testing.assert_array_equal(gv, vals)
     np.testing.assert_array_equal(gr.reshape(-1, 2).astype(np.int64), ranges)
 
@@ -174,8 +176,10 @@ def test_bin_sort_empty_and_single():
     plan.bin_sort()
     keys, vals, ranges = oracle.bin_sort([(1, 1), (1, 1)], [3, 1], rect, depth)
     assert plan.stats().num_pairs == 2
-    gk = plan.ws_view(capi.WS_KEYS, torch.int64, 2).cpu().numpy().view(np.uint64)
-    np.testing.assert_array_equal(gk, keys)
+    gk = plan.ws_view(capi.WS_KEYS, torch.int32, 2).cpu().numpy().view(np.uint32)
+    gv = plan.ws_view(capi.WS_VALS, torch.int32, 2).cpu().numpy().view(np.uint32)
+    np.testing.assert_array_equal(gk, (keys >> np.uint64(32)).astype(np.uint32))
+    np.testing.assert_array_equal(gv, vals)
 
 
 # ----------------------------------------------------------------- render

@@ -1,9 +1,11 @@
 """The allocation-free binning entry point (gs_bin_sort_noalloc), for
 callers that cannot allocate device memory and so cannot provide a
 workspace, against the workspace entry point gs_bin_sort on the same
-records: keys, values, tile ranges and pair counts must be identical (the
-sort is integer work, compared bit for bit), on two calls in a row with
-different inputs.  This file is collected last on purpose."""
+records: values, tile ranges and pair counts must be identical, and the
+full 64-bit keys must be the workspace's tile keys over the depth bits of
+each pair's record (the sort is integer work, compared bit for bit), on two
+calls in a row with different inputs.  This file is collected last on
+purpose."""
 import numpy as np
 import pytest
 import torch
@@ -57,9 +59,19 @@ def test_bin_sort_noalloc_matches_workspace_entry_point():
         capi.gs_bin_sort_noalloc(plan.batch, plan.copts, rect, depth, keys, vals, ranges, counts_out)
         torch.cuda.synchronize()
         assert counts_out.tolist() == [P, P], (call, counts_out.tolist(), P)
-        assert torch.equal(keys[:P], plan.ws_view(capi.WS_KEYS, torch.int64, P)), call
+        # same order: vals and ranges bit for bit; the full 64-bit keys are the
+        # workspace's tile keys over the depth bits of each pair's record
         assert torch.equal(vals[:P], plan.ws_view(capi.WS_VALS, torch.int32, P)), call
         assert torch.equal(ranges, plan.ws_view(capi.WS_RANGES, torch.int32, 2 * T)), call
+        k = keys[:P].cpu().numpy().view(np.uint64)
+        tile = plan.ws_view(capi.WS_KEYS, torch.int32, P).cpu().numpy().view(np.uint32)
+        np.testing.assert_array_equal((k >> np.uint64(32)).astype(np.uint32), tile)
+        v = vals[:P].cpu().numpy().view(np.uint32).astype(np.int64)
+        rec_off = np.array([plan.frame(i).record_offset for i in range(len(frames_wh))])
+        tile_off = np.array([plan.frame(i).tile_offset for i in range(len(frames_wh))])
+        fr = np.searchsorted(tile_off, tile, side="right") - 1
+        dbits = depth.cpu().numpy().view(np.uint32)[rec_off[fr] + v]
+        np.testing.assert_array_equal((k & np.uint64(0xFFFFFFFF)).astype(np.uint32), dbits)
 
 
 def test_bin_sort_noalloc_rejects_oversized_batches():
