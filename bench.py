@@ -63,7 +63,7 @@ def parse():
     ap.add_argument("--frames", type=int, default=8)
     ap.add_argument("--per-frame-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-pixels", type=int, default=48, help="oracle pixels per frame sample")
+    ap.add_argument("--cpu-pixels", type=int, default=400, help="oracle pixels per frame sample")
     ap.add_argument("--autotune", action="store_true", help="pick tile/batch with the autotuner first")
     ap.add_argument("--workload", choices=["batched", "uneven"], default="batched",
                     help="batched: 1M Gaussians, 8 frames 1408x376 (the headline); uneven: three scenes "
