@@ -61,6 +61,7 @@ def lib():
     if _lib is None:
         _lib = C.CDLL(_build.build())
         _lib.or_l1.restype = C.c_double
+        _lib.or_dssim.restype = C.c_double
         _lib.or_bin_sort.restype = C.c_int64
     return _lib
 
@@ -179,6 +180,42 @@ def l1(C_img, C_gt):
     grad = np.zeros_like(a)
     loss = lib().or_l1(C.c_int64(a.size), _p(a), _p(b), _p(grad))
     return loss, grad.reshape(np.shape(C_img))
+
+
+def dssim(imgs, tgts, with_map=False):
+    """D-SSIM part of Eq. 4 (1 - mean SSIM, 11x11 Gaussian window of sigma
+    1.5, zero padding) over a batch of HxWx3 images, and its gradient with
+    respect to the rendered images (a list like `imgs`)."""
+    shapes = [np.shape(a) for a in imgs]
+    rows = np.array([s[0] for s in shapes], np.int32)
+    cols = np.array([s[1] for s in shapes], np.int32)
+    sizes = [s[0] * s[1] * 3 for s in shapes]
+    off = np.concatenate([[0], np.cumsum(sizes)[:-1]]).astype(np.int64)
+    a = np.concatenate([_f64(x).ravel() for x in imgs])
+    b = np.concatenate([_f64(x).ravel() for x in tgts])
+    grad = np.zeros_like(a)
+    smap = np.zeros_like(a) if with_map else None
+    loss = lib().or_dssim(C.c_int(len(imgs)), rows.ctypes.data_as(C.POINTER(C.c_int32)),
+                          cols.ctypes.data_as(C.POINTER(C.c_int32)), off.ctypes.data_as(C.POINTER(C.c_int64)),
+                          _p(a), _p(b), _p(grad), _p(smap) if with_map else None)
+    grads = [grad[o:o + n].reshape(s) for o, n, s in zip(off, sizes, shapes)]
+    if with_map:
+        return loss, grads, [smap[o:o + n].reshape(s) for o, n, s in zip(off, sizes, shapes)]
+    return loss, grads
+
+
+def photo_loss(imgs, tgts, lambda1=0.2):
+    """L_photo = (1 - lambda1) L1 + lambda1 D-SSIM (Eq. 4, lambda1 = 0.2 in
+    the paper) over a batch of HxWx3 images, both means over every value of
+    the batch, and its gradient per image."""
+    a = np.concatenate([_f64(x).ravel() for x in imgs])
+    b = np.concatenate([_f64(x).ravel() for x in tgts])
+    l1_loss, g1 = l1(a, b)
+    ds, gs = dssim(imgs, tgts)
+    off = np.concatenate([[0], np.cumsum([np.size(x) for x in imgs])])
+    grads = [(1 - lambda1) * g1[off[i]:off[i + 1]].reshape(np.shape(imgs[i])) + lambda1 * gs[i]
+             for i in range(len(imgs))]
+    return (1 - lambda1) * l1_loss + lambda1 * ds, grads
 
 
 def bin_sort(frames_tiles, n_per_frame, rect, depth, cap=None):

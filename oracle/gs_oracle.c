@@ -17,7 +17,9 @@
  *                      back in depth order.
  *   Sec. III-B         backpropagation to the Gaussian parameters and, through
  *                      the input pose, to the extrinsic and the time offset.
- *   Sec. III-B, Eq. 4  the L1 part of the photometric loss.
+ *   Sec. III-B, Eq. 4  the photometric loss: its L1 part, and the D-SSIM
+ *                      part with the structural similarity of [kerbl20233d]
+ *                      (11x11 Gaussian window, sigma 1.5, zero padding).
  *
  * There is no tiling: every requested pixel is composited over every visible
  * Gaussian in one global (depth, index) order.  The renderer details the
@@ -767,6 +769,111 @@ double or_l1(int64_t n, const double *C, const double *Cgt, double *grad) {
         if (grad) grad[i] = (d > 0 ? 1.0 : (d < 0 ? -1.0 : 0.0)) / (double)n;
     }
     return s / (double)n;
+}
+
+/* Exported: the D-SSIM part of the photometric loss (Eq. 4) over a batch of
+ * F images and its gradient with respect to the rendered images.
+ *
+ * Image f is rows x cols x 3 (row-major, channels interleaved) at value
+ * offset off[f] in img/tgt/grad.  Per channel and pixel q, with the
+ * normalised 11x11 Gaussian window G (sigma 1.5) and zero padding outside
+ * the image (Wang et al.'s SSIM as used by 3DGS):
+ *   mu_a = sum_p G(p - q) a(p),   mu_b likewise,
+ *   s_aa = sum_p G a(p)^2 - mu_a^2,  s_bb likewise,  s_ab = sum_p G a b - mu_a mu_b,
+ *   SSIM(q) = (2 mu_a mu_b + C1)(2 s_ab + C2) / ((mu_a^2 + mu_b^2 + C1)(s_aa + s_bb + C2)),
+ * C1 = 0.01^2, C2 = 0.03^2.  D-SSIM = 1 - mean of SSIM over all pixels and
+ * channels of the batch (n values).  Its gradient follows the chain rule
+ * through mu_a, s_aa and s_ab:
+ *   d(mean SSIM)/da(p) = (1/n) sum_q G(p - q) [ S_mu(q) + S_aa(q) (2 a(p) - 2 mu_a(q))
+ *                                              + S_ab(q) (b(p) - mu_b(q)) ]
+ * with S_mu, S_aa, S_ab the partial derivatives of SSIM(q) in mu_a, s_aa,
+ * s_ab.  grad (optional) receives d(D-SSIM)/d img; ssim_map (optional)
+ * receives SSIM(q) per value.  Returns D-SSIM. */
+static void ssim_window(double g[11]) {
+    double s = 0;
+    for (int i = 0; i < 11; i++) {
+        g[i] = exp(-(double)((i - 5) * (i - 5)) / (2.0 * 1.5 * 1.5));
+        s += g[i];
+    }
+    for (int i = 0; i < 11; i++) g[i] /= s;
+}
+
+double or_dssim(int F, const int32_t *rows, const int32_t *cols, const int64_t *off, const double *img,
+                const double *tgt, double *grad, double *ssim_map) {
+    const double C1 = 0.01 * 0.01, C2 = 0.03 * 0.03;
+    double g[11];
+    ssim_window(g);
+    int64_t n = 0;
+    for (int f = 0; f < F; f++) n += (int64_t)rows[f] * cols[f] * 3;
+    double sum = 0;
+    for (int f = 0; f < F; f++) {
+        const int H = rows[f], W = cols[f];
+        const double *a = img + off[f], *b = tgt + off[f];
+        const int64_t m = (int64_t)H * W;
+        /* per pixel and channel: S_mu, S_aa, S_ab and mu_a, mu_b */
+        double *Smu = malloc(sizeof(double) * m * 3), *Saa = malloc(sizeof(double) * m * 3);
+        double *Sab = malloc(sizeof(double) * m * 3), *mua = malloc(sizeof(double) * m * 3);
+        double *mub = malloc(sizeof(double) * m * 3);
+        for (int y = 0; y < H; y++)
+            for (int x = 0; x < W; x++)
+                for (int c = 0; c < 3; c++) {
+                    double ma = 0, mb = 0, eaa = 0, ebb = 0, eab = 0;
+                    for (int dy = -5; dy <= 5; dy++) {
+                        const int yy = y + dy;
+                        if (yy < 0 || yy >= H) continue;
+                        for (int dx = -5; dx <= 5; dx++) {
+                            const int xx = x + dx;
+                            if (xx < 0 || xx >= W) continue;
+                            const double w = g[dy + 5] * g[dx + 5];
+                            const double va = a[((int64_t)yy * W + xx) * 3 + c];
+                            const double vb = b[((int64_t)yy * W + xx) * 3 + c];
+                            ma += w * va;
+                            mb += w * vb;
+                            eaa += w * va * va;
+                            ebb += w * vb * vb;
+                            eab += w * va * vb;
+                        }
+                    }
+                    const double saa = eaa - ma * ma, sbb = ebb - mb * mb, sab = eab - ma * mb;
+                    const double A = 2 * ma * mb + C1, B = 2 * sab + C2;
+                    const double Cc = ma * ma + mb * mb + C1, D = saa + sbb + C2;
+                    const double S = (A * B) / (Cc * D);
+                    const int64_t i = ((int64_t)y * W + x) * 3 + c;
+                    sum += S;
+                    if (ssim_map) ssim_map[off[f] + i] = S;
+                    Smu[i] = 2 * mb * B / (Cc * D) - 2 * ma * S / Cc;
+                    Saa[i] = -S / D;
+                    Sab[i] = 2 * A / (Cc * D);
+                    mua[i] = ma;
+                    mub[i] = mb;
+                }
+        if (grad) {
+            for (int y = 0; y < H; y++)
+                for (int x = 0; x < W; x++)
+                    for (int c = 0; c < 3; c++) {
+                        const int64_t ip = ((int64_t)y * W + x) * 3 + c;
+                        double d = 0;
+                        for (int dy = -5; dy <= 5; dy++) {
+                            const int yy = y + dy;
+                            if (yy < 0 || yy >= H) continue;
+                            for (int dx = -5; dx <= 5; dx++) {
+                                const int xx = x + dx;
+                                if (xx < 0 || xx >= W) continue;
+                                const int64_t iq = ((int64_t)yy * W + xx) * 3 + c;
+                                d += g[dy + 5] * g[dx + 5] *
+                                     (Smu[iq] + Saa[iq] * (2 * a[ip] - 2 * mua[iq]) + Sab[iq] * (b[ip] - mub[iq]));
+                            }
+                        }
+                        grad[off[f] + ip] = -d / (double)n;
+                    }
+        }
+        free(Smu);
+        free(Saa);
+        free(Sab);
+        free(mua);
+        free(mub);
+    }
+    return 1.0 - sum / (double)n;
 }
 
 /* --------------------------------------------------------- tile binning -- */

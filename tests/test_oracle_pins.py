@@ -427,3 +427,66 @@ def test_scale_clamp():
     a = oracle.render(sc, p.frames[0], p.ext[0], 0.0, oracle.Opts(scale_max=0.2))
     b = oracle.render(sc2, p.frames[0], p.ext[0], 0.0, oracle.Opts())
     np.testing.assert_allclose(a[0], b[0], atol=1e-12)
+
+
+# ------------------------------------------------------------ D-SSIM (Eq. 4)
+
+
+def _ssim_scipy(a, b):
+    """SSIM map from scipy's Gaussian filter: sigma 1.5, 11 taps (truncate at
+    5 px), zero padding, per channel; constants of Wang et al."""
+    from scipy.ndimage import gaussian_filter
+
+    def f(x):
+        return gaussian_filter(x, sigma=(1.5, 1.5, 0.0), mode="constant", cval=0.0, truncate=5.0 / 1.5)
+
+    C1, C2 = 0.01 ** 2, 0.03 ** 2
+    ma, mb = f(a), f(b)
+    saa, sbb, sab = f(a * a) - ma * ma, f(b * b) - mb * mb, f(a * b) - ma * mb
+    return ((2 * ma * mb + C1) * (2 * sab + C2)) / ((ma * ma + mb * mb + C1) * (saa + sbb + C2))
+
+
+def test_dssim_map_matches_scipy_gaussian_filter():
+    """The oracle's SSIM map is the textbook SSIM computed with a library
+    Gaussian filter (independent code path), on ragged sizes."""
+    rng = np.random.default_rng(3)
+    imgs = [rng.uniform(size=(19, 23, 3)), rng.uniform(size=(7, 40, 3))]
+    tgts = [np.clip(x + rng.normal(0, 0.1, x.shape), 0, 1) for x in imgs]
+    loss, _, maps = oracle.dssim(imgs, tgts, with_map=True)
+    ref = [_ssim_scipy(a, b) for a, b in zip(imgs, tgts)]
+    for m, r in zip(maps, ref):
+        np.testing.assert_allclose(m, r, rtol=0, atol=1e-12)
+    n = sum(x.size for x in imgs)
+    assert loss == pytest.approx(1 - sum(r.sum() for r in ref) / n, rel=1e-12)
+
+
+def test_dssim_identical_images_and_constant_closed_form():
+    rng = np.random.default_rng(4)
+    a = rng.uniform(size=(15, 18, 3))
+    loss, (g,) = oracle.dssim([a], [a])
+    assert abs(loss) < 1e-14 and np.abs(g).max() < 1e-13  # SSIM = 1 is the maximum
+    # constant images: away from the border the window sees only the constants,
+    # so SSIM = (2 a b + C1) / (a^2 + b^2 + C1) (the variance factor is 1)
+    ca, cb = 0.3, 0.7
+    _, _, (m,) = oracle.dssim([np.full((31, 33, 3), ca)], [np.full((31, 33, 3), cb)], with_map=True)
+    C1 = 0.01 ** 2
+    assert m[15, 16, 1] == pytest.approx((2 * ca * cb + C1) / (ca * ca + cb * cb + C1), rel=1e-13)
+
+
+@pytest.mark.parametrize("lambda1", [1.0, 0.2])
+def test_photo_loss_gradient_matches_central_differences(lambda1):
+    """d L_photo / d image against FP64 central differences (D-SSIM alone for
+    lambda1 = 1, the paper's mix for 0.2), at pixels near the border, in the
+    interior and in a second image."""
+    rng = np.random.default_rng(5)
+    imgs = [rng.uniform(0.1, 0.9, size=(12, 15, 3)), rng.uniform(0.1, 0.9, size=(9, 8, 3))]
+    tgts = [rng.uniform(0.1, 0.9, size=x.shape) for x in imgs]
+    loss, grads = oracle.photo_loss(imgs, tgts, lambda1)
+    for (k, y, x, c) in [(0, 0, 0, 0), (0, 6, 7, 1), (0, 11, 14, 2), (0, 3, 12, 0), (1, 4, 4, 1), (1, 8, 0, 2)]:
+        h = 1e-6
+        up = [v.copy() for v in imgs]
+        dn = [v.copy() for v in imgs]
+        up[k][y, x, c] += h
+        dn[k][y, x, c] -= h
+        fd = (oracle.photo_loss(up, tgts, lambda1)[0] - oracle.photo_loss(dn, tgts, lambda1)[0]) / (2 * h)
+        assert grads[k][y, x, c] == pytest.approx(fd, rel=1e-6, abs=1e-12), (k, y, x, c)
