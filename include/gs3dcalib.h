@@ -10,6 +10,7 @@
  *   bin/sort Eq. 5 (Phi) tile binning + depth order               gs_bin_sort
  *   render   Eq. 5 (Phi) front-to-back alpha compositing          gs_render_fwd
  *   loss     Eq. 4      L1 term of L_photo                        gs_loss_l1
+ *                       L_photo = (1 - lambda1) L1 + lambda1 D-SSIM gs_loss_photo
  *   backward Sec. III-B "gradients are backpropagated to both the Gaussian
  *                       parameters, and the calibration parameters through
  *                       the input pose"                           gs_render_bwd,
@@ -78,8 +79,14 @@ typedef struct {
     int64_t record_offset;      /* first per-(frame, Gaussian) record */
     int64_t pixel_offset;       /* first pixel in the image outputs */
     int32_t tile_offset;        /* first global tile id */
-    int32_t tiles_x, tiles_y;   /* tiles covering the image */
-    int32_t reserved;
+    int32_t tiles_x, tiles_y;   /* tiles covering rows [row0, height) */
+    /* input: */
+    int32_t row0;               /* first image row rendered: the frame's output
+                                   is rows [row0, height) of the full camera
+                                   image (0 = whole image; height / 2 = the
+                                   bottom half the paper's losses use,
+                                   Sec. III-D).  The camera, and so every
+                                   pixel's value, is unchanged by the crop. */
 } gs_frame;
 
 /* Renderer settings.  The paper defers the renderer to 3DGS
@@ -142,8 +149,9 @@ int32_t gs_struct_sizes(size_t *out, int32_t n);
  * gs_batch_init-written fields are filled; the completed table is copied
  * to frames_dev (caller-allocated device memory of F * sizeof(gs_frame)
  * bytes) with cudaMemcpy.  tile must be 8, 16 or 32.  Frames are checked:
- * positive sizes, camera_id < num_cameras, traj_id < num_trajs, Gaussian
- * range inside [0, num_gaussians), tiles_x and tiles_y < 65536.
+ * positive sizes, 0 <= row0 < height, camera_id < num_cameras, traj_id <
+ * num_trajs, Gaussian range inside [0, num_gaussians), tiles_x and tiles_y
+ * < 65536.  A frame contributes width * (height - row0) pixels.
  * Errors: GS_ERR_INVALID_ARG, GS_ERR_CUDA (copy failed). */
 gs_status gs_batch_init(gs_frame *frames_host, int32_t num_frames, int32_t num_gaussians,
                         int32_t num_cameras, int32_t num_trajs, int32_t tile,
@@ -259,6 +267,24 @@ gs_status gs_render_fwd(const gs_batch *batch, const float *colors, const gs_opt
  *   ws_dev: a workspace of this batch (uses its reduction scratch). */
 gs_status gs_loss_l1(const gs_batch *batch, const float *rgb, const float *target, int64_t n,
                      float scale, double *out_loss, float *out_grad, void *ws_dev, void *stream);
+
+/* The photometric loss of Eq. 4 over the batch's images:
+ *   L_photo = (1 - lambda1) L1 + lambda1 D-SSIM    (lambda1 = 0.2 in the paper)
+ * L1 = mean |rgb - target| and D-SSIM = 1 - mean SSIM, both over all
+ * 3 * num_pixels values.  SSIM per channel and pixel with the 11x11
+ * Gaussian window of sigma 1.5, zero padding at each frame's image border
+ * (a cropped frame's image is its rows [row0, height): the paper's losses
+ * use the bottom half, Sec. III-D) and C1 = 0.01^2, C2 = 0.03^2, as in
+ * [kerbl20233d].
+ *   rgb, target[num_pixels][3]  frame f at pixel_offset, row-major
+ *   lambda1 in [0, 1]
+ *   out_loss[3] (device double, overwritten): L_photo, L1, D-SSIM
+ *   out_grad[num_pixels][3] (optional): scale * dL_photo/drgb, overwritten
+ *   ws_dev: the batch's workspace (its SSIM maps and partial sums).
+ * The loss is reduced in a fixed order (deterministic).
+ * Errors: GS_ERR_INVALID_ARG, GS_ERR_CUDA. */
+gs_status gs_loss_photo(const gs_batch *batch, const float *rgb, const float *target, float lambda1,
+                        float scale, double *out_loss, float *out_grad, void *ws_dev, void *stream);
 
 /* Backward of Phi and of the projection (Sec. III-B): walks each pixel's
  * composited Gaussians in reverse order, recovering transmittance by

@@ -146,11 +146,22 @@ def render_pose(scene, cam, R_cw, t_cw, opts: Opts = Opts(), pixels=None):
     return out_rgb, out_T, out_last, out_flags
 
 
+def _frame_pixels(frame, pixels):
+    """The frame's image pixels (rows row0 .. H-1, row-major) when no pixel
+    list is given and the frame is cropped."""
+    row0 = getattr(frame, "row0", 0)
+    if pixels is not None or row0 == 0:
+        return pixels
+    cam = frame.camera
+    v, u = np.mgrid[row0:cam.height, 0:cam.width]
+    return np.stack([u.ravel(), v.ravel()], 1)
+
+
 def render(scene, frame, ext, delta, opts: Opts = Opts(), pixels=None):
     """Render a frame at the pose of Eq. 1 for extrinsic ext (omega, t) and
-    time offset delta."""
+    time offset delta (a cropped frame: its rows row0 .. H-1)."""
     R, t = frame_pose(scene, ext, delta, frame.timestamp)
-    return render_pose(scene, frame.camera, R, t, opts, pixels)
+    return render_pose(scene, frame.camera, R, t, opts, _frame_pixels(frame, pixels))
 
 
 def backward(scene, frame, ext, delta, dL_dC, opts: Opts = Opts(), pixels=None):
@@ -158,7 +169,7 @@ def backward(scene, frame, ext, delta, dL_dC, opts: Opts = Opts(), pixels=None):
     (q, log_scale, logit_opacity, rgb), calibration (ext[6], delta), and the
     per-Gaussian 2D gradients (mean2d, conic, opacity)."""
     X, q, ls, lo, rgb = _gauss(scene)
-    pix, npix = _pix(pixels)
+    pix, npix = _pix(_frame_pixels(frame, pixels))
     n = scene.n
     g = dict(quat=np.zeros((n, 4)), log_scale=np.zeros((n, 3)), logit_opacity=np.zeros(n),
              rgb=np.zeros((n, 3)), ext=np.zeros(6), delta=np.zeros(1), mean2d=np.zeros((n, 2)),

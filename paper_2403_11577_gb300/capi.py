@@ -22,7 +22,7 @@ class GsFrame(C.Structure):
                 ("cx", C.c_float), ("cy", C.c_float), ("camera_id", C.c_int32), ("traj_id", C.c_int32),
                 ("gauss_offset", C.c_int32), ("gauss_count", C.c_int32), ("timestamp", C.c_double),
                 ("record_offset", C.c_int64), ("pixel_offset", C.c_int64), ("tile_offset", C.c_int32),
-                ("tiles_x", C.c_int32), ("tiles_y", C.c_int32), ("reserved", C.c_int32)]
+                ("tiles_x", C.c_int32), ("tiles_y", C.c_int32), ("row0", C.c_int32)]
 
 
 class GsOpts(C.Structure):
@@ -63,6 +63,7 @@ _SIGS = {
     "gs_bin_sort": ([_P, _P, _P, _P], C.c_int32),
     "gs_render_fwd": ([_P, _P, _P, _P, _P, _P, _P, _P], C.c_int32),
     "gs_loss_l1": ([_P, _P, _P, C.c_int64, C.c_float, _P, _P, _P, _P], C.c_int32),
+    "gs_loss_photo": ([_P, _P, _P, C.c_float, C.c_float, _P, _P, _P, _P], C.c_int32),
     "gs_render_bwd": ([_P] * 15 + [C.c_int32, _P], C.c_int32),
     "gs_pose_grad": ([_P] * 6 + [C.c_int32, _P], C.c_int32),
     "gs_bin_sort_noalloc": ([_P] * 9, C.c_int32),
@@ -227,6 +228,19 @@ def gs_loss_l1(batch, rgb, target, scale, out_loss, out_grad, ws, stream=None):
     _check(lib().gs_loss_l1(C.byref(batch), _ptr(rgb, F32, "rgb"), _ptr(target, F32, "target"), n, float(scale),
                             _ptr(out_loss, F64, "out_loss"), _ptr(out_grad, F32, "out_grad", allow_none=True),
                             _ptr(ws, torch.uint8, "ws"), _stream(stream)), "gs_loss_l1")
+
+
+def gs_loss_photo(batch, rgb, target, lambda1, out_loss, out_grad, ws, scale=1.0, stream=None):
+    """out_loss: float64 [3] (L_photo, L1, D-SSIM); out_grad: float32 like rgb or None."""
+    n = 3 * batch.num_pixels
+    if rgb.numel() != n or target.numel() != n or (out_grad is not None and out_grad.numel() != n):
+        raise ValueError("gs_loss_photo: size mismatch")
+    if out_loss.numel() < 3:
+        raise ValueError("gs_loss_photo: out_loss needs 3 doubles")
+    _check(lib().gs_loss_photo(C.byref(batch), _ptr(rgb, F32, "rgb"), _ptr(target, F32, "target"), float(lambda1),
+                               float(scale), _ptr(out_loss, F64, "out_loss"),
+                               _ptr(out_grad, F32, "out_grad", allow_none=True), _ptr(ws, torch.uint8, "ws"),
+                               _stream(stream)), "gs_loss_photo")
 
 
 def gs_render_bwd(batch, X, quat, log_scale, logit_opacity, colors, opts, ws, out_T, out_last, dL_drgb,

@@ -27,6 +27,8 @@ cudaError_t launch_render_bwd(const gs_batch *, const gs_opts *, const uint32_t 
                               const float4 *, const float *, Stats *, const float *, const int32_t *, const float *,
                               float4 *, cudaStream_t);
 cudaError_t launch_l1(const float *, const float *, long long, float, double *, float *, double *, cudaStream_t);
+cudaError_t launch_photo(const gs_batch *, const float *, const float *, float, float, double *, float *, float *,
+                         double *, cudaStream_t);
 
 constexpr int kSortBlocksMax = 304;  // two per SM on a 152-SM GB300
 
@@ -66,6 +68,8 @@ bool make_layout(const gs_batch *b, Layout *L) {
     L->twist_part = take(F * (size_t)L->twist_blocks * 6 * 8);
     L->twist_frame = take(F * 6 * 8);
     L->loss_part = take((size_t)kLossBlocks * 8);
+    L->photo_maps = take((size_t)b->num_pixels * 9 * 4);  // 3 SSIM maps per channel
+    L->photo_part = take(T * 2 * 8);
     L->total = o;
     return true;
 }
@@ -148,17 +152,16 @@ gs_status gs_batch_init(gs_frame *frames, int32_t F, int32_t num_gaussians, int3
             fr.traj_id < 0 || fr.traj_id >= num_trajs || fr.gauss_offset < 0 || fr.gauss_count < 0 ||
             (int64_t)fr.gauss_offset + fr.gauss_count > num_gaussians || !std::isfinite(fr.fx) ||
             !std::isfinite(fr.fy) || !std::isfinite(fr.cx) || !std::isfinite(fr.cy) ||
-            !std::isfinite(fr.timestamp))
+            !std::isfinite(fr.timestamp) || fr.row0 < 0 || fr.row0 >= fr.height)
             return GS_ERR_INVALID_ARG;
         fr.tiles_x = (fr.width + tile - 1) / tile;
-        fr.tiles_y = (fr.height + tile - 1) / tile;
+        fr.tiles_y = (fr.height - fr.row0 + tile - 1) / tile;
         if (fr.tiles_x >= 65536 || fr.tiles_y >= 65536) return GS_ERR_INVALID_ARG;
         fr.record_offset = rec;
         fr.pixel_offset = pix;
         fr.tile_offset = (int32_t)tiles;
-        fr.reserved = 0;
         rec += fr.gauss_count;
-        pix += (int64_t)fr.width * fr.height;
+        pix += (int64_t)fr.width * (fr.height - fr.row0);
         tiles += (int64_t)fr.tiles_x * fr.tiles_y;
         if (tiles >= (1ll << 31) || rec >= (1ll << 31)) return GS_ERR_INVALID_ARG;
     }
@@ -272,6 +275,18 @@ gs_status gs_loss_l1(const gs_batch *b, const float *rgb, const float *target, i
     if (!batch_ok(b, ws) || !make_layout(b, &L) || !rgb || !target || !out_loss || n < 0) return GS_ERR_INVALID_ARG;
     return cuda_status(launch_l1(rgb, target, n, scale, out_loss, out_grad, (double *)(W(ws) + L.loss_part),
                                  S(stream)));
+}
+
+gs_status gs_loss_photo(const gs_batch *b, const float *rgb, const float *target, float lambda1, float scale,
+                        double *out_loss, float *out_grad, void *ws, void *stream) {
+    Layout L;
+    if (!batch_ok(b, ws) || !make_layout(b, &L) || !out_loss || !(lambda1 >= 0.f && lambda1 <= 1.f) ||
+        !std::isfinite(scale))
+        return GS_ERR_INVALID_ARG;
+    if (b->num_pixels > 0 && (!rgb || !target)) return GS_ERR_INVALID_ARG;
+    unsigned char *w = W(ws);
+    return cuda_status(launch_photo(b, rgb, target, lambda1, scale, out_loss, out_grad, (float *)(w + L.photo_maps),
+                                    (double *)(w + L.photo_part), S(stream)));
 }
 
 gs_status gs_render_bwd(const gs_batch *b, const float *X, const float *quat, const float *log_scale,

@@ -12,7 +12,8 @@
 // with Sigma = R_g diag(s)^2 R_g^T built once per Gaussian.
 //
 // Record outputs (frame f, Gaussian g -> record r):
-//   rect[r]   tiles [x0,x1]x[y0,y1] where alpha >= alpha_min is possible:
+//   rect[r]   tiles [x0,x1]x[y0,y1] where alpha >= alpha_min is possible
+//             (tile rows counted from the frame's first rendered row, row0):
 //             the box of the ellipse d^T conic d <= 2 ln(opacity/alpha_min),
 //             half-widths sqrt(k cov_xx), sqrt(k cov_yy), widened by a
 //             relative 1e-4 and 0.01 px against float32 rounding;
@@ -176,8 +177,9 @@ k_project(const gs_frame *__restrict__ frames, int F, int N, const float *__rest
             if (vis) {
                 int x0 = max(clamp_tile((Q.mean[0] - rx) * itile, fr.tiles_x), 0);
                 int x1 = min(clamp_tile((Q.mean[0] + rx) * itile, fr.tiles_x), fr.tiles_x - 1);
-                int y0 = max(clamp_tile((Q.mean[1] - ry) * itile, fr.tiles_y), 0);
-                int y1 = min(clamp_tile((Q.mean[1] + ry) * itile, fr.tiles_y), fr.tiles_y - 1);
+                const float my = Q.mean[1] - (float)fr.row0;  // tile rows start at the crop's first row
+                int y0 = max(clamp_tile((my - ry) * itile, fr.tiles_y), 0);
+                int y1 = min(clamp_tile((my + ry) * itile, fr.tiles_y), fr.tiles_y - 1);
                 if (x0 <= x1 && y0 <= y1) {
                     rc = make_uint2((uint32_t)x0 | ((uint32_t)y0 << 16), (uint32_t)x1 | ((uint32_t)y1 << 16));
                     const float s2 = -0.5f * kLog2e;

@@ -162,15 +162,15 @@ struct alignas(16) Staged {
     uint4 z;   // bits of b, position in the tile's range, Gaussian index, 0
 };
 
-// Band of warp `warp` in the work item starting at row row0 of tile (tx, ty),
-// clipped to the image.
+// Band of warp `warp` in the work item starting at row rbase of the tile
+// whose first image row is y_tile, clipped to the image.
 template <int TILE, int RPW>
-__device__ __forceinline__ void band_of(int tx, int ty, int row0, int warp, int W, int H, float &xlo, float &xhi,
+__device__ __forceinline__ void band_of(int tx, int y_tile, int rbase, int warp, int W, int H, float &xlo, float &xhi,
                                         float &ylo, float &yhi) {
     xlo = (float)(tx * TILE);
     xhi = (float)min(tx * TILE + TILE - 1, W - 1);
-    ylo = (float)(ty * TILE + row0 + warp * RPW);
-    yhi = (float)min(ty * TILE + row0 + warp * RPW + RPW - 1, H - 1);
+    ylo = (float)(y_tile + rbase + warp * RPW);
+    yhi = (float)min(y_tile + rbase + warp * RPW + RPW - 1, H - 1);
 }
 
 // Compact the chunk's kept entries, in order, into the warp's slot; returns
@@ -198,9 +198,9 @@ __device__ __forceinline__ int compact(Staged *st, const Entry (&cu)[PER], int p
     return cnt;
 }
 
-// Forward of one work item: rows [row0, row0 + ROWS) of tile t.
+// Forward of one work item: rows [rbase, rbase + ROWS) of tile t.
 template <int TILE, int PPT, int NT, int BATCH>
-__device__ __forceinline__ void fwd_item(int t, int row0, Staged *st_all, unsigned long long &s_eval,
+__device__ __forceinline__ void fwd_item(int t, int rbase, Staged *st_all, unsigned long long &s_eval,
                                          const gs_frame *__restrict__ frames, int F,
                                          const uint2 *__restrict__ ranges, const uint32_t *__restrict__ vals,
                                          const float4 *__restrict__ splat, const float *__restrict__ colors,
@@ -215,10 +215,11 @@ __device__ __forceinline__ void fwd_item(int t, int row0, Staged *st_all, unsign
     const int W = fr.width, H = fr.height;
     const int lt = t - fr.tile_offset;
     const int tx = lt % fr.tiles_x, ty = lt / fr.tiles_x;
+    const int y_tile = fr.row0 + ty * TILE;  // image row of the tile's first row (frames may be cropped)
     float xlo, xhi, ylo, yhi;
-    band_of<TILE, RPW>(tx, ty, row0, warp, W, H, xlo, xhi, ylo, yhi);
+    band_of<TILE, RPW>(tx, y_tile, rbase, warp, W, H, xlo, xhi, ylo, yhi);
     const int u = tx * TILE + (int)threadIdx.x % TILE;
-    const int v0 = ty * TILE + row0 + ((int)threadIdx.x / TILE) * PPT;  // first row of the thread's pixels
+    const int v0 = y_tile + rbase + ((int)threadIdx.x / TILE) * PPT;  // first image row of the thread's pixels
     const float px = (float)u;
     float py[PPT], T[PPT], c0[PPT], c1[PPT], c2[PPT];
     int last[PPT];
@@ -298,7 +299,7 @@ __device__ __forceinline__ void fwd_item(int t, int row0, Staged *st_all, unsign
     for (int k = 0; k < PPT; k++) {
         const int v = v0 + k;
         if (!(u < W && v < H)) continue;
-        const long long pix = fr.pixel_offset + (long long)v * W + u;
+        const long long pix = fr.pixel_offset + (long long)(v - fr.row0) * W + u;
         out_rgb[3 * pix] = c0[k] + T[k] * rp.bg0;
         out_rgb[3 * pix + 1] = c1[k] + T[k] * rp.bg1;
         out_rgb[3 * pix + 2] = c2[k] + T[k] * rp.bg2;
@@ -369,9 +370,9 @@ __device__ __forceinline__ float warp_sum8_transposed(const float (&v)[8], int l
     return y;
 }
 
-// Backward of one work item: rows [row0, row0 + ROWS) of tile t.
+// Backward of one work item: rows [rbase, rbase + ROWS) of tile t.
 template <int TILE, int PPT, int NT, int BATCH>
-__device__ __forceinline__ void bwd_item(int t, int row0, Staged *st_all, unsigned long long &s_eval,
+__device__ __forceinline__ void bwd_item(int t, int rbase, Staged *st_all, unsigned long long &s_eval,
                                          const gs_frame *__restrict__ frames, int F,
                                          const uint2 *__restrict__ ranges, const uint32_t *__restrict__ vals,
                                          const float4 *__restrict__ splat, const float *__restrict__ colors,
@@ -386,10 +387,11 @@ __device__ __forceinline__ void bwd_item(int t, int row0, Staged *st_all, unsign
     const int W = fr.width, H = fr.height;
     const int lt = t - fr.tile_offset;
     const int tx = lt % fr.tiles_x, ty = lt / fr.tiles_x;
+    const int y_tile = fr.row0 + ty * TILE;
     float xlo, xhi, ylo, yhi;
-    band_of<TILE, RPW>(tx, ty, row0, warp, W, H, xlo, xhi, ylo, yhi);
+    band_of<TILE, RPW>(tx, y_tile, rbase, warp, W, H, xlo, xhi, ylo, yhi);
     const int u = tx * TILE + (int)threadIdx.x % TILE;
-    const int v0 = ty * TILE + row0 + ((int)threadIdx.x / TILE) * PPT;
+    const int v0 = y_tile + rbase + ((int)threadIdx.x / TILE) * PPT;
     const float px = (float)u;
     if (threadIdx.x == 0) s_eval = 0;
     // the range of this tile; a pixel's start position never exceeds it
@@ -403,7 +405,7 @@ __device__ __forceinline__ void bwd_item(int t, int row0, Staged *st_all, unsign
         const int v = v0 + k;
         py[k] = (float)v;
         if (u < W && v < H) {
-            const long long pix = fr.pixel_offset + (long long)v * W + u;
+            const long long pix = fr.pixel_offset + (long long)(v - fr.row0) * W + u;
             T[k] = in_T[pix];
             last[k] = min(max(in_last[pix], 0), n);
             g0[k] = dL_drgb[3 * pix];

@@ -90,7 +90,8 @@ class Plan:
     """A planned batch of frames with its workspace and image outputs.
 
     frames: list of dicts with width, height, fx, fy, cx, cy, camera_id,
-    traj_id, gauss_offset, gauss_count, timestamp.
+    traj_id, gauss_offset, gauss_count, timestamp and optionally row0 (the
+    first image row rendered; the frame's image is rows [row0, height)).
     """
 
     def __init__(self, frames, num_gaussians, num_cameras, num_trajs, opts: RenderOptions,
@@ -104,6 +105,7 @@ class Plan:
             for k in ("width", "height", "fx", "fy", "cx", "cy", "camera_id", "traj_id", "gauss_offset",
                       "gauss_count", "timestamp"):
                 setattr(arr[i], k, fr[k])
+            arr[i].row0 = fr.get("row0", 0)
         self.frames_host = arr
         self.frames_dev = torch.empty(C.sizeof(capi.GsFrame) * F, dtype=torch.uint8, device=self.device)
         self.batch = capi.gs_batch_init(arr, num_gaussians, num_cameras, num_trajs, opts.tile, pair_capacity,
@@ -129,7 +131,7 @@ class Plan:
             out.append(dict(width=c.width, height=c.height, fx=c.fx, fy=c.fy, cx=c.cx, cy=c.cy,
                             camera_id=f.camera_id, traj_id=f.scene_id,
                             gauss_offset=scene.gauss_offset[f.scene_id],
-                            gauss_count=scene.gauss_count[f.scene_id], timestamp=f.timestamp))
+                            gauss_count=scene.gauss_count[f.scene_id], timestamp=f.timestamp, row0=f.row0))
         return out
 
     @staticmethod
@@ -150,10 +152,12 @@ class Plan:
         return self.frames_host[i]
 
     def image(self, t, i):
-        """View of frame i's pixels of a [P,...] tensor as [H, W, ...]."""
+        """View of frame i's pixels of a [P,...] tensor as [H - row0, W, ...]
+        (image rows row0 .. H-1)."""
         fr = self.frames_host[i]
-        n = fr.width * fr.height
-        return t[fr.pixel_offset:fr.pixel_offset + n].view(fr.height, fr.width, *t.shape[1:])
+        rows = fr.height - fr.row0
+        n = fr.width * rows
+        return t[fr.pixel_offset:fr.pixel_offset + n].view(rows, fr.width, *t.shape[1:])
 
     def ws_view(self, idx, dtype, count, start=0):
         """Typed view of a workspace region (offset index idx, capi.WS_*)."""
@@ -203,7 +207,7 @@ class Plan:
 
 def default_pair_capacity(frames, tile, per_pixel=24.0, minimum=1 << 16):
     """Pair capacity heuristic: per_pixel pairs per pixel of the batch."""
-    px = sum(f["width"] * f["height"] for f in frames)
+    px = sum(f["width"] * (f["height"] - f.get("row0", 0)) for f in frames)
     return int(min(max(minimum, per_pixel * px), (1 << 32) - 1))
 
 
@@ -251,16 +255,22 @@ def render(plan: Plan, scene: DeviceScene, quat, log_scale, logit_opacity, rgb, 
 
 class CalibStep:
     """One calibration iteration (the unit of the benchmark): pose, project,
-    bin + sort, render, L1 loss with its gradient, render/projection
-    backward and pose gradient, for every frame of the plan.  With
-    graph=True the whole iteration is one CUDA-graph replay; all inputs and
-    outputs are static tensors (update them in place)."""
+    bin + sort, render, the loss with its gradient, render/projection
+    backward and pose gradient, for every frame of the plan.  loss="l1" is
+    the L1 term of Eq. 4; loss="photo" is L_photo = (1 - lambda1) L1 +
+    lambda1 D-SSIM (lambda1 = 0.2 in the paper).  With graph=True the whole
+    iteration is one CUDA-graph replay; all inputs and outputs are static
+    tensors (update them in place).  self.loss[0] is the loss; for "photo",
+    self.loss[1:3] are its L1 and D-SSIM parts."""
 
-    def __init__(self, plan: Plan, scene: DeviceScene, target, ext, delta, graph=True):
+    def __init__(self, plan: Plan, scene: DeviceScene, target, ext, delta, graph=True, loss="l1", lambda1=0.2):
+        if loss not in ("l1", "photo"):
+            raise ValueError("loss must be 'l1' or 'photo'")
         self.plan, self.scene = plan, scene
         self.target = target
         self.ext, self.delta = ext, delta
-        self.loss = torch.zeros(1, dtype=torch.float64, device=plan.device)
+        self.kind, self.lambda1 = loss, lambda1
+        self.loss = torch.zeros(3, dtype=torch.float64, device=plan.device)
         self.dL = torch.zeros_like(plan.rgb)
         self.grads = empty_grads(scene, plan.batch.num_cameras)
         self.graph = None
@@ -279,7 +289,10 @@ class CalibStep:
     def _body(self):
         p = self.plan
         p.forward(self.scene, self.ext, self.delta)
-        capi.gs_loss_l1(p.batch, p.rgb, self.target, 1.0, self.loss, self.dL, p.ws)
+        if self.kind == "photo":
+            capi.gs_loss_photo(p.batch, p.rgb, self.target, self.lambda1, self.loss, self.dL, p.ws)
+        else:
+            capi.gs_loss_l1(p.batch, p.rgb, self.target, 1.0, self.loss, self.dL, p.ws)
         p.backward(self.scene, self.dL, self.grads, self.ext)
 
     def __call__(self):
@@ -287,7 +300,7 @@ class CalibStep:
             self.graph.replay()
         else:
             self._body()
-        return self.loss
+        return self.loss[:1]
 
 
 class PerFrameStep:

@@ -69,6 +69,7 @@ class Frame:
     timestamp: float       # t^{n_i}, seconds on the camera clock
     camera_id: int = 0     # which extrinsic / time offset
     scene_id: int = 0      # which scene (Gaussians + trajectory)
+    row0: int = 0          # first image row used (height // 2: the bottom half, Sec. III-D)
 
 
 @dataclass

@@ -37,13 +37,13 @@ def last_gaussian_ids(plan, frame_i):
     """Gaussian id (within the scene) of each pixel's last composited
     Gaussian, -1 if none, as [H*W] from the GPU's sorted pairs."""
     fr = plan.frame(frame_i)
-    H, W, T = fr.height, fr.width, plan.opts.tile
+    H, W, T = fr.height - fr.row0, fr.width, plan.opts.tile  # rows of the (cropped) image
     last = plan.image(plan.last, frame_i).cpu().numpy().reshape(-1)
     P = int(plan.stats().num_pairs)
     vals = plan.ws_view(capi.WS_VALS, torch.int32, max(P, 1)).cpu().numpy().view(np.uint32)
     ranges = plan.ws_view(capi.WS_RANGES, torch.int32, 2 * plan.batch.num_tiles).cpu().numpy().view(np.uint32)
     ranges = ranges.reshape(-1, 2)
-    v, u = np.divmod(np.arange(H * W), W)
+    v, u = np.divmod(np.arange(H * W), W)  # v counted from the first rendered row
     tile = fr.tile_offset + (v // T) * fr.tiles_x + (u // T)
     out = np.full(H * W, -1, np.int64)
     has = last > 0
