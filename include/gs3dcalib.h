@@ -188,7 +188,8 @@ enum {
     GS_PROF_BIN_SORT = 2,
     GS_PROF_RENDER_FWD = 3,
     GS_PROF_RENDER_BWD = 4,
-    GS_PROF_PROJECT_BWD = 5
+    GS_PROF_PROJECT_BWD = 5,
+    GS_PROF_LOSS = 6
 };
 /* Kernel timing hook.  After this call, every launch of the selected
  * kernel is bracketed by records of the start/stop events on the kernel's
@@ -198,7 +199,8 @@ enum {
  * kernel: GS_PROF_NONE (0) disables the hook; GS_PROF_PROJECT,
  * GS_PROF_BIN_SORT (the whole binning and sorting sequence),
  * GS_PROF_RENDER_FWD, GS_PROF_RENDER_BWD (the compositing backward only),
- * GS_PROF_PROJECT_BWD.  The events are cudaEvent_t handles owned by the
+ * GS_PROF_PROJECT_BWD, GS_PROF_LOSS (gs_loss_l1 or gs_loss_photo).  The
+ * events are cudaEvent_t handles owned by the
  * caller (created with timing enabled).  Process-wide setting; not thread
  * safe.  Errors: GS_ERR_INVALID_ARG for an unknown kernel or NULL events. */
 gs_status gs_profile_events(int32_t kernel, void *start_event, void *stop_event);

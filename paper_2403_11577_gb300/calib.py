@@ -6,7 +6,10 @@ the means stay at the LiDAR points, Sec. III-B), the camera-to-LiDAR
 extrinsic and the time offset with Adam, against target images rendered at
 the true calibration:
 
-  L_total = L_1 + lambda_2 * L_scale          (Eq. 4 with its L1 term, Eq. 7-8)
+  L_total = L_photo + lambda_2 * L_scale      (Eq. 4, 7-8)
+  L_photo = L1 (loss="l1") or (1 - lambda_1) L1 + lambda_1 D-SSIM with
+            lambda_1 = 0.2 (loss="photo", Eq. 4), optionally on the bottom
+            half of each image only (crop, Sec. III-D)
   L_scale = sum_g || s_g - mean(s_g) ||_1     (activated scales, lambda_2 = 1e-3)
 
 Learning rates follow Sec. IV-B (rotation 1e-4, translation 5e-3, time
@@ -47,7 +50,7 @@ def errors(ext, delta, ext_true, delta_true):
 
 def run_calibration(problem, iters=3000, warmup=500, lr_rot=1e-4, lr_trans=5e-3, lr_delta=1e-3,
                     lambda_scale=1e-3, opts=None, seed=0, log_every=250, reinit=True, train_scene=True,
-                    scene_lr_scale=1.0, device="cuda"):
+                    scene_lr_scale=1.0, device="cuda", loss="l1"):
     """Calibrate camera 0 of `problem` (its ext/delta are the start,
     ext_target/delta_target the truth).  train_scene=False keeps the
     Gaussian attributes fixed (calibration only).  Returns a dict with the
@@ -72,7 +75,7 @@ def run_calibration(problem, iters=3000, warmup=500, lr_rot=1e-4, lr_trans=5e-3,
         scene.quat[:, 0] = 1.0
     ext = torch.tensor(problem.ext, dtype=torch.float64, device=dev)
     delta = torch.tensor(problem.delta, dtype=torch.float64, device=dev)
-    step = render.CalibStep(plan, scene, target, ext, delta, graph=True)
+    step = render.CalibStep(plan, scene, target, ext, delta, graph=True, loss=loss)
     params = {k: getattr(scene, k) for k in GAUSS_LR}
     for t in params.values():
         t.grad = torch.zeros_like(t)
@@ -143,16 +146,22 @@ def main():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--gaussians", type=int, default=1_000_000)
     ap.add_argument("--trajectory", choices=["straight", "zigzag"], default="zigzag")
+    ap.add_argument("--loss", choices=["l1", "photo"], default="l1",
+                    help="l1, or L_photo = 0.8 L1 + 0.2 D-SSIM (Eq. 4)")
+    ap.add_argument("--crop", action="store_true", help="losses on the bottom half of each image (Sec. III-D)")
     ap.add_argument("--mode", choices=["joint", "pose"], default="joint",
                     help="joint: re-initialised scene trained with the calibration; "
                          "pose: the scene's attributes fixed at their true values")
     a = ap.parse_args()
     p = scenes.calibration_problem(seed=a.seed, n=a.gaussians, trajectory=a.trajectory)
+    if a.crop:
+        for f in p.frames:
+            f.row0 = f.camera.height // 2
     if a.mode == "pose":
-        res = run_calibration(p, iters=a.iters, warmup=0, seed=a.seed, reinit=False, train_scene=False)
+        res = run_calibration(p, iters=a.iters, warmup=0, seed=a.seed, reinit=False, train_scene=False, loss=a.loss)
     else:
-        res = run_calibration(p, iters=a.iters, warmup=a.warmup, seed=a.seed, reinit=True)
-    res.update(trajectory=a.trajectory, mode=a.mode, seed=a.seed, gaussians=a.gaussians)
+        res = run_calibration(p, iters=a.iters, warmup=a.warmup, seed=a.seed, reinit=True, loss=a.loss)
+    res.update(trajectory=a.trajectory, mode=a.mode, seed=a.seed, gaussians=a.gaussians, loss=a.loss, crop=a.crop)
     print(json.dumps(res))
 
 

@@ -45,7 +45,8 @@ class GsStats(C.Structure):
 
 GS_OK, GS_ERR_INVALID_ARG, GS_ERR_CAPACITY, GS_ERR_CUDA, GS_ERR_UNSUPPORTED = 0, 1, 2, 3, 4
 GS_DEV_PAIR_OVERFLOW, GS_DEV_NONFINITE = 1, 2
-GS_PROF_NONE, GS_PROF_PROJECT, GS_PROF_BIN_SORT, GS_PROF_RENDER_FWD, GS_PROF_RENDER_BWD, GS_PROF_PROJECT_BWD = range(6)
+(GS_PROF_NONE, GS_PROF_PROJECT, GS_PROF_BIN_SORT, GS_PROF_RENDER_FWD, GS_PROF_RENDER_BWD, GS_PROF_PROJECT_BWD,
+ GS_PROF_LOSS) = range(7)
 WS_STATS, WS_POSE32, WS_POSE64, WS_RECT, WS_DEPTH, WS_SPLAT, WS_GRAD2D, WS_KEYS, WS_VALS, WS_RANGES = range(10)
 
 _P = C.c_void_p

@@ -123,7 +123,7 @@ extern "C" {
 const char *gs_version(void) { return "gs3dcalib 0.1.0 (sm_103a)"; }
 
 gs_status gs_profile_events(int32_t kernel, void *start_event, void *stop_event) {
-    if (kernel < GS_PROF_NONE || kernel > GS_PROF_PROJECT_BWD) return GS_ERR_INVALID_ARG;
+    if (kernel < GS_PROF_NONE || kernel > GS_PROF_LOSS) return GS_ERR_INVALID_ARG;
     if (kernel != GS_PROF_NONE && (!start_event || !stop_event)) return GS_ERR_INVALID_ARG;
     g_prof_kernel = kernel;
     g_prof_start = reinterpret_cast<cudaEvent_t>(start_event);
@@ -273,8 +273,11 @@ gs_status gs_loss_l1(const gs_batch *b, const float *rgb, const float *target, i
                      double *out_loss, float *out_grad, void *ws, void *stream) {
     Layout L;
     if (!batch_ok(b, ws) || !make_layout(b, &L) || !rgb || !target || !out_loss || n < 0) return GS_ERR_INVALID_ARG;
-    return cuda_status(launch_l1(rgb, target, n, scale, out_loss, out_grad, (double *)(W(ws) + L.loss_part),
-                                 S(stream)));
+    cudaError_t e = prof_mark(GS_PROF_LOSS, true, S(stream));
+    if (e == cudaSuccess)
+        e = launch_l1(rgb, target, n, scale, out_loss, out_grad, (double *)(W(ws) + L.loss_part), S(stream));
+    if (e == cudaSuccess) e = prof_mark(GS_PROF_LOSS, false, S(stream));
+    return cuda_status(e);
 }
 
 gs_status gs_loss_photo(const gs_batch *b, const float *rgb, const float *target, float lambda1, float scale,
@@ -285,8 +288,12 @@ gs_status gs_loss_photo(const gs_batch *b, const float *rgb, const float *target
         return GS_ERR_INVALID_ARG;
     if (b->num_pixels > 0 && (!rgb || !target)) return GS_ERR_INVALID_ARG;
     unsigned char *w = W(ws);
-    return cuda_status(launch_photo(b, rgb, target, lambda1, scale, out_loss, out_grad, (float *)(w + L.photo_maps),
-                                    (double *)(w + L.photo_part), S(stream)));
+    cudaError_t e = prof_mark(GS_PROF_LOSS, true, S(stream));
+    if (e == cudaSuccess)
+        e = launch_photo(b, rgb, target, lambda1, scale, out_loss, out_grad, (float *)(w + L.photo_maps),
+                         (double *)(w + L.photo_part), S(stream));
+    if (e == cudaSuccess) e = prof_mark(GS_PROF_LOSS, false, S(stream));
+    return cuda_status(e);
 }
 
 gs_status gs_render_bwd(const gs_batch *b, const float *X, const float *quat, const float *log_scale,
