@@ -14,10 +14,10 @@
 //   d(mean SSIM)/da(p) = (1/n) [ G*(S_mu - 2 mu_a S_aa - mu_b S_ab) + 2 a(p) G*S_aa
 //                                + b(p) G*S_ab ](p).
 //
-// k_ssim_fwd: one block per render tile (its TR x TR pixels); per channel
-// the rendered and target values of the tile and a 5-pixel halo are staged
-// in shared memory, the five moments are filtered separably (11 taps along
-// rows, then along columns), and the three maps A1 = S_mu - 2 mu_a S_aa -
+// k_ssim_fwd: one block per render tile (its TR x TR pixels); the rendered
+// and target values of the tile and a 5-pixel halo are staged in shared
+// memory, the five moments of each channel are filtered separably (11 taps
+// along rows, then along columns), and the three maps A1 = S_mu - 2 mu_a S_aa -
 // mu_b S_ab, A2 = S_aa, A3 = S_ab are written to the workspace (planar:
 // map (3 ch + k) holds A_{k+1} of channel ch for every pixel) with FP64
 // per-block partial sums of SSIM and |a - b|.  k_ssim_bwd filters the maps
@@ -41,16 +41,16 @@ struct SsimWindow {
 template <int TR>
 struct FwdSmem {
     static constexpr int E = TR + 2 * kWin;
-    float in[2][E][E];    // rendered, target
-    float h[5][E][TR];    // row-filtered a, b, a^2, b^2, ab
+    float in[6][E][E];    // rendered r, g, b, target r, g, b
+    float h[15][E][TR];   // row-filtered a, b, a^2, b^2, ab per channel
     double red[2][kPhotoThreads / 32];
 };
 
 template <int TR>
 struct BwdSmem {
     static constexpr int E = TR + 2 * kWin;
-    float in[3][E][E];    // A1, A2, A3
-    float h[3][E][TR];
+    float in[9][E][E];    // A1, A2, A3 per channel
+    float h[9][E][TR];
 };
 
 // Frame f, image rows R = height - row0 and the tile's first (row, column).
@@ -72,74 +72,79 @@ __device__ __forceinline__ TileGeom tile_geom(const gs_frame *__restrict__ frame
     return g;
 }
 
+// The three channels are filtered together: one staging round, one
+// row-filter round and one column-filter round per block.
 template <int TR>
 __global__ void __launch_bounds__(kPhotoThreads)
 k_ssim_fwd(const gs_frame *__restrict__ frames, int F, long long P, const float *__restrict__ x,
            const float *__restrict__ y, SsimWindow G, float *__restrict__ maps, double *__restrict__ part) {
     constexpr int E = FwdSmem<TR>::E;
-    __shared__ FwdSmem<TR> S;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    FwdSmem<TR> &S = *reinterpret_cast<FwdSmem<TR> *>(smem_raw);
     const TileGeom g = tile_geom<TR>(frames, F, blockIdx.x);
     const long long pix0 = g.fr->pixel_offset;
     const float C1 = 0.01f * 0.01f, C2 = 0.03f * 0.03f;
     double ssim_acc = 0.0, l1_acc = 0.0;
-    for (int ch = 0; ch < 3; ch++) {
-        for (int i = threadIdx.x; i < E * E; i += kPhotoThreads) {
-            const int rr = g.r0 - kWin + i / E, cc = g.c0 - kWin + i % E;
-            const bool in = rr >= 0 && rr < g.R && cc >= 0 && cc < g.W;
-            const long long v = 3 * (pix0 + (long long)rr * g.W + cc) + ch;
-            S.in[0][i / E][i % E] = in ? x[v] : 0.f;
-            S.in[1][i / E][i % E] = in ? y[v] : 0.f;
-        }
-        __syncthreads();
-        for (int i = threadIdx.x; i < E * TR; i += kPhotoThreads) {
-            const int r = i / TR, c = i % TR;
-            float sa = 0.f, sb = 0.f, saa = 0.f, sbb = 0.f, sab = 0.f;
+    for (int i = threadIdx.x; i < E * E; i += kPhotoThreads) {
+        const int rr = g.r0 - kWin + i / E, cc = g.c0 - kWin + i % E;
+        const bool in = rr >= 0 && rr < g.R && cc >= 0 && cc < g.W;
+        const long long v = 3 * (pix0 + (long long)rr * g.W + cc);
 #pragma unroll
-            for (int k = 0; k < 2 * kWin + 1; k++) {
-                const float a = S.in[0][r][c + k], b = S.in[1][r][c + k], w = G.w[k];
-                sa = fmaf(w, a, sa);
-                sb = fmaf(w, b, sb);
-                saa = fmaf(w * a, a, saa);
-                sbb = fmaf(w * b, b, sbb);
-                sab = fmaf(w * a, b, sab);
-            }
-            S.h[0][r][c] = sa;
-            S.h[1][r][c] = sb;
-            S.h[2][r][c] = saa;
-            S.h[3][r][c] = sbb;
-            S.h[4][r][c] = sab;
+        for (int ch = 0; ch < 3; ch++) {
+            S.in[ch][i / E][i % E] = in ? x[v + ch] : 0.f;
+            S.in[3 + ch][i / E][i % E] = in ? y[v + ch] : 0.f;
         }
-        __syncthreads();
-        for (int i = threadIdx.x; i < TR * TR; i += kPhotoThreads) {
-            const int r = i / TR, c = i % TR;
-            const int rr = g.r0 + r, cc = g.c0 + c;
-            if (rr >= g.R || cc >= g.W) continue;
-            float ma = 0.f, mb = 0.f, eaa = 0.f, ebb = 0.f, eab = 0.f;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 3 * E * TR; i += kPhotoThreads) {
+        const int ch = i / (E * TR), j = i % (E * TR);
+        const int r = j / TR, c = j % TR;
+        float sa = 0.f, sb = 0.f, saa = 0.f, sbb = 0.f, sab = 0.f;
 #pragma unroll
-            for (int k = 0; k < 2 * kWin + 1; k++) {
-                const float w = G.w[k];
-                ma = fmaf(w, S.h[0][r + k][c], ma);
-                mb = fmaf(w, S.h[1][r + k][c], mb);
-                eaa = fmaf(w, S.h[2][r + k][c], eaa);
-                ebb = fmaf(w, S.h[3][r + k][c], ebb);
-                eab = fmaf(w, S.h[4][r + k][c], eab);
-            }
-            const float s_aa = eaa - ma * ma, s_bb = ebb - mb * mb, s_ab = eab - ma * mb;
-            const float A = 2.f * ma * mb + C1, B = 2.f * s_ab + C2;
-            const float Cc = ma * ma + mb * mb + C1, D = s_aa + s_bb + C2;
-            const float inv = 1.f / (Cc * D);
-            const float ssim = A * B * inv;
-            const float S_mu = 2.f * mb * B * inv - 2.f * ma * ssim / Cc;
-            const float S_aa = -ssim / D;
-            const float S_ab = 2.f * A * inv;
-            const long long p = pix0 + (long long)rr * g.W + cc;
-            maps[(3 * ch) * P + p] = S_mu - 2.f * ma * S_aa - mb * S_ab;
-            maps[(3 * ch + 1) * P + p] = S_aa;
-            maps[(3 * ch + 2) * P + p] = S_ab;
-            ssim_acc += (double)ssim;
-            l1_acc += (double)fabsf(S.in[0][r + kWin][c + kWin] - S.in[1][r + kWin][c + kWin]);
+        for (int k = 0; k < 2 * kWin + 1; k++) {
+            const float a = S.in[ch][r][c + k], b = S.in[3 + ch][r][c + k], w = G.w[k];
+            sa = fmaf(w, a, sa);
+            sb = fmaf(w, b, sb);
+            saa = fmaf(w * a, a, saa);
+            sbb = fmaf(w * b, b, sbb);
+            sab = fmaf(w * a, b, sab);
         }
-        __syncthreads();
+        S.h[5 * ch][r][c] = sa;
+        S.h[5 * ch + 1][r][c] = sb;
+        S.h[5 * ch + 2][r][c] = saa;
+        S.h[5 * ch + 3][r][c] = sbb;
+        S.h[5 * ch + 4][r][c] = sab;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 3 * TR * TR; i += kPhotoThreads) {
+        const int ch = i / (TR * TR), j = i % (TR * TR);
+        const int r = j / TR, c = j % TR;
+        const int rr = g.r0 + r, cc = g.c0 + c;
+        if (rr >= g.R || cc >= g.W) continue;
+        float ma = 0.f, mb = 0.f, eaa = 0.f, ebb = 0.f, eab = 0.f;
+#pragma unroll
+        for (int k = 0; k < 2 * kWin + 1; k++) {
+            const float w = G.w[k];
+            ma = fmaf(w, S.h[5 * ch][r + k][c], ma);
+            mb = fmaf(w, S.h[5 * ch + 1][r + k][c], mb);
+            eaa = fmaf(w, S.h[5 * ch + 2][r + k][c], eaa);
+            ebb = fmaf(w, S.h[5 * ch + 3][r + k][c], ebb);
+            eab = fmaf(w, S.h[5 * ch + 4][r + k][c], eab);
+        }
+        const float s_aa = eaa - ma * ma, s_bb = ebb - mb * mb, s_ab = eab - ma * mb;
+        const float A = 2.f * ma * mb + C1, B = 2.f * s_ab + C2;
+        const float Cc = ma * ma + mb * mb + C1, D = s_aa + s_bb + C2;
+        const float inv = 1.f / (Cc * D);
+        const float ssim = A * B * inv;
+        const float S_mu = 2.f * mb * B * inv - 2.f * ma * ssim / Cc;
+        const float S_aa = -ssim / D;
+        const float S_ab = 2.f * A * inv;
+        const long long p = pix0 + (long long)rr * g.W + cc;
+        maps[(3 * ch) * P + p] = S_mu - 2.f * ma * S_aa - mb * S_ab;
+        maps[(3 * ch + 1) * P + p] = S_aa;
+        maps[(3 * ch + 2) * P + p] = S_ab;
+        ssim_acc += (double)ssim;
+        l1_acc += (double)fabsf(S.in[ch][r + kWin][c + kWin] - S.in[3 + ch][r + kWin][c + kWin]);
     }
     for (int s = 16; s > 0; s >>= 1) {
         ssim_acc += __shfl_xor_sync(0xffffffffu, ssim_acc, s);
@@ -168,53 +173,52 @@ k_ssim_bwd(const gs_frame *__restrict__ frames, int F, long long P, const float 
            const float *__restrict__ y, SsimWindow G, const float *__restrict__ maps, float inv_n, float lambda1,
            float scale, float *__restrict__ grad) {
     constexpr int E = BwdSmem<TR>::E;
-    __shared__ BwdSmem<TR> S;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    BwdSmem<TR> &S = *reinterpret_cast<BwdSmem<TR> *>(smem_raw);
     const TileGeom g = tile_geom<TR>(frames, F, blockIdx.x);
     const long long pix0 = g.fr->pixel_offset;
-    for (int ch = 0; ch < 3; ch++) {
-        for (int i = threadIdx.x; i < E * E; i += kPhotoThreads) {
-            const int rr = g.r0 - kWin + i / E, cc = g.c0 - kWin + i % E;
-            const bool in = rr >= 0 && rr < g.R && cc >= 0 && cc < g.W;
-            const long long p = pix0 + (long long)rr * g.W + cc;
-            S.in[0][i / E][i % E] = in ? maps[(3 * ch) * P + p] : 0.f;
-            S.in[1][i / E][i % E] = in ? maps[(3 * ch + 1) * P + p] : 0.f;
-            S.in[2][i / E][i % E] = in ? maps[(3 * ch + 2) * P + p] : 0.f;
-        }
-        __syncthreads();
-        for (int i = threadIdx.x; i < E * TR; i += kPhotoThreads) {
-            const int r = i / TR, c = i % TR;
-            float s1 = 0.f, s2 = 0.f, s3 = 0.f;
+    for (int i = threadIdx.x; i < E * E; i += kPhotoThreads) {
+        const int rr = g.r0 - kWin + i / E, cc = g.c0 - kWin + i % E;
+        const bool in = rr >= 0 && rr < g.R && cc >= 0 && cc < g.W;
+        const long long p = pix0 + (long long)rr * g.W + cc;
 #pragma unroll
-            for (int k = 0; k < 2 * kWin + 1; k++) {
-                const float w = G.w[k];
-                s1 = fmaf(w, S.in[0][r][c + k], s1);
-                s2 = fmaf(w, S.in[1][r][c + k], s2);
-                s3 = fmaf(w, S.in[2][r][c + k], s3);
-            }
-            S.h[0][r][c] = s1;
-            S.h[1][r][c] = s2;
-            S.h[2][r][c] = s3;
-        }
-        __syncthreads();
-        for (int i = threadIdx.x; i < TR * TR; i += kPhotoThreads) {
-            const int r = i / TR, c = i % TR;
-            const int rr = g.r0 + r, cc = g.c0 + c;
-            if (rr >= g.R || cc >= g.W) continue;
-            float g1 = 0.f, g2 = 0.f, g3 = 0.f;
+        for (int m = 0; m < 9; m++) S.in[m][i / E][i % E] = in ? maps[m * P + p] : 0.f;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 3 * E * TR; i += kPhotoThreads) {
+        const int ch = i / (E * TR), j = i % (E * TR);
+        const int r = j / TR, c = j % TR;
+        float s1 = 0.f, s2 = 0.f, s3 = 0.f;
 #pragma unroll
-            for (int k = 0; k < 2 * kWin + 1; k++) {
-                const float w = G.w[k];
-                g1 = fmaf(w, S.h[0][r + k][c], g1);
-                g2 = fmaf(w, S.h[1][r + k][c], g2);
-                g3 = fmaf(w, S.h[2][r + k][c], g3);
-            }
-            const long long v = 3 * (pix0 + (long long)rr * g.W + cc) + ch;
-            const float a = x[v], b = y[v];
-            const float d_ssim = (g1 + 2.f * a * g2 + b * g3) * inv_n;  // d(mean SSIM)/da
-            const float d_l1 = (a > b ? inv_n : (a < b ? -inv_n : 0.f));
-            grad[v] = scale * ((1.f - lambda1) * d_l1 - lambda1 * d_ssim);
+        for (int k = 0; k < 2 * kWin + 1; k++) {
+            const float w = G.w[k];
+            s1 = fmaf(w, S.in[3 * ch][r][c + k], s1);
+            s2 = fmaf(w, S.in[3 * ch + 1][r][c + k], s2);
+            s3 = fmaf(w, S.in[3 * ch + 2][r][c + k], s3);
         }
-        __syncthreads();
+        S.h[3 * ch][r][c] = s1;
+        S.h[3 * ch + 1][r][c] = s2;
+        S.h[3 * ch + 2][r][c] = s3;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 3 * TR * TR; i += kPhotoThreads) {
+        const int ch = i / (TR * TR), j = i % (TR * TR);
+        const int r = j / TR, c = j % TR;
+        const int rr = g.r0 + r, cc = g.c0 + c;
+        if (rr >= g.R || cc >= g.W) continue;
+        float g1 = 0.f, g2 = 0.f, g3 = 0.f;
+#pragma unroll
+        for (int k = 0; k < 2 * kWin + 1; k++) {
+            const float w = G.w[k];
+            g1 = fmaf(w, S.h[3 * ch][r + k][c], g1);
+            g2 = fmaf(w, S.h[3 * ch + 1][r + k][c], g2);
+            g3 = fmaf(w, S.h[3 * ch + 2][r + k][c], g3);
+        }
+        const long long v = 3 * (pix0 + (long long)rr * g.W + cc) + ch;
+        const float a = x[v], b = y[v];
+        const float d_ssim = (g1 + 2.f * a * g2 + b * g3) * inv_n;  // d(mean SSIM)/da
+        const float d_l1 = (a > b ? inv_n : (a < b ? -inv_n : 0.f));
+        grad[v] = scale * ((1.f - lambda1) * d_l1 - lambda1 * d_ssim);
     }
 }
 
@@ -262,11 +266,15 @@ cudaError_t run_photo(const gs_batch *b, const float *x, const float *y, float l
     const SsimWindow G = make_window();
     const int T = b->num_tiles;
     const double n = 3.0 * (double)b->num_pixels;
-    k_ssim_fwd<TR><<<T, kPhotoThreads, 0, s>>>(b->frames_dev, b->num_frames, b->num_pixels, x, y, G, maps, part);
+    constexpr int fs = (int)sizeof(FwdSmem<TR>), bs = (int)sizeof(BwdSmem<TR>);
+    cudaError_t e = cudaFuncSetAttribute(k_ssim_fwd<TR>, cudaFuncAttributeMaxDynamicSharedMemorySize, fs);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_ssim_bwd<TR>, cudaFuncAttributeMaxDynamicSharedMemorySize, bs);
+    if (e != cudaSuccess) return e;
+    k_ssim_fwd<TR><<<T, kPhotoThreads, fs, s>>>(b->frames_dev, b->num_frames, b->num_pixels, x, y, G, maps, part);
     k_photo_final<<<1, 256, 0, s>>>(part, T, n, (double)lambda1, out);
     if (grad)
-        k_ssim_bwd<TR><<<T, kPhotoThreads, 0, s>>>(b->frames_dev, b->num_frames, b->num_pixels, x, y, G, maps,
-                                                   n > 0 ? (float)(1.0 / n) : 0.f, lambda1, scale, grad);
+        k_ssim_bwd<TR><<<T, kPhotoThreads, bs, s>>>(b->frames_dev, b->num_frames, b->num_pixels, x, y, G, maps,
+                                                    n > 0 ? (float)(1.0 / n) : 0.f, lambda1, scale, grad);
     return cudaGetLastError();
 }
 
