@@ -43,16 +43,27 @@ def rotation_error_deg(omega_a, omega_b):
 
 
 def errors(ext, delta, ext_true, delta_true):
+    """Calibration errors of one camera."""
     return {"rot_deg": rotation_error_deg(ext[:3], ext_true[:3]),
             "trans_cm": float(100 * np.linalg.norm(ext[3:] - ext_true[3:])),
             "delta_ms": float(1000 * abs(delta - delta_true))}
 
 
+def rig_errors(ext, delta, ext_true, delta_true):
+    """Worst error over the cameras, plus the per-camera errors when there
+    is more than one camera."""
+    per = [errors(ext[c], float(delta[c]), ext_true[c], float(delta_true[c])) for c in range(len(ext))]
+    out = {k: max(e[k] for e in per) for k in per[0]}
+    if len(per) > 1:
+        out["cameras"] = per
+    return out
+
+
 def run_calibration(problem, iters=3000, warmup=500, lr_rot=1e-4, lr_trans=5e-3, lr_delta=1e-3,
                     lambda_scale=1e-3, opts=None, seed=0, log_every=250, reinit=True, train_scene=True,
                     scene_lr_scale=1.0, device="cuda", loss="l1"):
-    """Calibrate camera 0 of `problem` (its ext/delta are the start,
-    ext_target/delta_target the truth).  train_scene=False keeps the
+    """Calibrate every camera of `problem` (its ext/delta are the start,
+    ext_target/delta_target the truth; errors are the worst over cameras).  train_scene=False keeps the
     Gaussian attributes fixed (calibration only).  Returns a dict with the
     error history, the final errors and the wall time."""
     build.build()
@@ -91,7 +102,7 @@ def run_calibration(problem, iters=3000, warmup=500, lr_rot=1e-4, lr_trans=5e-3,
                                 {"params": [delta_p], "lr": lr_delta}], eps=1e-15)
     base_lrs = [g["lr"] for g in opt_cal.param_groups]
     history = []
-    e_true_np, d_true_np = problem.ext_target[0], float(problem.delta_target[0])
+    e_true_np, d_true_np = np.asarray(problem.ext_target), np.asarray(problem.delta_target)
     torch.cuda.synchronize()
     t0 = time.time()
     for it in range(iters):
@@ -126,15 +137,15 @@ def run_calibration(problem, iters=3000, warmup=500, lr_rot=1e-4, lr_trans=5e-3,
                 q = params["quat"]
                 q.div_(q.norm(dim=1, keepdim=True).clamp_min(1e-8))
         if log_every and (it % log_every == 0 or it == iters - 1):
-            e_np = torch.cat([rot, trans], 1)[0].cpu().numpy()
-            err = errors(e_np, float(delta_p[0]), e_true_np, d_true_np)
+            e_np = torch.cat([rot, trans], 1).cpu().numpy()
+            err = rig_errors(e_np, delta_p.cpu().numpy(), e_true_np, d_true_np)
             err.update(it=it, loss=float(loss.item()))
             history.append(err)
     torch.cuda.synchronize()
     wall = time.time() - t0
-    e_np = torch.cat([rot, trans], 1)[0].cpu().numpy()
-    final = errors(e_np, float(delta_p[0]), e_true_np, d_true_np)
-    start = errors(problem.ext[0], float(problem.delta[0]), e_true_np, d_true_np)
+    e_np = torch.cat([rot, trans], 1).cpu().numpy()
+    final = rig_errors(e_np, delta_p.cpu().numpy(), e_true_np, d_true_np)
+    start = rig_errors(np.asarray(problem.ext), np.asarray(problem.delta), e_true_np, d_true_np)
     return {"start": start, "final": final, "wall_s": wall, "iters": iters, "warmup": warmup,
             "history": history, "ms_per_iter": 1e3 * wall / iters}
 
@@ -149,11 +160,12 @@ def main():
     ap.add_argument("--loss", choices=["l1", "photo"], default="l1",
                     help="l1, or L_photo = 0.8 L1 + 0.2 D-SSIM (Eq. 4)")
     ap.add_argument("--crop", action="store_true", help="losses on the bottom half of each image (Sec. III-D)")
+    ap.add_argument("--cameras", type=int, default=1, help="forward cameras of the rig, calibrated jointly")
     ap.add_argument("--mode", choices=["joint", "pose"], default="joint",
                     help="joint: re-initialised scene trained with the calibration; "
                          "pose: the scene's attributes fixed at their true values")
     a = ap.parse_args()
-    p = scenes.calibration_problem(seed=a.seed, n=a.gaussians, trajectory=a.trajectory)
+    p = scenes.calibration_problem(seed=a.seed, n=a.gaussians, trajectory=a.trajectory, cameras=a.cameras)
     if a.crop:
         for f in p.frames:
             f.row0 = f.camera.height // 2
@@ -161,7 +173,8 @@ def main():
         res = run_calibration(p, iters=a.iters, warmup=0, seed=a.seed, reinit=False, train_scene=False, loss=a.loss)
     else:
         res = run_calibration(p, iters=a.iters, warmup=a.warmup, seed=a.seed, reinit=True, loss=a.loss)
-    res.update(trajectory=a.trajectory, mode=a.mode, seed=a.seed, gaussians=a.gaussians, loss=a.loss, crop=a.crop)
+    res.update(trajectory=a.trajectory, mode=a.mode, seed=a.seed, gaussians=a.gaussians, loss=a.loss, crop=a.crop,
+               cameras=a.cameras)
     print(json.dumps(res))
 
 

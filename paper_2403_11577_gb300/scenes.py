@@ -378,24 +378,52 @@ def uneven_problem(seed: int = 3, sizes=(300_000, 1_000_000, 3_000_000),
     return Problem("uneven", scenes, frames, np.array(exts), np.full(len(sizes), 0.04), tile=16)
 
 
+STEREO_BASELINE = 0.6  # metres between the two front cameras of a rig (KITTI-360 scale)
+
+
+def rig_extrinsics(rng, cameras: int):
+    """True extrinsics of `cameras` forward cameras on one car: the nominal
+    mounting, each with its own seeded 2 deg tilt, spaced STEREO_BASELINE to
+    the left (LiDAR +y) of one another; and true time offsets 0, 20, 40 ms..."""
+    exts = []
+    for c in range(cameras):
+        e = _true_extrinsic(rng)
+        e[4] += c * STEREO_BASELINE
+        exts.append(e)
+    return np.array(exts), 0.02 * np.arange(cameras)
+
+
 def calibration_problem(seed: int = 0, n: int = 1_000_000, frames: int = 8,
                         rot_deg: float = 5.0, trans_m: float = 0.5,
-                        delta0: float = 0.05, scene_seed: int = 2, trajectory: str = "straight") -> Problem:
+                        delta0: float = 0.05, scene_seed: int = 2, trajectory: str = "straight",
+                        cameras: int = 1) -> Problem:
     """The batched scene; targets at the true extrinsic and delta = 0, start
     from the extrinsic perturbed by rot_deg about a seeded axis and trans_m
     along a seeded direction, and delta = delta0.  On the straight drive a
     time offset and a translation along the motion are interchangeable; the
-    zigzag drive makes both observable."""
+    zigzag drive makes both observable.
+
+    cameras > 1: a rig of forward cameras on one scene (rig_extrinsics),
+    `frames` frames per camera at the same timestamps, each camera with its
+    own true extrinsic and time offset and its own seeded start (the same
+    rot_deg / trans_m distance, delta0 above its true offset)."""
     base = batched_problem(scene_seed, n, frames, trajectory=trajectory)
     rng = np.random.default_rng(1000 + seed)
-    true = base.ext[0]
-    omega0 = _perturb_rotvec(rng, true[:3], rot_deg)
-    t0 = true[3:] + trans_m * _unit(rng, 1, 3)[0]
-    base.name = "calibration"
-    base.ext_target = base.ext.copy()
-    base.delta_target = np.zeros(1)
-    base.ext = np.concatenate([omega0, t0])[None]
-    base.delta = np.array([delta0])
+    if cameras == 1:
+        true, true_delta = base.ext.copy(), np.zeros(1)
+    else:
+        true, true_delta = rig_extrinsics(np.random.default_rng(2000 + scene_seed), cameras)
+        base.frames = [Frame(f.camera, f.timestamp, camera_id=c) for c in range(cameras) for f in base.frames]
+    start = []
+    for c in range(cameras):
+        omega0 = _perturb_rotvec(rng, true[c, :3], rot_deg)
+        t0 = true[c, 3:] + trans_m * _unit(rng, 1, 3)[0]
+        start.append(np.concatenate([omega0, t0]))
+    base.name = "calibration" if cameras == 1 else "rig calibration"
+    base.ext_target = true
+    base.delta_target = true_delta
+    base.ext = np.array(start)
+    base.delta = true_delta + delta0
     return base
 
 

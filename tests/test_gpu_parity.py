@@ -710,3 +710,38 @@ def test_calibration_recovers_pose_on_small_zigzag_scene():
     assert res["start"]["rot_deg"] > 0.9
     fin = res["final"]
     assert fin["rot_deg"] < 0.05 and fin["trans_cm"] < 1.0 and fin["delta_ms"] < 1.0, fin
+
+
+def _small_rig(n=4000, frames=2, seed=0):
+    p = scenes.calibration_problem(seed=seed, n=n, frames=frames, cameras=2, trajectory="zigzag")
+    for f in p.frames:
+        f.camera = scenes.Camera(176, 47, 69.0, 69.0, 85.25, 29.75)
+    return p
+
+
+def test_render_bwd_two_camera_rig():
+    """Two forward cameras of one rig (60 cm apart, their own extrinsics and
+    time offsets) on one scene in one batch: per-camera extrinsic and delta
+    gradients and the shared Gaussian gradients against the oracle."""
+    p = _small_rig()
+    p.ext = p.ext_target.copy()
+    p.ext[1, :3] += 0.01
+    p.delta = p.delta_target + np.array([0.004, -0.006])
+    opts = render.RenderOptions()
+    errs = _grads_vs_oracle(p, opts, _weights(p, opts, 9))
+    bad = {k: v for k, v in errs.items() if not v <= GRAD_TOL}
+    assert not bad, errs
+
+
+def test_calibration_recovers_a_two_camera_rig():
+    """Joint pose calibration of both cameras of a rig (per-camera extrinsic
+    and time offset, one shared scene) from 1 deg / 10 cm / 10 ms each."""
+    from paper_2403_11577_gb300 import calib
+    p = scenes.calibration_problem(seed=4, n=150_000, frames=4, rot_deg=1.0, trans_m=0.1, delta0=0.01,
+                                   trajectory="zigzag", cameras=2)
+    for f in p.frames:
+        f.camera = scenes.Camera(704, 188, 276.0, 276.0, 341.0, 119.0)
+    res = calib.run_calibration(p, iters=600, warmup=0, reinit=False, train_scene=False, log_every=0)
+    assert res["start"]["rot_deg"] > 0.9 and len(res["final"]["cameras"]) == 2
+    fin = res["final"]
+    assert fin["rot_deg"] < 0.05 and fin["trans_cm"] < 1.0 and fin["delta_ms"] < 1.0, fin
