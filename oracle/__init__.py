@@ -258,6 +258,30 @@ def bin_sort(frames_tiles, n_per_frame, rect, depth, cap=None):
     return keys[:P], vals[:P], ranges[:T]
 
 
+# ------------------------------------------------------- voxel downsampling
+
+VOXEL_LIMIT = 1 << 20  # voxel coordinates must lie in (-2^20, 2^20)
+
+
+def voxel_downsample(X, voxel):
+    """Accumulated-LiDAR downsampling (Sec. III-D): one point per occupied
+    voxel of edge `voxel`, the point of smallest index.  A point's voxel is
+    (floor(x / voxel), floor(y / voxel), floor(z / voxel)) with the quotient
+    taken in float32, the points' own precision, so that the integer voxel
+    coordinates are decided in the same precision as on the GPU.  Points with
+    a non-finite coordinate or a voxel coordinate outside (-2^20, 2^20) are
+    dropped.  Returns the kept indices in ascending order."""
+    X = np.ascontiguousarray(X, dtype=np.float32).reshape(-1, 3)
+    with np.errstate(invalid="ignore", over="ignore"):
+        q = np.floor(X / np.float32(voxel))
+    ok = np.all(np.isfinite(q), axis=1) & np.all(np.abs(q) < VOXEL_LIMIT, axis=1)
+    idx = np.nonzero(ok)[0]
+    if len(idx) == 0:
+        return idx.astype(np.int64)
+    _, first = np.unique(q[ok].astype(np.int64), axis=0, return_index=True)
+    return np.sort(idx[first]).astype(np.int64)
+
+
 # ------------------------------------------------------------ problem level
 
 def render_problem(problem, opts: Opts = Opts(), ext=None, delta=None, pixels=None):

@@ -490,3 +490,48 @@ def test_photo_loss_gradient_matches_central_differences(lambda1):
         dn[k][y, x, c] -= h
         fd = (oracle.photo_loss(up, tgts, lambda1)[0] - oracle.photo_loss(dn, tgts, lambda1)[0]) / (2 * h)
         assert grads[k][y, x, c] == pytest.approx(fd, rel=1e-6, abs=1e-12), (k, y, x, c)
+
+
+# ----------------------------------------------- voxel downsampling (Sec. III-D)
+
+
+def _voxel_brute(X, v):
+    """Definition, point by point: the first point (by index) of every
+    voxel, coordinates from float32 quotients."""
+    seen, kept = set(), []
+    v32 = np.float32(v)
+    for i, p in enumerate(np.asarray(X, np.float32)):
+        q = tuple(int(np.floor(c / v32)) if np.isfinite(np.floor(c / v32)) else None for c in p)
+        if None in q or any(abs(c) >= oracle.VOXEL_LIMIT for c in q):
+            continue
+        if q not in seen:
+            seen.add(q)
+            kept.append(i)
+    return np.array(kept, np.int64)
+
+
+@pytest.mark.parametrize("v", [0.1, 0.05, 0.02, 0.5])
+def test_voxel_downsample_matches_point_by_point_definition(v):
+    rng = np.random.default_rng(int(v * 1000))
+    # clustered points: many share voxels; negative coordinates; exact multiples of v
+    c = rng.uniform(-3, 3, (40, 3))
+    X = (c[rng.integers(0, 40, 3000)] + rng.normal(0, 2 * v, (3000, 3))).astype(np.float32)
+    X[:50] = (np.round(X[:50] / v) * v).astype(np.float32)
+    kept = oracle.voxel_downsample(X, v)
+    np.testing.assert_array_equal(kept, _voxel_brute(X, v))
+    # properties: kept voxels are distinct, every occupied voxel is kept once,
+    # and the kept point is the voxel's smallest index
+    q = np.floor(X / np.float32(v)).astype(np.int64)
+    keys = {tuple(r) for r in q}
+    assert len(kept) == len(keys) == len({tuple(q[i]) for i in kept})
+    first = {}
+    for i, r in enumerate(map(tuple, q)):
+        first.setdefault(r, i)
+    assert sorted(first.values()) == list(kept)
+
+
+def test_voxel_downsample_drops_non_finite_and_far_points():
+    X = np.array([[0.01, 0.02, 0.03], [np.nan, 0, 0], [0.04, 0.01, 0.02], [np.inf, 1, 1],
+                  [3e6, 0, 0], [-0.05, 0.0, 0.0]], np.float32)
+    np.testing.assert_array_equal(oracle.voxel_downsample(X, 0.1), [0, 5])
+    assert len(oracle.voxel_downsample(X[[1, 3]], 0.1)) == 0
