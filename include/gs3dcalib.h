@@ -322,6 +322,25 @@ gs_status gs_pose_grad(const gs_batch *batch, const double *ext, void *ws_dev, d
 
 /* ------------------------------------------------- no allocation at all -- */
 
+/* Accumulated-LiDAR downsampling (Sec. III-D): keep one point per occupied
+ * voxel of edge `voxel`, the point of smallest index.  A point's voxel is
+ * (floor(x / voxel), floor(y / voxel), floor(z / voxel)) with the quotients
+ * in float32 (IEEE division).  Points with a non-finite coordinate or a voxel
+ * coordinate outside (-2^20, 2^20) are dropped.  With one point per voxel,
+ * the paper also bounds the Gaussians' scales by the voxel size
+ * (gs_opts.scale_max).
+ *   X[n][3] (device float)     points
+ *   out_index[n] (device int32) receives the kept indices in ascending
+ *                              order (the first out_count[0] entries)
+ *   out_count[1] (device uint64) number of kept points
+ *   scratch_dev: gs_voxel_scratch_size(n) bytes of device memory, 256-byte
+ *                aligned, owned by the caller (no state kept between calls)
+ * Errors: GS_ERR_INVALID_ARG (n < 0 or n >= 2^31, voxel not finite or <= 0,
+ * NULL or misaligned pointers), GS_ERR_CUDA. */
+size_t gs_voxel_scratch_size(int64_t n);
+gs_status gs_voxel_downsample(const float *X, int64_t n, float voxel, int32_t *out_index, uint64_t *out_count,
+                              void *scratch_dev, void *stream);
+
 /* The tile binning and depth sort of gs_bin_sort for callers that cannot
  * allocate device memory: for instance a host framework that owns every
  * device buffer and hands a plugin only its inputs and outputs, or a

@@ -23,6 +23,7 @@ L_scale and Adam are plain torch on the parameter tensors.
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import math
 import time
@@ -61,33 +62,43 @@ def rig_errors(ext, delta, ext_true, delta_true):
 
 def run_calibration(problem, iters=3000, warmup=500, lr_rot=1e-4, lr_trans=5e-3, lr_delta=1e-3,
                     lambda_scale=1e-3, opts=None, seed=0, log_every=250, reinit=True, train_scene=True,
-                    scene_lr_scale=1.0, device="cuda", loss="l1"):
+                    scene_lr_scale=1.0, device="cuda", loss="l1", schedule=None, clamp_scale=True):
     """Calibrate every camera of `problem` (its ext/delta are the start,
-    ext_target/delta_target the truth; errors are the worst over cameras).  train_scene=False keeps the
-    Gaussian attributes fixed (calibration only).  Returns a dict with the
-    error history, the final errors and the wall time."""
+    ext_target/delta_target the truth; errors are the worst over cameras).
+    train_scene=False keeps the Gaussian attributes fixed (calibration only).
+
+    schedule: coarse-to-fine voxelization (Sec. III-D), a list of
+    (voxel size in metres, iterations).  Each phase renders one point per
+    voxel of the accumulated cloud (gs_voxel_downsample), with every
+    Gaussian's scale bounded by the voxel size when clamp_scale.  The
+    attributes live on the full cloud, so each phase continues from their
+    current values; iters is then the sum of the phases.  Targets are always
+    rendered from the full cloud at the true calibration.
+
+    Returns a dict with the error history, the final errors, the wall time
+    and, with a schedule, the Gaussians and time of each phase."""
     build.build()
     dev = torch.device(device)
     gen = torch.Generator(device="cpu").manual_seed(seed)
-    scene = render.DeviceScene.from_problem(problem, dev)
+    full = render.DeviceScene.from_problem(problem, dev)
     opts = opts or render.RenderOptions(tile=problem.tile)
-    plan = render.Plan.for_problem(problem, scene, opts)
     # targets: the true calibration and the scene's true attributes
     e_true = torch.tensor(problem.ext_target, dtype=torch.float64, device=dev)
     d_true = torch.tensor(problem.delta_target, dtype=torch.float64, device=dev)
-    plan.forward(scene, e_true, d_true)
+    plan = render.Plan.for_problem(problem, full, opts)
+    plan.forward(full, e_true, d_true)
     target = plan.rgb.clone()
-    # parameters
+    del plan
+    # parameters (on the full cloud)
     if reinit:
-        n = scene.n
-        scene.rgb.copy_(torch.rand((n, 3), generator=gen).to(dev))
-        scene.logit_opacity.fill_(math.log(0.1 / 0.9))
-        scene.quat.zero_()
-        scene.quat[:, 0] = 1.0
+        n = full.n
+        full.rgb.copy_(torch.rand((n, 3), generator=gen).to(dev))
+        full.logit_opacity.fill_(math.log(0.1 / 0.9))
+        full.quat.zero_()
+        full.quat[:, 0] = 1.0
     ext = torch.tensor(problem.ext, dtype=torch.float64, device=dev)
     delta = torch.tensor(problem.delta, dtype=torch.float64, device=dev)
-    step = render.CalibStep(plan, scene, target, ext, delta, graph=True, loss=loss)
-    params = {k: getattr(scene, k) for k in GAUSS_LR}
+    params = {k: getattr(full, k) for k in GAUSS_LR}
     for t in params.values():
         t.grad = torch.zeros_like(t)
     rot = ext[:, :3].clone()
@@ -95,59 +106,101 @@ def run_calibration(problem, iters=3000, warmup=500, lr_rot=1e-4, lr_trans=5e-3,
     rot.grad, trans.grad = torch.zeros_like(rot), torch.zeros_like(trans)
     delta_p = delta.clone()
     delta_p.grad = torch.zeros_like(delta_p)
-    log_s = scene.log_scale
     opt_scene = torch.optim.Adam([{"params": [params[k]], "lr": GAUSS_LR[k] * scene_lr_scale} for k in GAUSS_LR],
                                  eps=1e-15)
     opt_cal = torch.optim.Adam([{"params": [rot], "lr": lr_rot}, {"params": [trans], "lr": lr_trans},
                                 {"params": [delta_p], "lr": lr_delta}], eps=1e-15)
     base_lrs = [g["lr"] for g in opt_cal.param_groups]
-    history = []
+    phases = list(schedule) if schedule else [(None, iters)]
+    iters = sum(n for _, n in phases)
+    history, phase_log = [], []
     e_true_np, d_true_np = np.asarray(problem.ext_target), np.asarray(problem.delta_target)
     torch.cuda.synchronize()
     t0 = time.time()
-    for it in range(iters):
-        # the graph reads ext/delta from its static tensors
-        ext[:, :3].copy_(rot)
-        ext[:, 3:].copy_(trans)
-        delta.copy_(delta_p)
-        loss = step()
-        if train_scene:
-            for k in GAUSS_LR:
-                params[k].grad.copy_(step.grads[k])
-            # L_scale on the activated scales (Eq. 7)
-            if lambda_scale > 0:
-                with torch.enable_grad():
-                    ls = log_s.detach().requires_grad_(True)
-                    s = torch.exp(ls)
-                    reg = lambda_scale * (s - s.mean(dim=1, keepdim=True)).abs().sum()
-                    (g_ls,) = torch.autograd.grad(reg, ls)
-                params["log_scale"].grad.add_(g_ls)
-            opt_scene.step()
-        if it >= warmup:
-            frac = (it - warmup) / max(1, iters - warmup)
-            for g, lr0 in zip(opt_cal.param_groups, base_lrs):
-                g["lr"] = lr0 * (1.0 - 0.9 * frac)
-            rot.grad.copy_(step.grads["ext"][:, :3])
-            trans.grad.copy_(step.grads["ext"][:, 3:])
-            delta_p.grad.copy_(step.grads["delta"])
-            opt_cal.step()
-        # keep quaternions away from zero norm
-        if train_scene and it % 100 == 99:
-            with torch.no_grad():
-                q = params["quat"]
-                q.div_(q.norm(dim=1, keepdim=True).clamp_min(1e-8))
-        if log_every and (it % log_every == 0 or it == iters - 1):
+    it = 0
+    for voxel, n_it in phases:
+        tp = time.time()
+        if voxel is None:
+            idx, scene, opts_p = None, full, opts
+        else:
+            idx = render.voxel_downsample(full.X, voxel)
+            scene = full.subset(idx)
+            opts_p = dataclasses.replace(opts, scale_max=voxel) if clamp_scale else opts
+        plan = render.Plan.for_problem(problem, scene, opts_p)
+        step = render.CalibStep(plan, scene, target, ext, delta, graph=True, loss=loss)
+        for _ in range(n_it):
+            # the graph reads ext/delta (and a phase's Gaussians) from static tensors
+            ext[:, :3].copy_(rot)
+            ext[:, 3:].copy_(trans)
+            delta.copy_(delta_p)
+            if idx is not None and train_scene:
+                for k in GAUSS_LR:
+                    getattr(scene, k).copy_(params[k][idx])
+            loss_v = step()
+            if train_scene:
+                for k in GAUSS_LR:
+                    if idx is None:
+                        params[k].grad.copy_(step.grads[k])
+                    else:
+                        params[k].grad.zero_()
+                        params[k].grad[idx] = step.grads[k]
+                # L_scale on the activated scales (Eq. 7) of the rendered Gaussians
+                if lambda_scale > 0:
+                    with torch.enable_grad():
+                        ls = (params["log_scale"] if idx is None else params["log_scale"][idx]).detach()
+                        ls.requires_grad_(True)
+                        sc = torch.exp(ls)
+                        reg = lambda_scale * (sc - sc.mean(dim=1, keepdim=True)).abs().sum()
+                        (g_ls,) = torch.autograd.grad(reg, ls)
+                    if idx is None:
+                        params["log_scale"].grad.add_(g_ls)
+                    else:
+                        params["log_scale"].grad[idx] += g_ls
+                opt_scene.step()
+            if it >= warmup:
+                frac = (it - warmup) / max(1, iters - warmup)
+                for g, lr0 in zip(opt_cal.param_groups, base_lrs):
+                    g["lr"] = lr0 * (1.0 - 0.9 * frac)
+                rot.grad.copy_(step.grads["ext"][:, :3])
+                trans.grad.copy_(step.grads["ext"][:, 3:])
+                delta_p.grad.copy_(step.grads["delta"])
+                opt_cal.step()
+            # keep quaternions away from zero norm
+            if train_scene and it % 100 == 99:
+                with torch.no_grad():
+                    q = params["quat"]
+                    q.div_(q.norm(dim=1, keepdim=True).clamp_min(1e-8))
+            if log_every and (it % log_every == 0 or it == iters - 1):
+                e_np = torch.cat([rot, trans], 1).cpu().numpy()
+                err = rig_errors(e_np, delta_p.cpu().numpy(), e_true_np, d_true_np)
+                err.update(it=it, loss=float(loss_v.item()))
+                history.append(err)
+            it += 1
+        torch.cuda.synchronize()
+        if voxel is not None:
             e_np = torch.cat([rot, trans], 1).cpu().numpy()
-            err = rig_errors(e_np, delta_p.cpu().numpy(), e_true_np, d_true_np)
-            err.update(it=it, loss=float(loss.item()))
-            history.append(err)
+            phase_log.append({"voxel_m": voxel, "iters": n_it, "gaussians": scene.n, "wall_s": time.time() - tp,
+                              "errors": rig_errors(e_np, delta_p.cpu().numpy(), e_true_np, d_true_np)})
+        del step, plan
     torch.cuda.synchronize()
     wall = time.time() - t0
     e_np = torch.cat([rot, trans], 1).cpu().numpy()
     final = rig_errors(e_np, delta_p.cpu().numpy(), e_true_np, d_true_np)
     start = rig_errors(np.asarray(problem.ext), np.asarray(problem.delta), e_true_np, d_true_np)
-    return {"start": start, "final": final, "wall_s": wall, "iters": iters, "warmup": warmup,
-            "history": history, "ms_per_iter": 1e3 * wall / iters}
+    out = {"start": start, "final": final, "wall_s": wall, "iters": iters, "warmup": warmup,
+           "history": history, "ms_per_iter": 1e3 * wall / iters}
+    if schedule:
+        out["phases"] = phase_log
+    return out
+
+
+def parse_schedule(text):
+    """"0.10:2000,0.05:500,0.02:500" -> [(0.10, 2000), (0.05, 500), (0.02, 500)]."""
+    out = []
+    for part in text.split(","):
+        v, n = part.split(":")
+        out.append((float(v), int(n)))
+    return out
 
 
 def main():
@@ -161,6 +214,10 @@ def main():
                     help="l1, or L_photo = 0.8 L1 + 0.2 D-SSIM (Eq. 4)")
     ap.add_argument("--crop", action="store_true", help="losses on the bottom half of each image (Sec. III-D)")
     ap.add_argument("--cameras", type=int, default=1, help="forward cameras of the rig, calibrated jointly")
+    ap.add_argument("--schedule", default=None,
+                    help="coarse-to-fine voxelization, e.g. 0.10:2000,0.05:500,0.02:500 (Sec. III-D, Sec. IV-C)")
+    ap.add_argument("--no-scale-clamp", action="store_true",
+                    help="with --schedule: do not bound the scales by the voxel size")
     ap.add_argument("--mode", choices=["joint", "pose"], default="joint",
                     help="joint: re-initialised scene trained with the calibration; "
                          "pose: the scene's attributes fixed at their true values")
@@ -169,12 +226,14 @@ def main():
     if a.crop:
         for f in p.frames:
             f.row0 = f.camera.height // 2
+    sched = parse_schedule(a.schedule) if a.schedule else None
+    kw = dict(seed=a.seed, loss=a.loss, schedule=sched, clamp_scale=not a.no_scale_clamp)
     if a.mode == "pose":
-        res = run_calibration(p, iters=a.iters, warmup=0, seed=a.seed, reinit=False, train_scene=False, loss=a.loss)
+        res = run_calibration(p, iters=a.iters, warmup=0, reinit=False, train_scene=False, **kw)
     else:
-        res = run_calibration(p, iters=a.iters, warmup=a.warmup, seed=a.seed, reinit=True, loss=a.loss)
+        res = run_calibration(p, iters=a.iters, warmup=a.warmup, reinit=True, **kw)
     res.update(trajectory=a.trajectory, mode=a.mode, seed=a.seed, gaussians=a.gaussians, loss=a.loss, crop=a.crop,
-               cameras=a.cameras)
+               cameras=a.cameras, schedule=a.schedule, scale_clamp=not a.no_scale_clamp)
     print(json.dumps(res))
 
 

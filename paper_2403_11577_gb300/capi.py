@@ -68,6 +68,8 @@ _SIGS = {
     "gs_render_bwd": ([_P] * 15 + [C.c_int32, _P], C.c_int32),
     "gs_pose_grad": ([_P] * 6 + [C.c_int32, _P], C.c_int32),
     "gs_bin_sort_noalloc": ([_P] * 9, C.c_int32),
+    "gs_voxel_scratch_size": ([C.c_int64], C.c_size_t),
+    "gs_voxel_downsample": ([_P, C.c_int64, C.c_float, _P, _P, _P, _P], C.c_int32),
 }
 
 _lib = None
@@ -261,6 +263,21 @@ def gs_pose_grad(batch, ext, ws, d_ext, d_delta, d_xi=None, accumulate=False, st
                               _ptr(d_ext, F64, "d_ext"), _ptr(d_delta, F64, "d_delta"),
                               _ptr(d_xi, F64, "d_xi", allow_none=True), int(bool(accumulate)), _stream(stream)),
            "gs_pose_grad")
+
+
+def gs_voxel_scratch_size(n):
+    return int(lib().gs_voxel_scratch_size(int(n)))
+
+
+def gs_voxel_downsample(X, voxel, out_index, out_count, scratch, stream=None):
+    """X: float32 [n,3]; out_index: int32 [n]; out_count: int64 [1] (as uint64);
+    scratch: uint8 tensor of gs_voxel_scratch_size(n) bytes, 256-byte aligned."""
+    n = X.shape[0]
+    if out_index.numel() < n or out_count.numel() < 1 or scratch.numel() < gs_voxel_scratch_size(n):
+        raise ValueError("gs_voxel_downsample: buffer too small")
+    _check(lib().gs_voxel_downsample(_ptr(X, F32, "X"), n, float(voxel), _ptr(out_index, torch.int32, "out_index"),
+                                     _ptr(out_count, torch.int64, "out_count"), _ptr(scratch, torch.uint8, "scratch"),
+                                     _stream(stream)), "gs_voxel_downsample")
 
 
 def gs_bin_sort_noalloc(batch, opts, rect, depth, keys, vals, ranges, out_pairs, stream=None):

@@ -19,7 +19,8 @@
 // 4. k_tile_ranges: [start, end) of every tile; k_tile_order: the tiles
 //    sorted heavy-first for the render kernels.
 // gs_bin_sort_noalloc sorts 64-bit full keys over all their bits instead
-// (one stage, no record buffers).
+// (one stage, no record buffers).  gs_voxel_downsample (Sec. III-D) uses the
+// same 64-bit passes to bin LiDAR points into voxels.
 // Each radix pass: k_radix_hist (per-block digit counts) -> k_radix_colscan
 // (per-digit prefix over blocks, digit totals) -> k_radix_scatter (stable:
 // per-warp ranking with match_any in index order, per-tile prefix over
@@ -517,6 +518,135 @@ cudaError_t launch_bin_sort(const gs_batch *b, const Layout &L, unsigned char *w
     if ((e = cudaMemsetAsync(ranges, 0, sizeof(uint2) * (size_t)b->num_tiles, s)) != cudaSuccess) return e;
     k_tile_ranges<uint32_t><<<1216, 256, 0, s>>>(keys[0], &stats->num_pairs, ranges);
     k_tile_order<<<1, 1024, 0, s>>>(ranges, b->num_tiles, reinterpret_cast<uint32_t *>(ws + L.order));
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------- voxel downsampling
+//
+// Sec. III-D: one point per occupied voxel of edge v, the point of smallest
+// index.  A point's voxel is (floor(x/v), floor(y/v), floor(z/v)), the
+// quotients in float32 (IEEE division); the three coordinates, biased by
+// 2^20, are packed into 21 bits each.  A stable LSD sort of (key, index)
+// over index-ordered input puts every voxel's smallest index first; that
+// point is flagged, and the flags are compacted in index order.  Points with
+// a non-finite coordinate or a voxel coordinate outside (-2^20, 2^20) get
+// the all-ones key, which sorts last and is never flagged.
+
+namespace {
+
+constexpr long long kVoxLimit = 1ll << 20;
+constexpr int kVoxItems = 1024;  // flags per compaction block
+
+__global__ void k_set_count(unsigned long long *c, long long n) { *c = (unsigned long long)n; }
+
+__global__ void k_voxel_keys(const float *__restrict__ X, long long n, float v, unsigned long long *__restrict__ keys,
+                             uint32_t *__restrict__ vals) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    unsigned long long key = 0;
+    bool ok = true;
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        const float q = floorf(__fdiv_rn(X[3 * i + a], v));
+        ok = ok && isfinite(q) && fabsf(q) < (float)kVoxLimit;
+        key = (key << 21) | (ok ? (unsigned long long)((long long)q + kVoxLimit) : 0ull);
+    }
+    keys[i] = ok ? key : ~0ull;
+    vals[i] = (uint32_t)i;
+}
+
+// flag[point] = 1 for the first (smallest index) point of each voxel
+__global__ void k_voxel_first(const unsigned long long *__restrict__ keys, const uint32_t *__restrict__ vals,
+                              long long n, uint32_t *__restrict__ flag) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const unsigned long long k = keys[i];
+    flag[vals[i]] = (k != ~0ull && (i == 0 || keys[i - 1] != k)) ? 1u : 0u;
+}
+
+__global__ void __launch_bounds__(kEmitThreads)
+k_flag_count(const uint32_t *__restrict__ flag, long long n, unsigned long long *__restrict__ sums) {
+    __shared__ unsigned long long sh[kEmitThreads / 32];
+    const long long base = (long long)blockIdx.x * kVoxItems;
+    unsigned long long c = 0;
+    for (int i = threadIdx.x; i < kVoxItems; i += kEmitThreads)
+        if (base + i < n) c += flag[base + i];
+    const unsigned long long t = block_sum_u64<kEmitThreads>(c, sh);
+    if (threadIdx.x == 0) sums[blockIdx.x] = t;
+}
+
+__global__ void __launch_bounds__(1024)
+k_flag_scan(unsigned long long *__restrict__ sums, int nb, unsigned long long *__restrict__ total) {
+    block_exclusive_scan_u64(sums, nb, total);
+}
+
+// kept indices in ascending order: block b's flags go to sums[b] + the
+// exclusive count within the block (each thread owns 4 consecutive flags)
+__global__ void __launch_bounds__(kEmitThreads)
+k_flag_emit(const uint32_t *__restrict__ flag, long long n, const unsigned long long *__restrict__ sums,
+            int32_t *__restrict__ out) {
+    __shared__ unsigned long long wsum[kEmitThreads / 32];
+    constexpr int PER = kVoxItems / kEmitThreads;
+    const long long base = (long long)blockIdx.x * kVoxItems + (long long)threadIdx.x * PER;
+    uint32_t f[PER];
+    unsigned long long mine = 0;
+#pragma unroll
+    for (int j = 0; j < PER; j++) {
+        f[j] = base + j < n ? flag[base + j] : 0u;
+        mine += f[j];
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned long long incl = mine;
+    for (int s2 = 1; s2 < 32; s2 <<= 1) {
+        const unsigned long long y = __shfl_up_sync(0xffffffffu, incl, s2);
+        if (lane >= s2) incl += y;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    unsigned long long pos = sums[blockIdx.x] + incl - mine;
+    for (int w = 0; w < warp; w++) pos += wsum[w];
+#pragma unroll
+    for (int j = 0; j < PER; j++)
+        if (f[j]) out[pos++] = (int32_t)(base + j);
+}
+
+}  // namespace
+
+size_t voxel_scratch_bytes(long long n, int *sort_blocks) {
+    const long long st = (n + kSortTile - 1) / kSortTile;
+    const int nb = (int)std::max(1ll, std::min(st, 304ll));
+    if (sort_blocks) *sort_blocks = nb;
+    const long long fb = (n + kVoxItems - 1) / kVoxItems;
+    return align256((size_t)n * 8) * 2 + align256((size_t)n * 4) * 3 + align256((size_t)kRadix * (nb + 1) * 4) +
+           align256((size_t)std::max(fb, 1ll) * 8) + 256;
+}
+
+cudaError_t launch_voxel(const float *X, long long n, float v, int32_t *out_index, unsigned long long *out_count,
+                         unsigned char *scratch, cudaStream_t s) {
+    int nb = 1;
+    voxel_scratch_bytes(n, &nb);
+    size_t o = 0;
+    auto take = [&](size_t bytes) { unsigned char *p = scratch + o; o += align256(bytes); return p; };
+    unsigned long long *kb[2] = {(unsigned long long *)take((size_t)n * 8), (unsigned long long *)take((size_t)n * 8)};
+    uint32_t *vb[2] = {(uint32_t *)take((size_t)n * 4), (uint32_t *)take((size_t)n * 4)};
+    uint32_t *flag = (uint32_t *)take((size_t)n * 4);
+    uint32_t *hist = (uint32_t *)take((size_t)kRadix * (nb + 1) * 4);
+    const long long fb = (n + kVoxItems - 1) / kVoxItems;
+    unsigned long long *sums = (unsigned long long *)take((size_t)std::max(fb, 1ll) * 8);
+    unsigned long long *count = (unsigned long long *)take(8);
+    if (n == 0) return cudaMemsetAsync(out_count, 0, 8, s);
+    cudaError_t e = scatter_smem_attr<unsigned long long>();
+    if (e != cudaSuccess) return e;
+    k_set_count<<<1, 1, 0, s>>>(count, n);
+    const int g = (int)((n + 255) / 256);
+    k_voxel_keys<<<g, 256, 0, s>>>(X, n, v, kb[0], vb[0]);
+    for (int p = 0; p < 8 && e == cudaSuccess; p++)  // 63 key bits
+        e = radix_pass(kb[p & 1], vb[p & 1], kb[(p + 1) & 1], vb[(p + 1) & 1], count, 8 * p, nb, hist, s);
+    if (e != cudaSuccess) return e;
+    k_voxel_first<<<g, 256, 0, s>>>(kb[0], vb[0], n, flag);
+    k_flag_count<<<(int)fb, kEmitThreads, 0, s>>>(flag, n, sums);
+    k_flag_scan<<<1, 1024, 0, s>>>(sums, (int)fb, out_count);
+    k_flag_emit<<<(int)fb, kEmitThreads, 0, s>>>(flag, n, sums, out_index);
     return cudaGetLastError();
 }
 

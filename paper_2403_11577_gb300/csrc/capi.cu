@@ -29,6 +29,9 @@ cudaError_t launch_render_bwd(const gs_batch *, const gs_opts *, const uint32_t 
 cudaError_t launch_l1(const float *, const float *, long long, float, double *, float *, double *, cudaStream_t);
 cudaError_t launch_photo(const gs_batch *, const float *, const float *, float, float, double *, float *, float *,
                          double *, cudaStream_t);
+size_t voxel_scratch_bytes(long long n, int *sort_blocks);
+cudaError_t launch_voxel(const float *X, long long n, float v, int32_t *out_index, unsigned long long *out_count,
+                         unsigned char *scratch, cudaStream_t s);
 
 constexpr int kSortBlocksMax = 304;  // two per SM on a 152-SM GB300
 
@@ -294,6 +297,20 @@ gs_status gs_loss_photo(const gs_batch *b, const float *rgb, const float *target
                          (double *)(w + L.photo_part), S(stream));
     if (e == cudaSuccess) e = prof_mark(GS_PROF_LOSS, false, S(stream));
     return cuda_status(e);
+}
+
+size_t gs_voxel_scratch_size(int64_t n) {
+    if (n < 0 || n >= (1ll << 31)) return 0;
+    return voxel_scratch_bytes(n, nullptr);
+}
+
+gs_status gs_voxel_downsample(const float *X, int64_t n, float voxel, int32_t *out_index, uint64_t *out_count,
+                              void *scratch, void *stream) {
+    if (n < 0 || n >= (1ll << 31) || !(std::isfinite(voxel) && voxel > 0.f) || !out_count || !scratch ||
+        (n > 0 && (!X || !out_index)) || (reinterpret_cast<uintptr_t>(scratch) & 255))
+        return GS_ERR_INVALID_ARG;
+    return cuda_status(launch_voxel(X, n, voxel, out_index, reinterpret_cast<unsigned long long *>(out_count),
+                                    static_cast<unsigned char *>(scratch), S(stream)));
 }
 
 gs_status gs_render_bwd(const gs_batch *b, const float *X, const float *quat, const float *log_scale,

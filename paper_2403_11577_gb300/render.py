@@ -58,6 +58,22 @@ class DeviceScene:
     def n(self) -> int:
         return int(self.X.shape[0])
 
+    def subset(self, idx: torch.Tensor) -> "DeviceScene":
+        """The Gaussians idx (ascending global indices), same trajectories;
+        each scene keeps its kept Gaussians in order."""
+        idx = idx.to(self.X.device)
+        offs, counts = [], []
+        for o, c in zip(self.gauss_offset, self.gauss_count):
+            lo = int(torch.searchsorted(idx, torch.tensor(o, device=idx.device)))
+            hi = int(torch.searchsorted(idx, torch.tensor(o + c, device=idx.device)))
+            offs.append(lo)
+            counts.append(hi - lo)
+        return DeviceScene(X=self.X[idx].contiguous(), quat=self.quat[idx].contiguous(),
+                           log_scale=self.log_scale[idx].contiguous(),
+                           logit_opacity=self.logit_opacity[idx].contiguous(), rgb=self.rgb[idx].contiguous(),
+                           traj_t=self.traj_t, traj_pose=self.traj_pose, traj_offset=self.traj_offset,
+                           gauss_offset=offs, gauss_count=counts)
+
     @staticmethod
     def from_problem(problem, device="cuda") -> "DeviceScene":
         sc = problem.scenes
@@ -77,6 +93,18 @@ class DeviceScene:
             traj_t=cat("traj_t", np.float64),
             traj_pose=torch.from_numpy(np.ascontiguousarray(traj_pose, np.float64)).to(device),
             traj_offset=torch.from_numpy(offs).to(device), gauss_offset=goff, gauss_count=[s.n for s in sc])
+
+
+def voxel_downsample(X: torch.Tensor, voxel: float) -> torch.Tensor:
+    """Indices (int64, ascending) of the points kept by the accumulated-LiDAR
+    voxel downsampling of Sec. III-D (gs_voxel_downsample): one point per
+    occupied voxel, the one of smallest index."""
+    n = int(X.shape[0])
+    _raw, scratch = _aligned_workspace(capi.gs_voxel_scratch_size(n), X.device)
+    idx = torch.empty(max(n, 1), dtype=torch.int32, device=X.device)
+    cnt = torch.zeros(1, dtype=torch.int64, device=X.device)
+    capi.gs_voxel_downsample(X.contiguous(), voxel, idx, cnt, scratch)
+    return idx[:int(cnt.item())].long()
 
 
 def _aligned_workspace(nbytes: int, device) -> tuple:

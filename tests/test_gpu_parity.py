@@ -745,3 +745,56 @@ def test_calibration_recovers_a_two_camera_rig():
     assert res["start"]["rot_deg"] > 0.9 and len(res["final"]["cameras"]) == 2
     fin = res["final"]
     assert fin["rot_deg"] < 0.05 and fin["trans_cm"] < 1.0 and fin["delta_ms"] < 1.0, fin
+
+
+
+# ------------------------------------------------ voxel downsampling (Sec. III-D)
+
+
+@pytest.mark.parametrize("voxel", [0.10, 0.05, 0.02])
+def test_voxel_downsample_matches_oracle_on_the_accumulated_cloud(voxel):
+    """The 1M-point accumulated LiDAR cloud of the batched scene: the kept
+    points are the oracle's, index for index."""
+    p = scenes.batched_problem(n=1_000_000)
+    X = p.scenes[0].X
+    got = render.voxel_downsample(torch.from_numpy(X).cuda(), voxel).cpu().numpy()
+    ref = oracle.voxel_downsample(X, voxel)
+    assert len(ref) > 10_000
+    np.testing.assert_array_equal(got, ref)
+
+
+def test_voxel_downsample_edge_cases():
+    rng = np.random.default_rng(2)
+    X = rng.normal(0, 1, (5000, 3)).astype(np.float32)
+    X[10] = [np.nan, 0, 0]
+    X[11] = [np.inf, 1, 1]
+    X[12] = [3e6, 0, 0]
+    X[20:40] = X[19]  # duplicates keep the first
+    X[50:60] = np.round(X[50:60] / 0.25) * 0.25  # exact voxel boundaries
+    for v in (0.25, 0.1, 1e-3):
+        got = render.voxel_downsample(torch.from_numpy(X).cuda(), v).cpu().numpy()
+        np.testing.assert_array_equal(got, oracle.voxel_downsample(X, v))
+    one = render.voxel_downsample(torch.zeros((1, 3), device="cuda"), 0.1).cpu().numpy()
+    np.testing.assert_array_equal(one, [0])
+    assert render.voxel_downsample(torch.zeros((0, 3), device="cuda"), 0.1).numel() == 0
+    with pytest.raises(capi.GsError):
+        render.voxel_downsample(torch.zeros((4, 3), device="cuda"), 0.0)
+
+
+def test_coarse_to_fine_calibration_phases():
+    """Coarse-to-fine voxelization (Sec. III-D): each phase renders the
+    oracle's voxel-kept Gaussians (checked by count), and pose calibration
+    through 10 / 5 / 2 cm phases recovers a 1 deg / 10 cm / 10 ms error."""
+    from paper_2403_11577_gb300 import calib
+    p = scenes.calibration_problem(seed=3, n=150_000, frames=4, rot_deg=1.0, trans_m=0.1, delta0=0.01,
+                                   trajectory="zigzag")
+    for f in p.frames:
+        f.camera = scenes.Camera(704, 188, 276.0, 276.0, 341.0, 119.0)
+    sched = [(0.10, 300), (0.05, 150), (0.02, 150)]
+    res = calib.run_calibration(p, warmup=0, reinit=False, train_scene=False, log_every=0, schedule=sched,
+                                clamp_scale=False)
+    counts = [ph["gaussians"] for ph in res["phases"]]
+    assert counts == [len(oracle.voxel_downsample(p.scenes[0].X, v)) for v, _ in sched]
+    assert counts[0] < counts[1] < counts[2] <= 150_000
+    fin = res["final"]
+    assert fin["rot_deg"] < 0.05 and fin["trans_cm"] < 1.0 and fin["delta_ms"] < 1.0, fin
