@@ -12,8 +12,10 @@ design notes:
   - a level whose (N_l + 1)^3 vertices fit in the table is indexed densely,
     x + y (N_l + 1) + z (N_l + 1)^2, otherwise by the spatial hash
     (x * 1 XOR y * 2654435761 XOR z * 805459861) mod 2^32 mod T;
-  - a point p in [0, 1]^3 has level coordinates q = p * N_l, cell floor(q),
-    and its feature is the trilinear interpolation of the cell's 8 vertices;
+  - a point is mapped to p in [0, 1]^3 (clamped) by the bounding box; its
+    level coordinates are q = p * N_l, its cell c = min(floor(q), N_l - 1)
+    (so that p = 1 stays in the last cell), and its feature is the trilinear
+    interpolation of the cell's 8 vertices with weights from q - c;
   - MLP: 32 -> 64 -> 64 -> 11, ReLU after the two hidden layers;
   - heads (the renderer's raw inputs): rgb = sigmoid(o[0:3]),
     logit_opacity = o[3], log_scale = o[4:7], quat = o[7:11].
@@ -68,12 +70,12 @@ def vertex_index(cfg, level, v):
 
 def encode_point(cfg, tables, x):
     """Encoding of one point and the (level, slot, weight) list it reads."""
-    p = (np.asarray(x, np.float64) - cfg.aabb_min) / (cfg.aabb_max - cfg.aabb_min)
+    p = np.clip((np.asarray(x, np.float64) - cfg.aabb_min) / (cfg.aabb_max - cfg.aabb_min), 0.0, 1.0)
     enc = np.zeros(cfg.D)
     taps = []
     for l in range(cfg.L):
         q = p * cfg.res[l]
-        c = np.floor(q)
+        c = np.minimum(np.floor(q), cfg.res[l] - 1)
         f = q - c
         for corner in range(8):
             d = np.array([(corner >> a) & 1 for a in range(3)])

@@ -44,6 +44,21 @@ def test_dense_levels_interpolate_affine_fields_exactly():
             np.testing.assert_allclose(enc[l * 2:(l + 1) * 2], want, rtol=1e-12, atol=1e-10)
 
 
+def test_points_on_and_beyond_the_box_faces():
+    """p is clamped to [0, 1]; a point on the far face uses the last cell
+    (weight 1 on its far vertices), so the encoding is continuous there."""
+    cfg = _cfg()
+    rng = np.random.default_rng(6)
+    tables = rng.normal(size=(cfg.L, cfg.T, cfg.F))
+    top = cfg.aabb_max.copy()
+    e_face, taps = ngp.encode_point(cfg, tables, top)
+    e_near, _ = ngp.encode_point(cfg, tables, top - 1e-9 * (cfg.aabb_max - cfg.aabb_min))
+    np.testing.assert_allclose(e_face, e_near, atol=1e-5)
+    assert all(0 <= s < cfg.T for (_, s, _) in taps)
+    e_out, _ = ngp.encode_point(cfg, tables, top + 5.0)
+    np.testing.assert_array_equal(e_out, e_face)
+
+
 def test_hash_matches_uint32_arithmetic():
     """Hashed levels: (x * 1 ^ y * 2654435761 ^ z * 805459861) mod 2^32 mod T,
     against numpy's wrapping uint32 products."""
