@@ -52,7 +52,7 @@ def test_points_on_and_beyond_the_box_faces():
     tables = rng.normal(size=(cfg.L, cfg.T, cfg.F))
     top = cfg.aabb_max.copy()
     e_face, taps = ngp.encode_point(cfg, tables, top)
-    e_near, _ = ngp.encode_point(cfg, tables, top - 1e-9 * (cfg.aabb_max - cfg.aabb_min))
+    e_near, _ = ngp.encode_point(cfg, tables, top - 1e-12 * (cfg.aabb_max - cfg.aabb_min))
     np.testing.assert_allclose(e_face, e_near, atol=1e-5)
     assert all(0 <= s < cfg.T for (_, s, _) in taps)
     e_out, _ = ngp.encode_point(cfg, tables, top + 5.0)
