@@ -322,6 +322,43 @@ gs_status gs_pose_grad(const gs_batch *batch, const double *ext, void *ws_dev, d
 
 /* ------------------------------------------------- no allocation at all -- */
 
+/* The attribute model F(X | Theta) of Sec. III-C: the Instant-NGP
+ * multiresolution hash encoding of a Gaussian's centre, then an MLP
+ * 2L -> 64 -> 64 -> 11 (ReLU after the hidden layers) whose four heads give
+ * the renderer's inputs: rgb = sigmoid(o0..2), logit_opacity = o3,
+ * log_scale = o4..6, quat = o7..10.
+ * Encoding: 2 features per level; a point maps to p in [0, 1]^3 (clamped)
+ * through the box; at level l, q = p * res[l], cell c = min(floor(q),
+ * res[l] - 1), trilinear interpolation of the cell's 8 vertices.  A vertex
+ * v indexes the level's table densely (x + y (res+1) + z (res+1)^2) when the
+ * (res+1)^3 vertices fit in T = 2^log2_table entries, otherwise by the
+ * spatial hash (x * 1 ^ y * 2654435761 ^ z * 805459861) mod 2^32 mod T.
+ * theta (float, device): the tables [levels][T][2], then W1 [64][2 levels],
+ * b1 [64], W2 [64][64], b2 [64], W3 [11][64], b3 [11]; 8-byte aligned. */
+typedef struct {
+    float aabb_min[3], aabb_max[3];  /* box mapped to [0, 1]^3 */
+    int32_t levels;                  /* L, 1..16 */
+    int32_t log2_table;              /* 4..26 */
+    int32_t res[16];                 /* per-level grid resolution, 1..2^20 */
+} gs_ngp;
+
+/* Number of floats of theta; -1 for an invalid configuration (host). */
+int64_t gs_ngp_param_count(const gs_ngp *cfg);
+
+/* Attributes of n points X[n][3]: rgb[n][3], logit_opacity[n],
+ * log_scale[n][3], quat[n][4] (device float, overwritten).
+ * Errors: GS_ERR_INVALID_ARG, GS_ERR_CUDA. */
+gs_status gs_ngp_forward(const gs_ngp *cfg, const float *theta, const float *X, int64_t n, float *rgb,
+                         float *logit_opacity, float *log_scale, float *quat, void *stream);
+
+/* Backward of sum(d_attr . F(X | theta)): adds the gradient with respect to
+ * theta into d_theta (the caller zeroes it first; table entries are summed
+ * with atomics, so their float rounding order varies between runs).
+ * Errors: GS_ERR_INVALID_ARG, GS_ERR_CUDA. */
+gs_status gs_ngp_backward(const gs_ngp *cfg, const float *theta, const float *X, int64_t n, const float *d_rgb,
+                          const float *d_logit_opacity, const float *d_log_scale, const float *d_quat,
+                          float *d_theta, void *stream);
+
 /* Accumulated-LiDAR downsampling (Sec. III-D): keep one point per occupied
  * voxel of edge `voxel`, the point of smallest index.  A point's voxel is
  * (floor(x / voxel), floor(y / voxel), floor(z / voxel)) with the quotients

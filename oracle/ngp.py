@@ -12,7 +12,12 @@ design notes:
   - a level whose (N_l + 1)^3 vertices fit in the table is indexed densely,
     x + y (N_l + 1) + z (N_l + 1)^2, otherwise by the spatial hash
     (x * 1 XOR y * 2654435761 XOR z * 805459861) mod 2^32 mod T;
-  - a point is mapped to p in [0, 1]^3 (clamped) by the bounding box; its
+  - a point is mapped to p in [0, 1]^3 (clamped) by the bounding box, in
+    float32 like the points themselves: p = clamp((x - lo) * inv), with lo
+    the box minimum and inv = 1 / (hi - lo) rounded to float32 (a rough
+    hash field is sensitive to the last bit of p, so the oracle takes the
+    input coordinate in the same precision as the kernel and works in FP64
+    from there); its
     level coordinates are q = p * N_l, its cell c = min(floor(q), N_l - 1)
     (so that p = 1 stays in the last cell), and its feature is the trilinear
     interpolation of the cell's 8 vertices with weights from q - c;
@@ -68,9 +73,17 @@ def vertex_index(cfg, level, v):
     return h % cfg.T
 
 
+def unit_point(cfg, x):
+    """p = clamp((x - lo) * inv, 0, 1) in float32 (see the module notes)."""
+    lo = np.float32(cfg.aabb_min)
+    inv = np.float32(1.0) / (np.float32(cfg.aabb_max) - lo)
+    p = (np.asarray(x, np.float32) - lo) * inv
+    return np.clip(p, np.float32(0), np.float32(1)).astype(np.float64)
+
+
 def encode_point(cfg, tables, x):
     """Encoding of one point and the (level, slot, weight) list it reads."""
-    p = np.clip((np.asarray(x, np.float64) - cfg.aabb_min) / (cfg.aabb_max - cfg.aabb_min), 0.0, 1.0)
+    p = unit_point(cfg, x)
     enc = np.zeros(cfg.D)
     taps = []
     for l in range(cfg.L):

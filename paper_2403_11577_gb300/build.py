@@ -11,7 +11,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libgs3dcalib.so")
-SOURCES = ["capi.cu", "pose.cu", "project.cu", "binsort.cu", "render.cu", "loss.cu", "photo.cu"]
+SOURCES = ["capi.cu", "pose.cu", "project.cu", "binsort.cu", "render.cu", "loss.cu", "photo.cu", "ngp.cu"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]

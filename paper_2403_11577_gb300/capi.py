@@ -38,6 +38,11 @@ class GsBatch(C.Structure):
                 ("pair_capacity", C.c_int64)]
 
 
+class GsNgp(C.Structure):
+    _fields_ = [("aabb_min", C.c_float * 3), ("aabb_max", C.c_float * 3), ("levels", C.c_int32),
+                ("log2_table", C.c_int32), ("res", C.c_int32 * 16)]
+
+
 class GsStats(C.Structure):
     _fields_ = [("status", C.c_uint32), ("reserved", C.c_uint32), ("num_pairs", C.c_uint64),
                 ("eval_fwd", C.c_uint64), ("eval_bwd", C.c_uint64)]
@@ -69,6 +74,9 @@ _SIGS = {
     "gs_pose_grad": ([_P] * 6 + [C.c_int32, _P], C.c_int32),
     "gs_bin_sort_noalloc": ([_P] * 9, C.c_int32),
     "gs_voxel_scratch_size": ([C.c_int64], C.c_size_t),
+    "gs_ngp_param_count": ([_P], C.c_int64),
+    "gs_ngp_forward": ([_P, _P, _P, C.c_int64, _P, _P, _P, _P, _P], C.c_int32),
+    "gs_ngp_backward": ([_P, _P, _P, C.c_int64, _P, _P, _P, _P, _P, _P], C.c_int32),
     "gs_voxel_downsample": ([_P, C.c_int64, C.c_float, _P, _P, _P, _P], C.c_int32),
 }
 
@@ -263,6 +271,24 @@ def gs_pose_grad(batch, ext, ws, d_ext, d_delta, d_xi=None, accumulate=False, st
                               _ptr(d_ext, F64, "d_ext"), _ptr(d_delta, F64, "d_delta"),
                               _ptr(d_xi, F64, "d_xi", allow_none=True), int(bool(accumulate)), _stream(stream)),
            "gs_pose_grad")
+
+
+def gs_ngp_param_count(cfg):
+    return int(lib().gs_ngp_param_count(C.byref(cfg)))
+
+
+def gs_ngp_forward(cfg, theta, X, rgb, logit_opacity, log_scale, quat, stream=None):
+    _check(lib().gs_ngp_forward(C.byref(cfg), _ptr(theta, F32, "theta"), _ptr(X, F32, "X"), X.shape[0],
+                                _ptr(rgb, F32, "rgb"), _ptr(logit_opacity, F32, "logit_opacity"),
+                                _ptr(log_scale, F32, "log_scale"), _ptr(quat, F32, "quat"), _stream(stream)),
+           "gs_ngp_forward")
+
+
+def gs_ngp_backward(cfg, theta, X, d_rgb, d_logit_opacity, d_log_scale, d_quat, d_theta, stream=None):
+    _check(lib().gs_ngp_backward(C.byref(cfg), _ptr(theta, F32, "theta"), _ptr(X, F32, "X"), X.shape[0],
+                                 _ptr(d_rgb, F32, "d_rgb"), _ptr(d_logit_opacity, F32, "d_logit_opacity"),
+                                 _ptr(d_log_scale, F32, "d_log_scale"), _ptr(d_quat, F32, "d_quat"),
+                                 _ptr(d_theta, F32, "d_theta"), _stream(stream)), "gs_ngp_backward")
 
 
 def gs_voxel_scratch_size(n):

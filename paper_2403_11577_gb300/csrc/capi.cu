@@ -30,6 +30,12 @@ cudaError_t launch_l1(const float *, const float *, long long, float, double *, 
 cudaError_t launch_photo(const gs_batch *, const float *, const float *, float, float, double *, float *, float *,
                          double *, cudaStream_t);
 size_t voxel_scratch_bytes(long long n, int *sort_blocks);
+long long ngp_param_count(const gs_ngp *c);
+cudaError_t launch_ngp_fwd(const gs_ngp *c, const float *theta, const float *X, long long n, float *rgb,
+                           float *logit_o, float *log_s, float *quat, cudaStream_t s);
+cudaError_t launch_ngp_bwd(const gs_ngp *c, const float *theta, const float *X, long long n, const float *d_rgb,
+                           const float *d_logit_o, const float *d_log_s, const float *d_quat, float *d_theta,
+                           cudaStream_t s);
 cudaError_t launch_voxel(const float *X, long long n, float v, int32_t *out_index, unsigned long long *out_count,
                          unsigned char *scratch, cudaStream_t s);
 
@@ -297,6 +303,27 @@ gs_status gs_loss_photo(const gs_batch *b, const float *rgb, const float *target
                          (double *)(w + L.photo_part), S(stream));
     if (e == cudaSuccess) e = prof_mark(GS_PROF_LOSS, false, S(stream));
     return cuda_status(e);
+}
+
+int64_t gs_ngp_param_count(const gs_ngp *cfg) { return ngp_param_count(cfg); }
+
+gs_status gs_ngp_forward(const gs_ngp *cfg, const float *theta, const float *X, int64_t n, float *rgb,
+                         float *logit_opacity, float *log_scale, float *quat, void *stream) {
+    if (ngp_param_count(cfg) < 0 || n < 0 || !theta || (reinterpret_cast<uintptr_t>(theta) & 7) ||
+        (n > 0 && (!X || !rgb || !logit_opacity || !log_scale || !quat)))
+        return GS_ERR_INVALID_ARG;
+    return cuda_status(launch_ngp_fwd(cfg, theta, X, n, rgb, logit_opacity, log_scale, quat, S(stream)));
+}
+
+gs_status gs_ngp_backward(const gs_ngp *cfg, const float *theta, const float *X, int64_t n, const float *d_rgb,
+                          const float *d_logit_opacity, const float *d_log_scale, const float *d_quat,
+                          float *d_theta, void *stream) {
+    if (ngp_param_count(cfg) < 0 || n < 0 || !theta || !d_theta || (reinterpret_cast<uintptr_t>(theta) & 7) ||
+        (reinterpret_cast<uintptr_t>(d_theta) & 7) ||
+        (n > 0 && (!X || !d_rgb || !d_logit_opacity || !d_log_scale || !d_quat)))
+        return GS_ERR_INVALID_ARG;
+    return cuda_status(launch_ngp_bwd(cfg, theta, X, n, d_rgb, d_logit_opacity, d_log_scale, d_quat, d_theta,
+                                      S(stream)));
 }
 
 size_t gs_voxel_scratch_size(int64_t n) {

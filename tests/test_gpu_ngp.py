@@ -1,0 +1,114 @@
+"""The hash-grid MLP F(X | Theta) (Sec. III-C) on the GPU, through the
+C-ABI, against the FP64 oracle (oracle/ngp.py)."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import ngp as ongp
+from paper_2403_11577_gb300 import ngp, scenes
+
+from _util import ensure_built, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+LO, HI = [-10.0, -8.0, -1.0], [30.0, 12.0, 9.0]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    ensure_built()
+
+
+def _random_theta(cfg, seed):
+    """Parameters of the sizes the oracle expects, scaled so that every part
+    of the model matters (tables +-0.5, weights ~ 1/sqrt(fan_in))."""
+    rng = np.random.default_rng(seed)
+    o = ongp.NgpConfig(cfg.aabb_min, cfg.aabb_max, levels=cfg.levels, log2_table=cfg.log2_table)
+    theta = np.zeros(o.count())
+    P = o.unpack(theta)
+    P["tables"][...] = rng.uniform(-0.5, 0.5, P["tables"].shape)
+    for k, fan in (("W1", o.D), ("W2", o.H), ("W3", o.H)):
+        P[k][...] = rng.normal(0, 1.0 / np.sqrt(fan), P[k].shape)
+    for k in ("b1", "b2", "b3"):
+        P[k][...] = rng.normal(0, 0.1, P[k].shape)
+    return o, theta.astype(np.float32)
+
+
+def _attrs(n):
+    return {"rgb": torch.empty((n, 3), device="cuda"), "logit_opacity": torch.empty(n, device="cuda"),
+            "log_scale": torch.empty((n, 3), device="cuda"), "quat": torch.empty((n, 4), device="cuda")}
+
+
+def _points(rng, n):
+    X = rng.uniform(LO, HI, (n, 3))
+    X[:4] = [LO, HI, [HI[0], LO[1], HI[2]], [LO[0] - 3.0, HI[1] + 2.0, 0.5]]  # corners and outside the box
+    return X.astype(np.float32)
+
+
+@pytest.mark.parametrize("log2_table", [19, 12])
+def test_ngp_forward_matches_oracle(log2_table):
+    cfg = ngp.HashGridConfig(LO, HI, log2_table=log2_table)
+    o, theta = _random_theta(cfg, 1)
+    assert cfg.res == o.res and cfg.param_count() == o.count()
+    mlp = ngp.HashGridMLP(cfg)
+    mlp.theta.copy_(torch.from_numpy(theta))
+    X = _points(np.random.default_rng(2), 400)
+    out = _attrs(len(X))
+    mlp.forward(torch.from_numpy(X).cuda(), out)
+    ref = ongp.forward(o, theta.astype(np.float64), X)
+    for k in ref:
+        np.testing.assert_allclose(out[k].cpu().numpy(), ref[k], rtol=0, atol=5e-5, err_msg=k)
+
+
+@pytest.mark.parametrize("log2_table", [19, 10])
+def test_ngp_backward_matches_oracle(log2_table):
+    """Every parameter block of the gradient, with dense, hashed and (small
+    tables) colliding levels."""
+    cfg = ngp.HashGridConfig(LO, HI, log2_table=log2_table)
+    o, theta = _random_theta(cfg, 3)
+    mlp = ngp.HashGridMLP(cfg)
+    mlp.theta.copy_(torch.from_numpy(theta))
+    rng = np.random.default_rng(4)
+    X = _points(rng, 300)
+    d = {"rgb": rng.normal(size=(300, 3)), "logit_opacity": rng.normal(size=300),
+         "log_scale": rng.normal(size=(300, 3)), "quat": rng.normal(size=(300, 4))}
+    mlp.backward(torch.from_numpy(X).cuda(), {k: torch.from_numpy(v.astype(np.float32)).cuda() for k, v in d.items()})
+    got = mlp.grad.cpu().numpy()
+    ref = ongp.backward(o, theta.astype(np.float64), X, d["rgb"], d["logit_opacity"], d["log_scale"], d["quat"])
+    off = 0
+    for name, numel in cfg.blocks():
+        assert rel_l2(got[off:off + numel], ref[off:off + numel]) <= 1e-4, name
+        off += numel
+
+
+def test_ngp_on_the_accumulated_cloud():
+    """The 1M-point cloud of the batched scene with the default configuration
+    (2^19 entries, initial parameters): attributes of sampled points, and the
+    full gradient for attribute gradients on those points only (the oracle's
+    backward over them is then exact)."""
+    X = scenes.batched_problem(n=1_000_000).scenes[0].X
+    Xd = torch.from_numpy(X).cuda()
+    cfg = ngp.HashGridConfig.for_points(Xd)
+    mlp = ngp.HashGridMLP(cfg, seed=5)
+    o = ongp.NgpConfig(cfg.aabb_min, cfg.aabb_max)
+    assert o.res == cfg.res
+    theta = mlp.theta.cpu().numpy().astype(np.float64)
+    out = _attrs(len(X))
+    mlp.forward(Xd, out)
+    rng = np.random.default_rng(6)
+    idx = np.sort(rng.choice(len(X), 120, replace=False))
+    ref = ongp.forward(o, theta, X[idx])
+    for k in ref:
+        np.testing.assert_allclose(out[k].cpu().numpy()[idx], ref[k], rtol=0, atol=2e-5, err_msg=k)
+    dd = {"rgb": rng.normal(size=(120, 3)), "logit_opacity": rng.normal(size=120),
+          "log_scale": rng.normal(size=(120, 3)), "quat": rng.normal(size=(120, 4))}
+    full = {k: torch.zeros_like(v) for k, v in out.items()}
+    for k, v in dd.items():
+        full[k][torch.from_numpy(idx).cuda()] = torch.from_numpy(v.astype(np.float32)).cuda().view(-1, *full[k].shape[1:])
+    mlp.backward(Xd, full)
+    ref_g = ongp.backward(o, theta, X[idx], dd["rgb"], dd["logit_opacity"], dd["log_scale"], dd["quat"])
+    got = mlp.grad.cpu().numpy()
+    off = 0
+    for name, numel in cfg.blocks():
+        assert rel_l2(got[off:off + numel], ref_g[off:off + numel]) <= 1e-4, name
+        off += numel
