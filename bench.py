@@ -285,8 +285,28 @@ def paper_loop(args, problem, scene, opts, ext, delta, ext_t, delta_t, dev, worl
         vb.record()
         torch.cuda.synchronize()
         vox.append(va.elapsed_time(vb))
+    # the attribute model F(X | Theta) (hash-grid MLP) over the 2 cm voxel points
+    from paper_2403_11577_gb300 import ngp
+    Xk = scene.X[kept].contiguous()
+    mlp = ngp.HashGridMLP(ngp.HashGridConfig.for_points(scene.X), device=dev)
+    attrs = {"rgb": torch.empty_like(Xk), "logit_opacity": torch.empty(Xk.shape[0], device=dev),
+             "log_scale": torch.empty_like(Xk), "quat": torch.empty((Xk.shape[0], 4), device=dev)}
+    grads = {k: torch.randn_like(v) for k, v in attrs.items()}
+    tf, tb = [], []
+    for _ in range(4):
+        va.record()
+        mlp.forward(Xk, attrs)
+        vb.record()
+        torch.cuda.synchronize()
+        tf.append(va.elapsed_time(vb))
+        va.record()
+        mlp.backward(Xk, grads)
+        vb.record()
+        torch.cuda.synchronize()
+        tb.append(va.elapsed_time(vb))
     return {"value": world * args.steps / t, "unit": "iters/s", "ms_per_step": t * 1e3 / args.steps,
             "voxel_downsample_ms": statistics.median(vox), "voxel_kept_2cm": int(kept.numel()),
+            "ngp_forward_ms": statistics.median(tf[1:]), "ngp_backward_ms": statistics.median(tb[1:]),
             "loss": "L_photo = 0.8 L1 + 0.2 D-SSIM (11x11 Gaussian window), rows 188-375 of each 1408x376 frame",
             "loss_ms": statistics.median(ts), "pairs_per_iter": int(plan.stats().num_pairs),
             "l_photo": float(loss[0]), "l1": float(loss[1]), "dssim": float(loss[2])}

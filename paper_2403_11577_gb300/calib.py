@@ -31,7 +31,7 @@ import time
 import numpy as np
 import torch
 
-from . import build, render, scenes
+from . import build, ngp, render, scenes
 
 GAUSS_LR = {"rgb": 2.5e-3, "logit_opacity": 5e-2, "log_scale": 5e-3, "quat": 1e-3}
 
@@ -62,7 +62,8 @@ def rig_errors(ext, delta, ext_true, delta_true):
 
 def run_calibration(problem, iters=3000, warmup=500, lr_rot=1e-4, lr_trans=5e-3, lr_delta=1e-3,
                     lambda_scale=1e-3, opts=None, seed=0, log_every=250, reinit=True, train_scene=True,
-                    scene_lr_scale=1.0, device="cuda", loss="l1", schedule=None, clamp_scale=True):
+                    scene_lr_scale=1.0, device="cuda", loss="l1", schedule=None, clamp_scale=True, model="direct",
+                    mlp_lr=1e-2, grid_weight_decay=1e-4):
     """Calibrate every camera of `problem` (its ext/delta are the start,
     ext_target/delta_target the truth; errors are the worst over cameras).
     train_scene=False keeps the Gaussian attributes fixed (calibration only).
@@ -74,6 +75,12 @@ def run_calibration(problem, iters=3000, warmup=500, lr_rot=1e-4, lr_trans=5e-3,
     attributes live on the full cloud, so each phase continues from their
     current values; iters is then the sum of the phases.  Targets are always
     rendered from the full cloud at the true calibration.
+
+    model="mlp" learns the attributes through F(X | Theta) (Sec. III-C,
+    ngp.HashGridMLP): every iteration evaluates it for the rendered
+    Gaussians and carries their attribute gradients back into Theta (Adam,
+    lr mlp_lr, weight decay grid_weight_decay on the hash grid as in the
+    paper); model="direct" learns per-Gaussian attributes.
 
     Returns a dict with the error history, the final errors, the wall time
     and, with a schedule, the Gaussians and time of each phase."""
@@ -108,6 +115,17 @@ def run_calibration(problem, iters=3000, warmup=500, lr_rot=1e-4, lr_trans=5e-3,
     delta_p.grad = torch.zeros_like(delta_p)
     opt_scene = torch.optim.Adam([{"params": [params[k]], "lr": GAUSS_LR[k] * scene_lr_scale} for k in GAUSS_LR],
                                  eps=1e-15)
+    mlp = None
+    if model == "mlp":
+        mlp = ngp.HashGridMLP(ngp.HashGridConfig.for_points(full.X), device=dev, seed=seed)
+        nt = mlp.cfg.levels * mlp.cfg.T * 2
+        grid, net = mlp.theta[:nt], mlp.theta[nt:]
+        grid.grad, net.grad = mlp.grad[:nt], mlp.grad[nt:]
+        opt_scene = torch.optim.Adam([{"params": [grid], "weight_decay": grid_weight_decay},
+                                      {"params": [net], "weight_decay": 0.0}], lr=mlp_lr, betas=(0.9, 0.99),
+                                     eps=1e-15)
+    elif model != "direct":
+        raise ValueError("model must be 'direct' or 'mlp'")
     opt_cal = torch.optim.Adam([{"params": [rot], "lr": lr_rot}, {"params": [trans], "lr": lr_trans},
                                 {"params": [delta_p], "lr": lr_delta}], eps=1e-15)
     base_lrs = [g["lr"] for g in opt_cal.param_groups]
@@ -133,11 +151,24 @@ def run_calibration(problem, iters=3000, warmup=500, lr_rot=1e-4, lr_trans=5e-3,
             ext[:, :3].copy_(rot)
             ext[:, 3:].copy_(trans)
             delta.copy_(delta_p)
-            if idx is not None and train_scene:
+            if mlp is not None:
+                mlp.forward(scene.X, {k: getattr(scene, k) for k in GAUSS_LR})
+            elif idx is not None and train_scene:
                 for k in GAUSS_LR:
                     getattr(scene, k).copy_(params[k][idx])
             loss_v = step()
-            if train_scene:
+            if mlp is not None and train_scene:
+                g = dict(step.grads)
+                if lambda_scale > 0:  # L_scale (Eq. 7) on the predicted scales
+                    with torch.enable_grad():
+                        ls = scene.log_scale.detach().requires_grad_(True)
+                        sc = torch.exp(ls)
+                        reg = lambda_scale * (sc - sc.mean(dim=1, keepdim=True)).abs().sum()
+                        (g_ls,) = torch.autograd.grad(reg, ls)
+                    g["log_scale"] = g["log_scale"] + g_ls
+                mlp.backward(scene.X, g)
+                opt_scene.step()
+            elif train_scene:
                 for k in GAUSS_LR:
                     if idx is None:
                         params[k].grad.copy_(step.grads[k])
@@ -166,7 +197,7 @@ def run_calibration(problem, iters=3000, warmup=500, lr_rot=1e-4, lr_trans=5e-3,
                 delta_p.grad.copy_(step.grads["delta"])
                 opt_cal.step()
             # keep quaternions away from zero norm
-            if train_scene and it % 100 == 99:
+            if train_scene and mlp is None and it % 100 == 99:
                 with torch.no_grad():
                     q = params["quat"]
                     q.div_(q.norm(dim=1, keepdim=True).clamp_min(1e-8))
@@ -216,24 +247,30 @@ def main():
     ap.add_argument("--cameras", type=int, default=1, help="forward cameras of the rig, calibrated jointly")
     ap.add_argument("--schedule", default=None,
                     help="coarse-to-fine voxelization, e.g. 0.10:2000,0.05:500,0.02:500 (Sec. III-D, Sec. IV-C)")
+    ap.add_argument("--attributes", choices=["random", "surface"], default="random",
+                    help="the target scene's Gaussian shapes and opacities: i.i.d. random, or smooth along surfaces")
+    ap.add_argument("--model", choices=["direct", "mlp"], default="direct",
+                    help="joint mode: per-Gaussian attributes, or the hash-grid MLP F(X | Theta) (Sec. III-C)")
     ap.add_argument("--no-scale-clamp", action="store_true",
                     help="with --schedule: do not bound the scales by the voxel size")
     ap.add_argument("--mode", choices=["joint", "pose"], default="joint",
                     help="joint: re-initialised scene trained with the calibration; "
                          "pose: the scene's attributes fixed at their true values")
     a = ap.parse_args()
-    p = scenes.calibration_problem(seed=a.seed, n=a.gaussians, trajectory=a.trajectory, cameras=a.cameras)
+    p = scenes.calibration_problem(seed=a.seed, n=a.gaussians, trajectory=a.trajectory, cameras=a.cameras,
+                                   attributes=a.attributes)
     if a.crop:
         for f in p.frames:
             f.row0 = f.camera.height // 2
     sched = parse_schedule(a.schedule) if a.schedule else None
-    kw = dict(seed=a.seed, loss=a.loss, schedule=sched, clamp_scale=not a.no_scale_clamp)
+    kw = dict(seed=a.seed, loss=a.loss, schedule=sched, clamp_scale=not a.no_scale_clamp, model=a.model)
     if a.mode == "pose":
         res = run_calibration(p, iters=a.iters, warmup=0, reinit=False, train_scene=False, **kw)
     else:
         res = run_calibration(p, iters=a.iters, warmup=a.warmup, reinit=True, **kw)
     res.update(trajectory=a.trajectory, mode=a.mode, seed=a.seed, gaussians=a.gaussians, loss=a.loss, crop=a.crop,
-               cameras=a.cameras, schedule=a.schedule, scale_clamp=not a.no_scale_clamp)
+               cameras=a.cameras, schedule=a.schedule, scale_clamp=not a.no_scale_clamp, model=a.model,
+               attributes=a.attributes)
     print(json.dumps(res))
 
 

@@ -310,7 +310,34 @@ def _yaw_rotate(dirs, yaw):
     return out
 
 
-def _drive_scene(rng, n, sweeps=50, speed=10.0, rate=10.0, smooth=True, trajectory="straight"):
+def _surface_attributes(rng, world, pts, ids):
+    """Attributes that vary smoothly along each surface: discs flattened
+    along the surface normal (the ground's z; for a box, the axis of the face
+    the point lies on), about 6 cm across and 1 cm thick with a low-frequency
+    modulation, opacity between ~0.8 and ~0.95, no rotation.  Real surfaces
+    are continuous over large areas (walls, roads), which a spatially
+    regularised attribute model can represent."""
+    n = len(pts)
+    normal = np.full(n, 2)
+    on_box = ids < len(world.lo)
+    if on_box.any():
+        lo, hi = world.lo[ids[on_box]], world.hi[ids[on_box]]
+        p = pts[on_box]
+        d = np.minimum(np.abs(p - lo), np.abs(p - hi))
+        normal[on_box] = np.argmin(d, axis=1)
+    k = rng.uniform(0.3, 0.8, size=3)
+    ph = rng.uniform(0, 2 * math.pi, size=3)
+    wave = np.sin(k[0] * pts[:, 0] + ph[0]) + np.sin(k[1] * pts[:, 1] + ph[1]) + np.sin(k[2] * pts[:, 2] + ph[2])
+    s = np.full((n, 3), 0.06) * np.exp(0.15 * wave)[:, None]
+    s[np.arange(n), normal] = 0.01
+    logit_o = 2.0 + 0.4 * np.sin(0.5 * pts[:, 0] + ph[0]) * np.cos(0.5 * pts[:, 1] + ph[1])
+    q = np.zeros((n, 4))
+    q[:, 0] = 1.0
+    return q.astype(np.float32), np.log(s).astype(np.float32), logit_o.astype(np.float32)
+
+
+def _drive_scene(rng, n, sweeps=50, speed=10.0, rate=10.0, smooth=True, trajectory="straight",
+                 attributes="random"):
     """Points from LiDAR sweeps along a drive.  'straight': 10 m/s along x
     with a constant heading.  'zigzag': the same forward speed with a lateral
     swing y = 3 sin(2 pi t / 2.5) m and the heading following the path (so
@@ -344,6 +371,10 @@ def _drive_scene(rng, n, sweeps=50, speed=10.0, rate=10.0, smooth=True, trajecto
     sel.sort()
     pts, ids = pts[sel], ids[sel]
     q, log_s, logit_o = _attributes(rng, n, 0.02, 0.3)
+    if attributes == "surface":
+        q, log_s, logit_o = _surface_attributes(rng, world, pts, ids)
+    elif attributes != "random":
+        raise ValueError(attributes)
     if smooth:
         rgb = _smooth_colour(rng, world, pts, ids)
     else:
@@ -352,12 +383,13 @@ def _drive_scene(rng, n, sweeps=50, speed=10.0, rate=10.0, smooth=True, trajecto
                  traj_t, traj_p, traj_q)
 
 
-def batched_problem(seed: int = 2, n: int = 1_000_000, frames: int = 8, trajectory: str = "straight") -> Problem:
+def batched_problem(seed: int = 2, n: int = 1_000_000, frames: int = 8, trajectory: str = "straight",
+                    attributes: str = "random") -> Problem:
     """1M Gaussians from 50 sweeps along a 10 m/s drive sampled at 10 Hz
     (straight by default); eight 1408x376 frames at t = 0.5, 1.0, ..., 4.0 s;
     true delta 40 ms."""
     rng = np.random.default_rng(seed)
-    scene = _drive_scene(rng, n, trajectory=trajectory)
+    scene = _drive_scene(rng, n, trajectory=trajectory, attributes=attributes)
     ext = _true_extrinsic(rng)[None]
     fr = [Frame(CAM_KITTI, 0.5 * (i + 1)) for i in range(frames)]
     return Problem("batched", [scene], fr, ext, np.array([0.04]), tile=16)
@@ -396,7 +428,7 @@ def rig_extrinsics(rng, cameras: int):
 def calibration_problem(seed: int = 0, n: int = 1_000_000, frames: int = 8,
                         rot_deg: float = 5.0, trans_m: float = 0.5,
                         delta0: float = 0.05, scene_seed: int = 2, trajectory: str = "straight",
-                        cameras: int = 1) -> Problem:
+                        cameras: int = 1, attributes: str = "random") -> Problem:
     """The batched scene; targets at the true extrinsic and delta = 0, start
     from the extrinsic perturbed by rot_deg about a seeded axis and trans_m
     along a seeded direction, and delta = delta0.  On the straight drive a
@@ -406,8 +438,11 @@ def calibration_problem(seed: int = 0, n: int = 1_000_000, frames: int = 8,
     cameras > 1: a rig of forward cameras on one scene (rig_extrinsics),
     `frames` frames per camera at the same timestamps, each camera with its
     own true extrinsic and time offset and its own seeded start (the same
-    rot_deg / trans_m distance, delta0 above its true offset)."""
-    base = batched_problem(scene_seed, n, frames, trajectory=trajectory)
+    rot_deg / trans_m distance, delta0 above its true offset).
+
+    attributes="surface": Gaussian shapes and opacities that vary smoothly
+    along each surface (_surface_attributes) instead of i.i.d. random ones."""
+    base = batched_problem(scene_seed, n, frames, trajectory=trajectory, attributes=attributes)
     rng = np.random.default_rng(1000 + seed)
     if cameras == 1:
         true, true_delta = base.ext.copy(), np.zeros(1)
