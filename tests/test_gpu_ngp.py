@@ -112,3 +112,20 @@ def test_ngp_on_the_accumulated_cloud():
     for name, numel in cfg.blocks():
         assert rel_l2(got[off:off + numel], ref_g[off:off + numel]) <= 1e-4, name
         off += numel
+
+
+def test_joint_calibration_through_the_hash_grid_mlp():
+    """Joint calibration (Sec. III-C, III-D): the Gaussians' attributes are
+    learned through F(X | Theta) from its initialisation while the extrinsic
+    and the time offset are recovered from 1 deg / 10 cm / 10 ms, with
+    L_photo on the bottom half of every frame of a small surface scene."""
+    from paper_2403_11577_gb300 import calib
+    p = scenes.calibration_problem(seed=3, n=150_000, frames=4, rot_deg=1.0, trans_m=0.1, delta0=0.01,
+                                   trajectory="zigzag", attributes="surface")
+    for f in p.frames:
+        f.camera = scenes.Camera(704, 188, 276.0, 276.0, 341.0, 119.0)
+        f.row0 = f.camera.height // 2
+    res = calib.run_calibration(p, iters=1500, warmup=300, model="mlp", loss="photo", log_every=0)
+    st, fin = res["start"], res["final"]
+    assert st["rot_deg"] > 0.9 and st["trans_cm"] > 9.0 and st["delta_ms"] > 9.0
+    assert fin["rot_deg"] < 0.2 and fin["trans_cm"] < 3.0 and fin["delta_ms"] < 3.0, fin
