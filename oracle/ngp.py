@@ -118,6 +118,29 @@ def forward(cfg, theta, X):
             "quat": out[:, 7:11].copy()}
 
 
+def relu_margins(cfg, theta, X):
+    """Per point, the smallest |a| / (sum_k |W_jk x_k| + |b_j|) over the
+    pre-activations a_j of both hidden layers: how close a ReLU decision is
+    to zero relative to the size of the terms that form it.  A kernel whose
+    products carry a relative error e can take a different decision only
+    where this margin is below about e; tests exclude such points instead of
+    comparing a gradient that depends on which side of zero a rounding fell."""
+    P = cfg.unpack(np.asarray(theta, np.float64))
+    X = np.asarray(X, np.float64).reshape(-1, 3)
+    out = np.zeros(len(X))
+    for i, x in enumerate(X):
+        enc, _ = encode_point(cfg, P["tables"], x)
+        a1 = P["W1"] @ enc + P["b1"]
+        s1 = np.abs(P["W1"]) @ np.abs(enc) + np.abs(P["b1"])
+        h1 = np.maximum(a1, 0.0)
+        a2 = P["W2"] @ h1 + P["b2"]
+        s2 = np.abs(P["W2"]) @ h1 + np.abs(P["b2"])
+        with np.errstate(divide="ignore", invalid="ignore"):
+            m = np.concatenate([np.abs(a1) / s1, np.abs(a2) / s2])
+        out[i] = np.nanmin(np.where(np.isfinite(m), m, np.inf))
+    return out
+
+
 def backward(cfg, theta, X, d_rgb, d_logit_opacity, d_log_scale, d_quat):
     """Gradient of sum(d_attr . attr) with respect to theta (flat)."""
     theta = np.asarray(theta, np.float64)

@@ -111,6 +111,29 @@ def test_mlp_matches_torch_float64_layers():
     np.testing.assert_allclose(out["quat"], o[:, 7:11], rtol=1e-13)
 
 
+def test_relu_margins_against_torch_layers_and_an_exact_zero():
+    """The margin is the smallest |pre-activation| / (sum of |terms| + |bias|)
+    over both hidden layers (torch float64 layers on |W| and |x| give the
+    scales); a bias set to cancel one pre-activation exactly gives 0."""
+    cfg = _cfg(log2_table=12)
+    rng = np.random.default_rng(5)
+    theta = _random_theta(cfg, rng)
+    P = cfg.unpack(theta)
+    X = rng.uniform(cfg.aabb_min, cfg.aabb_max, (12, 3))
+    enc = torch.tensor(np.stack([ngp.encode_point(cfg, P["tables"], x)[0] for x in X]))
+    t = {k: torch.tensor(v) for k, v in P.items() if k != "tables"}
+    lin = torch.nn.functional.linear
+    a1 = lin(enc, t["W1"], t["b1"])
+    s1 = lin(enc.abs(), t["W1"].abs(), t["b1"].abs())
+    h1 = torch.relu(a1)
+    a2 = lin(h1, t["W2"], t["b2"])
+    s2 = lin(h1, t["W2"].abs(), t["b2"].abs())
+    want = torch.cat([a1.abs() / s1, a2.abs() / s2], dim=1).min(dim=1).values.numpy()
+    np.testing.assert_allclose(ngp.relu_margins(cfg, theta, X), want, rtol=1e-12)
+    P["b1"][5] = -float(P["W1"][5] @ enc[3].numpy())
+    assert ngp.relu_margins(cfg, theta, X[3:4])[0] < 1e-14
+
+
 @pytest.mark.parametrize("log2_table", [19, 8])
 def test_backward_matches_central_differences(log2_table):
     """Gradient of sum(d . F(X | theta)) against FP64 central differences, on
