@@ -359,6 +359,13 @@ gs_status gs_ngp_backward(const gs_ngp *cfg, const float *theta, const float *X,
                           const float *d_logit_opacity, const float *d_log_scale, const float *d_quat,
                           float *d_theta, void *stream);
 
+/* Reads and clears the fault word of the hash-grid kernels on the current
+ * device (host; waits for the device).  Bit 0: a tensor-core wait of
+ * gs_ngp_forward or gs_ngp_backward ran out of time (one second), so that
+ * call's outputs are incomplete; the backward then also adds NaN to
+ * d_theta[0].  Errors: GS_ERR_INVALID_ARG (NULL out), GS_ERR_CUDA. */
+gs_status gs_ngp_fault(uint32_t *out);
+
 /* Accumulated-LiDAR downsampling (Sec. III-D): keep one point per occupied
  * voxel of edge `voxel`, the point of smallest index.  A point's voxel is
  * (floor(x / voxel), floor(y / voxel), floor(z / voxel)) with the quotients

@@ -75,6 +75,7 @@ _SIGS = {
     "gs_bin_sort_noalloc": ([_P] * 9, C.c_int32),
     "gs_voxel_scratch_size": ([C.c_int64], C.c_size_t),
     "gs_ngp_param_count": ([_P], C.c_int64),
+    "gs_ngp_fault": ([_P], C.c_int32),
     "gs_ngp_forward": ([_P, _P, _P, C.c_int64, _P, _P, _P, _P, _P], C.c_int32),
     "gs_ngp_backward": ([_P, _P, _P, C.c_int64, _P, _P, _P, _P, _P, _P], C.c_int32),
     "gs_voxel_downsample": ([_P, C.c_int64, C.c_float, _P, _P, _P, _P], C.c_int32),
@@ -289,6 +290,14 @@ def gs_ngp_backward(cfg, theta, X, d_rgb, d_logit_opacity, d_log_scale, d_quat, 
                                  _ptr(d_rgb, F32, "d_rgb"), _ptr(d_logit_opacity, F32, "d_logit_opacity"),
                                  _ptr(d_log_scale, F32, "d_log_scale"), _ptr(d_quat, F32, "d_quat"),
                                  _ptr(d_theta, F32, "d_theta"), _stream(stream)), "gs_ngp_backward")
+
+
+def gs_ngp_fault():
+    """Read and clear the hash-grid kernels' fault word (bit 0: a tensor-core
+    wait ran out; that call's outputs are incomplete)."""
+    v = C.c_uint32(0)
+    _check(lib().gs_ngp_fault(C.byref(v)), "gs_ngp_fault")
+    return int(v.value)
 
 
 def gs_voxel_scratch_size(n):
