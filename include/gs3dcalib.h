@@ -354,7 +354,9 @@ gs_status gs_ngp_forward(const gs_ngp *cfg, const float *theta, const float *X, 
 /* Backward of sum(d_attr . F(X | theta)): adds the gradient with respect to
  * theta into d_theta (the caller zeroes it first; table entries are summed
  * with atomics, so their float rounding order varies between runs).
- * Errors: GS_ERR_INVALID_ARG, GS_ERR_CUDA. */
+ * theta must be 8-byte and d_theta 16-byte aligned (the table gradient is
+ * added with float2 and float4 atomics).
+ * Errors: GS_ERR_INVALID_ARG (also for misaligned pointers), GS_ERR_CUDA. */
 gs_status gs_ngp_backward(const gs_ngp *cfg, const float *theta, const float *X, int64_t n, const float *d_rgb,
                           const float *d_logit_opacity, const float *d_log_scale, const float *d_quat,
                           float *d_theta, void *stream);

@@ -328,7 +328,7 @@ gs_status gs_ngp_backward(const gs_ngp *cfg, const float *theta, const float *X,
                           const float *d_logit_opacity, const float *d_log_scale, const float *d_quat,
                           float *d_theta, void *stream) {
     if (ngp_param_count(cfg) < 0 || n < 0 || !theta || !d_theta || (reinterpret_cast<uintptr_t>(theta) & 7) ||
-        (reinterpret_cast<uintptr_t>(d_theta) & 7) ||
+        (reinterpret_cast<uintptr_t>(d_theta) & 15) ||
         (n > 0 && (!X || !d_rgb || !d_logit_opacity || !d_log_scale || !d_quat)))
         return GS_ERR_INVALID_ARG;
     return cuda_status(launch_ngp_bwd(cfg, theta, X, n, d_rgb, d_logit_opacity, d_log_scale, d_quat, d_theta,

@@ -30,8 +30,9 @@
 //
 // Backward: per tile the forward is recomputed, dO = dL/do goes back through
 // the heads, dH2 = dO W3, dH1 = dA2 W2 and dENC = dA1 W1 (dA = dH masked by
-// the ReLU), and the table gradient is scattered with one float2 atomic per
-// (point, level, vertex).  The weight gradients are contractions over the
+// the ReLU), and the table gradient is scattered with float2 atomics per
+// (point, level, vertex), one float4 atomic where two x-neighbours of a cell
+// are adjacent table entries.  The weight gradients are contractions over the
 // points.  They accumulate in tensor memory over all tiles of a block as two
 // stacked 128-row MMAs whose operands are the tile buffers read transposed
 // (MN-major):
@@ -275,7 +276,7 @@ constexpr int kBwdY = kTile * 128 * 2;          // [dO (16) | H1 (64) | ENC (32)
 constexpr int kBias = (kH + kH + 16 + 16) * 4;  // b1, b2, b3 (16), db3 (16)
 
 constexpr size_t fwd_smem() { return 2 * (kW1 + kW2 + kW3 + kFwdF) + kBias + 64; }
-constexpr size_t bwd_smem() { return 2 * (2 * (kW1 + kW2 + kW3) + kBwdX + kBwdY) + kBias + 64; }
+constexpr size_t bwd_smem() { return 2 * (2 * (kW1 + kW2 + kW3) + kBwdX + kBwdY) + kBias + 64 + 4 * kTile; }
 static_assert(bwd_smem() <= 227 * 1024, "backward shared memory");
 
 struct Carve {
@@ -541,6 +542,7 @@ k_ngp_bwd(NgpArgs a, const float *__restrict__ theta, const float *__restrict__ 
     float *db3 = bias + 2 * kH + 16;
     uint64_t *bar = reinterpret_cast<uint64_t *>(cv.p + kBias);
     uint32_t *tslot = reinterpret_cast<uint32_t *>(cv.p + kBias + 16);
+    unsigned int *live = reinterpret_cast<unsigned int *>(cv.p + kBias + 64);  // [128]: point has a gradient
     stage_weights(a, theta, W1, W2, W3, &W1t, &W2t, &W3t, bias);
     for (int e = threadIdx.x; e < 16; e += kThreads) db3[e] = 0.f;
     // Y columns 80 + 2L .. 111 stay zero, column 112 is one, 113 .. 127 zero
@@ -605,6 +607,10 @@ k_ngp_bwd(NgpArgs a, const float *__restrict__ theta, const float *__restrict__ 
             }
             put8(Yb, ln.row, 0, g);
             put8(Yb, ln.row, 8, g + 8);
+            bool any = false;
+#pragma unroll
+            for (int k = 0; k < kO; k++) any |= g[k] != 0.f;
+            live[ln.row] = any ? 1u : 0u;
 #pragma unroll
             for (int k = 0; k < kO; k++) {
                 float v = g[k];
@@ -641,11 +647,13 @@ k_ngp_bwd(NgpArgs a, const float *__restrict__ theta, const float *__restrict__ 
         }
         if (!(ok = s.wait_all())) break;
         started = true;
+        const bool point_live = live[ln.row] != 0u;
         // encoding gradient into the tables: this thread's levels 8 half .. 8 half + 7
+        // (a point without upstream gradient adds exact zeros: skipped)
         {
             float g[16];
             tmem_ld16(tm + kB_DENC + ln.lane_base + (uint32_t)(16 * ln.half), g);
-            if (i < n) {
+            if (i < n && point_live) {
                 float px, py, pz;
                 unit_point(a, X, i, px, py, pz);
 #pragma unroll
@@ -656,9 +664,19 @@ k_ngp_bwd(NgpArgs a, const float *__restrict__ theta, const float *__restrict__ 
                     float w[8];
                     cell_taps(a, l, px, py, pz, slot, w);
                     float2 *tab = reinterpret_cast<float2 *>(d_theta) + (size_t)l * a.T;
+                    // corners c and c + 1 differ in x only; when the first slot is
+                    // even the two entries form one aligned float4
 #pragma unroll
-                    for (int c = 0; c < 8; c++)
-                        atomicAdd(tab + slot[c], make_float2(w[c] * g[2 * q], w[c] * g[2 * q + 1]));
+                    for (int c = 0; c < 8; c += 2) {
+                        const float2 v0 = make_float2(w[c] * g[2 * q], w[c] * g[2 * q + 1]);
+                        const float2 v1 = make_float2(w[c + 1] * g[2 * q], w[c + 1] * g[2 * q + 1]);
+                        if ((slot[c] & 1u) == 0u && slot[c + 1] == slot[c] + 1u) {
+                            atomicAdd(reinterpret_cast<float4 *>(tab + slot[c]), make_float4(v0.x, v0.y, v1.x, v1.y));
+                        } else {
+                            atomicAdd(tab + slot[c], v0);
+                            atomicAdd(tab + slot[c + 1], v1);
+                        }
+                    }
                 }
             }
         }
