@@ -94,3 +94,44 @@ class HashGridMLP:
             self.grad.zero_()
         capi.gs_ngp_backward(self.cfg_c, self.theta, X, grads["rgb"], grads["logit_opacity"], grads["log_scale"],
                              grads["quat"], self.grad)
+
+
+def _main():
+    """Times forward and backward on a synthetic cloud: points uniform in a
+    120 x 40 x 15 m box, random upstream gradients on every point (CUDA
+    events; one JSON line with the median times)."""
+    import argparse
+    import json
+    import statistics
+
+    ap = argparse.ArgumentParser(description=_main.__doc__)
+    ap.add_argument("--points", type=int, default=831_000)
+    ap.add_argument("--reps", type=int, default=20)
+    a = ap.parse_args()
+    n = a.points
+    g = torch.Generator(device="cpu").manual_seed(0)
+    X = (torch.rand((n, 3), generator=g) * torch.tensor([120.0, 40.0, 15.0]) - torch.tensor([10.0, 20.0, 2.0]))
+    X = X.cuda()
+    mlp = HashGridMLP(HashGridConfig.for_points(X), device="cuda")
+    out = {"rgb": torch.empty((n, 3), device="cuda"), "logit_opacity": torch.empty(n, device="cuda"),
+           "log_scale": torch.empty((n, 3), device="cuda"), "quat": torch.empty((n, 4), device="cuda")}
+    grads = {k: torch.randn(v.shape, generator=g).cuda() * 1e-3 for k, v in out.items()}
+    res = {"points": n}
+    for name, fn in (("forward", lambda: mlp.forward(X, out)), ("backward", lambda: mlp.backward(X, grads))):
+        for _ in range(min(3, a.reps)):
+            fn()
+        ts = []
+        for _ in range(a.reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        res[name + "_ms"] = statistics.median(ts)
+    res["fault"] = capi.gs_ngp_fault()
+    print(json.dumps(res))
+
+
+if __name__ == "__main__":
+    _main()
