@@ -271,13 +271,9 @@ __device__ __forceinline__ void mma3(uint32_t d, const Op &A, const Op &B, int k
 // Byte size of one part of each matrix.
 constexpr int kW1 = kH * kK1 * 2, kW2 = kH * kH * 2, kW3 = 16 * kH * 2;
 constexpr int kFwdF = kTile * 96 * 2;           // [ENC (32) | H (64)]
-constexpr int kBwdX = kTile * 192 * 2;          // [H2 | dA2 | dA1]
-constexpr int kBwdY = kTile * 128 * 2;          // [dO (16) | H1 (64) | ENC (32) | 1 (16)]
 constexpr int kBias = (kH + kH + 16 + 16) * 4;  // b1, b2, b3 (16), db3 (16)
 
 constexpr size_t fwd_smem() { return 2 * (kW1 + kW2 + kW3 + kFwdF) + kBias + 64; }
-constexpr size_t bwd_smem() { return 2 * (2 * (kW1 + kW2 + kW3) + kBwdX + kBwdY) + kBias + 64 + 4 * kTile; }
-static_assert(bwd_smem() <= 227 * 1024, "backward shared memory");
 
 struct Carve {
     unsigned char *p;
@@ -288,35 +284,26 @@ struct Carve {
     }
 };
 
-// Weights of the forward (B operands, rows = outputs) and, with the
-// transposes, of the backward, as bf16 hi/lo parts from theta; biases FP32.
+// Weights (B operands, rows = outputs; the backward reads them MN-major as
+// their transposes) as bf16 hi/lo parts from theta; biases in FP32.
 __device__ void stage_weights(const NgpArgs &a, const float *__restrict__ theta, const Mat &W1, const Mat &W2,
-                              const Mat &W3, const Mat *W1t, const Mat *W2t, const Mat *W3t, float *bias) {
-    const int D = a.D;
+                              const Mat &W3, float *bias) {
+    const int D = a.D, nt = (int)blockDim.x;
     const float *m = theta + a.w1;
-    for (int e = threadIdx.x; e < kH * kK1; e += kThreads) {
+    for (int e = threadIdx.x; e < kH * kK1; e += nt) {
         const int j = e / kK1, i = e % kK1;
-        const float v = i < D ? m[j * D + i] : 0.f;
-        put(W1, j, i, v);
-        if (W1t) put(*W1t, i, j, v);
+        put(W1, j, i, i < D ? m[j * D + i] : 0.f);
     }
-    for (int e = threadIdx.x; e < kH * kH; e += kThreads) {
-        const int j = e / kH, k = e % kH;
-        const float v = m[off_w2(D) + e];
-        put(W2, j, k, v);
-        if (W2t) put(*W2t, k, j, v);
-    }
-    for (int e = threadIdx.x; e < 16 * kH; e += kThreads) {
+    for (int e = threadIdx.x; e < kH * kH; e += nt) put(W2, e / kH, e % kH, m[off_w2(D) + e]);
+    for (int e = threadIdx.x; e < 16 * kH; e += nt) {
         const int k = e / kH, j = e % kH;
-        const float v = k < kO ? m[off_w3(D) + k * kH + j] : 0.f;
-        put(W3, k, j, v);
-        if (W3t) put(*W3t, j, k, v);
+        put(W3, k, j, k < kO ? m[off_w3(D) + k * kH + j] : 0.f);
     }
-    for (int e = threadIdx.x; e < kH; e += kThreads) {
+    for (int e = threadIdx.x; e < kH; e += nt) {
         bias[e] = m[off_b1(D) + e];
         bias[kH + e] = m[off_b2(D) + e];
     }
-    for (int e = threadIdx.x; e < 16; e += kThreads) bias[2 * kH + e] = (e < kO) ? m[off_b3(D) + e] : 0.f;
+    for (int e = threadIdx.x; e < 16; e += nt) bias[2 * kH + e] = (e < kO) ? m[off_b3(D) + e] : 0.f;
 }
 
 // Encoding of the tile's points into columns c0 + 2l, c0 + 2l + 1 of E
@@ -454,8 +441,6 @@ __device__ __forceinline__ void on_timeout(const Sync &s) {
 
 // Tensor-memory columns.
 constexpr uint32_t kFwdCols = 256, kF_D1 = 0, kF_D2 = 64, kF_D3 = 128;
-constexpr uint32_t kBwdCols = 512, kB_ACCA = 0, kB_ACCB = 128, kB_D1 = 192, kB_D2 = 256, kB_D3 = 320, kB_DH2 = 336,
-                   kB_DH1 = 400, kB_DENC = 464;
 
 // Two blocks per SM (2 x 256 tensor-memory columns).
 __global__ void __launch_bounds__(kThreads, 2)
@@ -467,7 +452,7 @@ k_ngp_fwd(NgpArgs a, const float *__restrict__ theta, const float *__restrict__ 
     float *bias = reinterpret_cast<float *>(cv.p);
     uint64_t *bar = reinterpret_cast<uint64_t *>(cv.p + kBias);
     uint32_t *tslot = reinterpret_cast<uint32_t *>(cv.p + kBias + 16);
-    stage_weights(a, theta, W1, W2, W3, nullptr, nullptr, nullptr, bias);
+    stage_weights(a, theta, W1, W2, W3, bias);
     // encoding columns 2L .. 31 stay zero
     const int pad = kK1 - a.D;
     for (int e = threadIdx.x; e < kTile * pad; e += kThreads) put(F, e / pad, a.D + e % pad, 0.f);
@@ -528,7 +513,151 @@ k_ngp_fwd(NgpArgs a, const float *__restrict__ theta, const float *__restrict__ 
     tmem_free(tm, kFwdCols);
 }
 
-__global__ void __launch_bounds__(kThreads, 1)
+// ------------------------------------------------------------ backward
+
+// The backward block: 8 consumer warps (warps 0-7) run the MMA chain of tile
+// k while 4 producer warps (warps 8-11, one per tensor-memory lane quarter)
+// gather the encoding of tile k + 1 into the other encoding buffer and
+// scatter the table gradient of tile k - 1 from the other dENC columns.
+// The roles meet once per tile at a block barrier; inside the chain the
+// consumers synchronise among themselves (named barrier 1).
+constexpr int kBwdThreads = 384, kConsumers = 256;
+constexpr int kBwdX = kTile * 128 * 2;  // [H2, later dA1 (64) | dA2 (64)]
+constexpr int kBwdY = kTile * 96 * 2;   // [dO (16) | H1 (64) | 1 (16)]
+constexpr int kBwdE = kTile * 48 * 2;   // [ENC (32) | 1 (16)], two of them
+constexpr size_t bwd_smem() {
+    return 2 * (kW1 + kW2 + kW3 + kBwdX + kBwdY + 2 * kBwdE) + kBias + 64 + 2 * 4 * kTile;
+}
+static_assert(bwd_smem() <= 227 * 1024, "backward shared memory");
+
+// Tensor-memory columns of the backward (dENC double-buffered).
+constexpr uint32_t kB_ACCA = 0, kB_ACCB = 128, kB_T1 = 192, kB_T2 = 256, kB_DENC = 320;
+
+__device__ __forceinline__ void consumer_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+
+__device__ __forceinline__ void consumer_publish() {
+    fence_async_smem();
+    fence_before_sync();
+    consumer_sync();
+}
+
+// The consumers wait for the issuing thread's MMAs; a timeout in any of them
+// sets *abort (read by all consumers after their barrier).
+__device__ __forceinline__ bool consumer_wait(Sync &s, volatile int *abort) {
+    const bool ok = mbar_wait(s.bar, s.phase);
+    if (ok) s.phase ^= 1u;
+    else *abort = 1;
+    consumer_sync();
+    fence_after_sync();
+    return *abort == 0;
+}
+
+// Producer: the encoding of the tile's points (thread pt: point pt, every
+// level) into columns 2l, 2l + 1 of E.
+__device__ __forceinline__ void produce_encoding(const NgpArgs &a, const float *__restrict__ theta,
+                                                 const float *__restrict__ X, long long n, long long base,
+                                                 const Mat &E, int pt) {
+    const long long i = base + pt;
+    const bool valid = i < n;
+    float px = 0.f, py = 0.f, pz = 0.f;
+    if (valid) unit_point(a, X, i, px, py, pz);
+#pragma unroll 2
+    for (int l = 0; l < a.L; l++) {
+        float e0 = 0.f, e1 = 0.f;
+        if (valid) {
+            uint32_t slot[8];
+            float w[8];
+            cell_taps(a, l, px, py, pz, slot, w);
+            const float2 *tab = reinterpret_cast<const float2 *>(theta) + (size_t)l * a.T;
+            float2 v[8];
+#pragma unroll
+            for (int c = 0; c < 8; c++) v[c] = __ldg(tab + slot[c]);
+#pragma unroll
+            for (int c = 0; c < 8; c++) {
+                e0 = fmaf(w[c], v[c].x, e0);
+                e1 = fmaf(w[c], v[c].y, e1);
+            }
+        }
+        put2(E, pt, 2 * l, e0, e1);
+    }
+}
+
+// Producer: the table gradient of the warp's 32 points (one per lane, in
+// input order) from their dENC rows (32 columns of tensor memory at tdenc,
+// the warp's lane quarter).  Per level, lanes whose point lies in the same
+// cell as the previous lane's form a run (coherent inputs such as LiDAR
+// sweeps put many consecutive points in one coarse cell); a segmented scan
+// over the run sums its 8 vertex contributions and the run's last lane adds
+// them, so that one atomic per vertex replaces up to 32 on the same table
+// entry.  A warp without such runs at a level adds per lane.  Entries are
+// added as float2, or as one float4 where two x-neighbours of the cell are
+// adjacent table entries (the first slot even).
+__device__ __forceinline__ void add_vertex_pairs(float2 *tab, const uint32_t (&slot)[8], const float (&v)[16]) {
+#pragma unroll
+    for (int c = 0; c < 8; c += 2) {
+        if ((slot[c] & 1u) == 0u && slot[c + 1] == slot[c] + 1u) {
+            atomicAdd(reinterpret_cast<float4 *>(tab + slot[c]),
+                      make_float4(v[2 * c], v[2 * c + 1], v[2 * c + 2], v[2 * c + 3]));
+        } else {
+            atomicAdd(tab + slot[c], make_float2(v[2 * c], v[2 * c + 1]));
+            atomicAdd(tab + slot[c + 1], make_float2(v[2 * c + 2], v[2 * c + 3]));
+        }
+    }
+}
+
+__device__ __forceinline__ void produce_table_grad(const NgpArgs &a, const float *__restrict__ X, long long i,
+                                                   bool live, uint32_t tdenc, float *__restrict__ d_theta) {
+    float g[32];
+    tmem_ld16(tdenc, *reinterpret_cast<float(*)[16]>(g));
+    tmem_ld16(tdenc + 16u, *reinterpret_cast<float(*)[16]>(g + 16));
+    const uint32_t live_mask = __ballot_sync(0xffffffffu, live);
+    if (live_mask == 0u) return;
+    const int lane = (int)(threadIdx.x & 31);
+    float px = 0.f, py = 0.f, pz = 0.f;
+    if (live) unit_point(a, X, i, px, py, pz);
+#pragma unroll
+    for (int l = 0; l < kMaxLevels; l++) {
+        if (l >= a.L) break;
+        uint32_t slot[8];
+        float w[8];
+        cell_taps(a, l, px, py, pz, slot, w);
+        const float g0 = live ? g[2 * l] : 0.f, g1 = live ? g[2 * l + 1] : 0.f;
+        float v[16];
+#pragma unroll
+        for (int c = 0; c < 8; c++) {
+            v[2 * c] = w[c] * g0;
+            v[2 * c + 1] = w[c] * g1;
+        }
+        // the cell's integer coordinates (as in cell_taps): equal cells have equal slots
+        const float r = (float)a.res[l];
+        const uint32_t cx = (uint32_t)fminf(floorf(px * r), r - 1.f), cy = (uint32_t)fminf(floorf(py * r), r - 1.f),
+                       cz = (uint32_t)fminf(floorf(pz * r), r - 1.f);
+        const uint32_t qx = __shfl_up_sync(0xffffffffu, cx, 1), qy = __shfl_up_sync(0xffffffffu, cy, 1),
+                       qz = __shfl_up_sync(0xffffffffu, cz, 1);
+        const bool head = lane == 0 || cx != qx || cy != qy || cz != qz;
+        const uint32_t heads = __ballot_sync(0xffffffffu, head);
+        float2 *tab = reinterpret_cast<float2 *>(d_theta) + (size_t)l * a.T;
+        if (heads == 0xffffffffu) {
+            if (live) add_vertex_pairs(tab, slot, v);
+            continue;
+        }
+        // segmented inclusive scan over runs of lanes in the same cell
+        const int start = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+#pragma unroll
+            for (int q = 0; q < 16; q++) {
+                const float t = __shfl_up_sync(0xffffffffu, v[q], d);
+                if (lane - d >= start) v[q] += t;
+            }
+        }
+        const bool tail = lane == 31 || ((heads >> (lane + 1)) & 1u);
+        const uint32_t run = (0xffffffffu >> (31 - lane)) & ~((1u << start) - 1u);  // lanes start .. lane
+        if (tail && (live_mask & run)) add_vertex_pairs(tab, slot, v);
+    }
+}
+
+__global__ void __launch_bounds__(kBwdThreads, 1)
 k_ngp_bwd(NgpArgs a, const float *__restrict__ theta, const float *__restrict__ X, long long n,
           const float *__restrict__ d_rgb, const float *__restrict__ d_logit_o, const float *__restrict__ d_log_s,
           const float *__restrict__ d_quat, float *__restrict__ d_theta) {
@@ -536,193 +665,195 @@ k_ngp_bwd(NgpArgs a, const float *__restrict__ theta, const float *__restrict__ 
     const int D = a.D;
     Carve cv{smem};
     const Mat W1 = cv.mat(kW1, kK1), W2 = cv.mat(kW2, kH), W3 = cv.mat(kW3, kH);
-    const Mat W1t = cv.mat(kW1, kH), W2t = cv.mat(kW2, kH), W3t = cv.mat(kW3, 16);
-    const Mat Xb = cv.mat(kBwdX, 192), Yb = cv.mat(kBwdY, 128);
+    const Mat Xb = cv.mat(kBwdX, 128), Yb = cv.mat(kBwdY, 96);
+    const Mat E[2] = {cv.mat(kBwdE, 48), cv.mat(kBwdE, 48)};
     float *bias = reinterpret_cast<float *>(cv.p);
     float *db3 = bias + 2 * kH + 16;
     uint64_t *bar = reinterpret_cast<uint64_t *>(cv.p + kBias);
     uint32_t *tslot = reinterpret_cast<uint32_t *>(cv.p + kBias + 16);
-    unsigned int *live = reinterpret_cast<unsigned int *>(cv.p + kBias + 64);  // [128]: point has a gradient
-    stage_weights(a, theta, W1, W2, W3, &W1t, &W2t, &W3t, bias);
-    for (int e = threadIdx.x; e < 16; e += kThreads) db3[e] = 0.f;
-    // Y columns 80 + 2L .. 111 stay zero, column 112 is one, 113 .. 127 zero
-    for (int e = threadIdx.x; e < kTile * 48; e += kThreads) {
-        const int r = e / 48, c = 80 + e % 48;
-        if (c >= 80 + D) put(Yb, r, c, c == 112 ? 1.f : 0.f);
+    volatile int *abort = reinterpret_cast<volatile int *>(cv.p + kBias + 32);
+    unsigned int *live = reinterpret_cast<unsigned int *>(cv.p + kBias + 64);  // [2][128]: the point has a gradient
+    stage_weights(a, theta, W1, W2, W3, bias);
+    for (int e = threadIdx.x; e < 16; e += kBwdThreads) db3[e] = 0.f;
+    if (threadIdx.x == 0) *abort = 0;
+    // constant columns: Y 80 = 1, 81..95 = 0; E 2L..31 = 0, 32 = 1, 33..47 = 0
+    for (int e = threadIdx.x; e < kTile * 16; e += kBwdThreads) put(Yb, e / 16, 80 + e % 16, e % 16 == 0 ? 1.f : 0.f);
+    for (int e = threadIdx.x; e < 2 * kTile * 48; e += kBwdThreads) {
+        const int b = e / (kTile * 48), r = (e / 48) % kTile, c = e % 48;
+        if (c >= D) put(E[b], r, c, c == 32 ? 1.f : 0.f);
     }
     Sync s{smem_addr(bar), 0u};
     init_bar(s.bar);
-    tmem_alloc(tslot, kBwdCols);
+    tmem_alloc(tslot, 512u);
+    const int warp = (int)(threadIdx.x >> 5);
+    const bool consumer = warp < kConsumers / 32;
+    const int pt = consumer ? 0 : (int)threadIdx.x - kConsumers;  // producer: its point in the tile
+    const long long tiles = (n + kTile - 1) / kTile;
+    const long long K = tiles > blockIdx.x ? (tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;  // tiles of this block
+    if (!consumer) produce_encoding(a, theta, X, n, (long long)blockIdx.x * kTile, E[0], pt);
     publish();
     fence_after_sync();
     const uint32_t tm = *tslot;
-    const Lane ln = lane_role();
-    const long long tiles = (n + kTile - 1) / kTile;
-    bool ok = true, started = false;
-    for (long long t = blockIdx.x; t < tiles; t += gridDim.x) {
-        const long long base = t * kTile;
-        const long long i = base + ln.row;
-        encode_tile(a, theta, X, n, base, Yb, 80);
-        publish();
-        if (threadIdx.x == 0) {
-            fence_after_sync();
-            mma3(tm + kB_D1, kmajor(Yb, 80), kmajor(W1, 0), kK1 / 16, idesc_bf16(128, 64, 0, 0), false);
-            mma_commit(s.bar);
-        }
-        if (!(ok = s.wait_all())) break;
-        const uint32_t mask1 = epi_relu(tm + kB_D1, ln, bias, Yb, 16);  // H1
-        publish();
-        if (threadIdx.x == 0) {
-            fence_after_sync();
-            mma3(tm + kB_D2, kmajor(Yb, 16), kmajor(W2, 0), kH / 16, idesc_bf16(128, 64, 0, 0), false);
-            mma_commit(s.bar);
-        }
-        if (!(ok = s.wait_all())) break;
-        const uint32_t mask2 = epi_relu(tm + kB_D2, ln, bias + kH, Xb, 0);  // H2
-        publish();
-        if (threadIdx.x == 0) {
-            fence_after_sync();
-            mma3(tm + kB_D3, kmajor(Xb, 0), kmajor(W3, 0), kH / 16, idesc_bf16(128, 16, 0, 0), false);
-            mma_commit(s.bar);
-        }
-        if (!(ok = s.wait_all())) break;
-        // heads: dO = dL/do (zero beyond the 11 outputs and for points beyond n)
-        if (ln.half == 0) {
-            float o[16], g[16];
-            tmem_ld16(tm + kB_D3 + ln.lane_base, o);
-#pragma unroll
-            for (int k = 0; k < 16; k++) g[k] = 0.f;
-            if (i < n) {
-                const float *b3 = bias + 2 * kH;
-#pragma unroll
-                for (int k = 0; k < 3; k++) {
-                    const float sg = sigmoidf(o[k] + b3[k]);
-                    g[k] = d_rgb[3 * i + k] * sg * (1.f - sg);
+    const Lane ln = lane_role();  // consumers: row, column half; producers: row = 32 (warp % 4) + lane
+    for (long long k = 0; k < K; k++) {
+        const long long base = ((long long)blockIdx.x + k * gridDim.x) * kTile;
+        const int eb = (int)(k & 1);
+        if (consumer) {
+            const long long i = base + ln.row;
+            const Mat &Ek = E[eb];
+            do {
+                if (threadIdx.x == 0) {
+                    fence_after_sync();
+                    mma3(tm + kB_T1, kmajor(Ek, 0), kmajor(W1, 0), kK1 / 16, idesc_bf16(128, 64, 0, 0), false);
+                    mma_commit(s.bar);
                 }
-                g[3] = d_logit_o[i];
+                if (!consumer_wait(s, abort)) break;
+                const uint32_t mask1 = epi_relu(tm + kB_T1, ln, bias, Yb, 16);  // H1
+                consumer_publish();
+                if (threadIdx.x == 0) {
+                    fence_after_sync();
+                    mma3(tm + kB_T2, kmajor(Yb, 16), kmajor(W2, 0), kH / 16, idesc_bf16(128, 64, 0, 0), false);
+                    mma_commit(s.bar);
+                }
+                if (!consumer_wait(s, abort)) break;
+                const uint32_t mask2 = epi_relu(tm + kB_T2, ln, bias + kH, Xb, 0);  // H2
+                consumer_publish();
+                if (threadIdx.x == 0) {
+                    fence_after_sync();
+                    mma3(tm + kB_T1, kmajor(Xb, 0), kmajor(W3, 0), kH / 16, idesc_bf16(128, 16, 0, 0), false);
+                    mma_commit(s.bar);
+                }
+                if (!consumer_wait(s, abort)) break;
+                // heads: dO = dL/do (zero beyond the 11 outputs and for points beyond n)
+                if (ln.half == 0) {
+                    float o[16], g[16];
+                    tmem_ld16(tm + kB_T1 + ln.lane_base, o);
 #pragma unroll
-                for (int k = 0; k < 3; k++) g[4 + k] = d_log_s[3 * i + k];
+                    for (int q = 0; q < 16; q++) g[q] = 0.f;
+                    if (i < n) {
+                        const float *b3 = bias + 2 * kH;
 #pragma unroll
-                for (int k = 0; k < 4; k++) g[7 + k] = d_quat[4 * i + k];
-            }
-            put8(Yb, ln.row, 0, g);
-            put8(Yb, ln.row, 8, g + 8);
-            bool any = false;
-#pragma unroll
-            for (int k = 0; k < kO; k++) any |= g[k] != 0.f;
-            live[ln.row] = any ? 1u : 0u;
-#pragma unroll
-            for (int k = 0; k < kO; k++) {
-                float v = g[k];
-#pragma unroll
-                for (int sft = 16; sft > 0; sft >>= 1) v += __shfl_xor_sync(0xffffffffu, v, sft);
-                if ((threadIdx.x & 31) == 0) atomicAdd(db3 + k, v);
-            }
-        }
-        publish();
-        if (threadIdx.x == 0) {
-            fence_after_sync();
-            mma3(tm + kB_DH2, kmajor(Yb, 0), kmajor(W3t, 0), 1, idesc_bf16(128, 64, 0, 0), false);
-            mma_commit(s.bar);
-        }
-        if (!(ok = s.wait_all())) break;
-        epi_mask(tm + kB_DH2, ln, mask2, Xb, 64);  // dA2
-        publish();
-        if (threadIdx.x == 0) {
-            fence_after_sync();
-            mma3(tm + kB_DH1, kmajor(Xb, 64), kmajor(W2t, 0), kH / 16, idesc_bf16(128, 64, 0, 0), false);
-            // [H2 | dA2]^T [dO | H1 | ENC | 1]
-            mma3(tm + kB_ACCA, mnmajor(Xb, 0), mnmajor(Yb, 0), kTile / 16, idesc_bf16(128, 128, 1, 1), started);
-            mma_commit(s.bar);
-        }
-        if (!(ok = s.wait_all())) break;
-        epi_mask(tm + kB_DH1, ln, mask1, Xb, 128);  // dA1
-        publish();
-        if (threadIdx.x == 0) {
-            fence_after_sync();
-            mma3(tm + kB_DENC, kmajor(Xb, 128), kmajor(W1t, 0), kH / 16, idesc_bf16(128, 32, 0, 0), false);
-            // [dA2 | dA1]^T [ENC | 1]
-            mma3(tm + kB_ACCB, mnmajor(Xb, 64), mnmajor(Yb, 80), kTile / 16, idesc_bf16(128, 48, 1, 1), started);
-            mma_commit(s.bar);
-        }
-        if (!(ok = s.wait_all())) break;
-        started = true;
-        const bool point_live = live[ln.row] != 0u;
-        // encoding gradient into the tables: this thread's levels 8 half .. 8 half + 7
-        // (a point without upstream gradient adds exact zeros: skipped)
-        {
-            float g[16];
-            tmem_ld16(tm + kB_DENC + ln.lane_base + (uint32_t)(16 * ln.half), g);
-            if (i < n && point_live) {
-                float px, py, pz;
-                unit_point(a, X, i, px, py, pz);
-#pragma unroll
-                for (int q = 0; q < 8; q++) {
-                    const int l = 8 * ln.half + q;
-                    if (l >= a.L) continue;
-                    uint32_t slot[8];
-                    float w[8];
-                    cell_taps(a, l, px, py, pz, slot, w);
-                    float2 *tab = reinterpret_cast<float2 *>(d_theta) + (size_t)l * a.T;
-                    // corners c and c + 1 differ in x only; when the first slot is
-                    // even the two entries form one aligned float4
-#pragma unroll
-                    for (int c = 0; c < 8; c += 2) {
-                        const float2 v0 = make_float2(w[c] * g[2 * q], w[c] * g[2 * q + 1]);
-                        const float2 v1 = make_float2(w[c + 1] * g[2 * q], w[c + 1] * g[2 * q + 1]);
-                        if ((slot[c] & 1u) == 0u && slot[c + 1] == slot[c] + 1u) {
-                            atomicAdd(reinterpret_cast<float4 *>(tab + slot[c]), make_float4(v0.x, v0.y, v1.x, v1.y));
-                        } else {
-                            atomicAdd(tab + slot[c], v0);
-                            atomicAdd(tab + slot[c + 1], v1);
+                        for (int q = 0; q < 3; q++) {
+                            const float sg = sigmoidf(o[q] + b3[q]);
+                            g[q] = d_rgb[3 * i + q] * sg * (1.f - sg);
                         }
+                        g[3] = d_logit_o[i];
+#pragma unroll
+                        for (int q = 0; q < 3; q++) g[4 + q] = d_log_s[3 * i + q];
+#pragma unroll
+                        for (int q = 0; q < 4; q++) g[7 + q] = d_quat[4 * i + q];
+                    }
+                    put8(Yb, ln.row, 0, g);
+                    put8(Yb, ln.row, 8, g + 8);
+                    bool any = false;
+#pragma unroll
+                    for (int q = 0; q < kO; q++) any |= g[q] != 0.f;
+                    live[eb * kTile + ln.row] = any ? 1u : 0u;
+#pragma unroll
+                    for (int q = 0; q < kO; q++) {
+                        float v = g[q];
+#pragma unroll
+                        for (int sft = 16; sft > 0; sft >>= 1) v += __shfl_xor_sync(0xffffffffu, v, sft);
+                        if ((threadIdx.x & 31) == 0) atomicAdd(db3 + q, v);
+                    }
+                }
+                consumer_publish();
+                if (threadIdx.x == 0) {
+                    fence_after_sync();
+                    // dH2 = dO W3 (W3 read MN-major as its transpose)
+                    mma3(tm + kB_T2, kmajor(Yb, 0), mnmajor(W3, 0), 1, idesc_bf16(128, 64, 0, 1), false);
+                    mma_commit(s.bar);
+                }
+                if (!consumer_wait(s, abort)) break;
+                epi_mask(tm + kB_T2, ln, mask2, Xb, 64);  // dA2
+                consumer_publish();
+                if (threadIdx.x == 0) {
+                    fence_after_sync();
+                    mma3(tm + kB_T1, kmajor(Xb, 64), mnmajor(W2, 0), kH / 16, idesc_bf16(128, 64, 0, 1), false);
+                    // [H2 | dA2]^T [dO | H1 | 1]
+                    mma3(tm + kB_ACCA, mnmajor(Xb, 0), mnmajor(Yb, 0), kTile / 16, idesc_bf16(128, 96, 1, 1), k > 0);
+                    mma_commit(s.bar);
+                }
+                if (!consumer_wait(s, abort)) break;
+                epi_mask(tm + kB_T1, ln, mask1, Xb, 0);  // dA1 replaces H2 (the product above is done)
+                consumer_publish();
+                if (threadIdx.x == 0) {
+                    fence_after_sync();
+                    mma3(tm + kB_DENC + 32u * (uint32_t)eb, kmajor(Xb, 0), mnmajor(W1, 0), kH / 16,
+                         idesc_bf16(128, 32, 0, 1), false);
+                    // [dA1 | dA2]^T [ENC | 1]
+                    mma3(tm + kB_ACCB, mnmajor(Xb, 0), mnmajor(Ek, 0), kTile / 16, idesc_bf16(128, 48, 1, 1), k > 0);
+                    mma_commit(s.bar);
+                }
+                if (!consumer_wait(s, abort)) break;
+            } while (false);
+        } else {
+            // the next tile's encoding, then the previous tile's table gradient
+            if (k + 1 < K) produce_encoding(a, theta, X, n, base + (long long)gridDim.x * kTile, E[eb ^ 1], pt);
+            if (k > 0) {
+                fence_after_sync();
+                const long long ip = base - (long long)gridDim.x * kTile + pt;
+                produce_table_grad(a, X, ip, ip < n && live[(eb ^ 1) * kTile + pt] != 0u,
+                                   tm + ln.lane_base + kB_DENC + 32u * (uint32_t)(eb ^ 1), d_theta);
+            }
+        }
+        publish();
+        fence_after_sync();
+        if (*abort) break;
+    }
+    if (*abort) {
+        if (threadIdx.x == 0) {
+            atomicOr(&g_ngp_fault, 1u);
+            mbar_wait(s.bar, s.phase);  // the MMAs still in flight, bounded
+            atomicAdd(d_theta, __int_as_float(0x7fc00000));  // poison: the gradient is incomplete
+        }
+    } else if (K > 0) {
+        if (!consumer) {
+            // the last tile's table gradient
+            const long long last = ((long long)blockIdx.x + (K - 1) * gridDim.x) * kTile;
+            const int eb = (int)((K - 1) & 1);
+            const long long ip = last + pt;
+            produce_table_grad(a, X, ip, ip < n && live[eb * kTile + pt] != 0u,
+                               tm + ln.lane_base + kB_DENC + 32u * (uint32_t)eb, d_theta);
+        } else {
+            // the block's weight gradients: this thread's row of the accumulators
+            float *g1 = d_theta + a.w1;
+            const int r = ln.row;
+            const int c_end = ln.half == 0 ? 64 : 96;
+#pragma unroll 1
+            for (int c0 = 64 * ln.half; c0 < c_end; c0 += 16) {
+                float v[16];
+                tmem_ld16(tm + kB_ACCA + ln.lane_base + (uint32_t)c0, v);
+#pragma unroll
+                for (int j = 0; j < 16; j++) {
+                    const int c = c0 + j;
+                    if (r < 64) {
+                        if (c < kO) atomicAdd(g1 + off_w3(D) + c * kH + r, v[j]);  // dW3[c][r]
+                    } else if (c >= 16 && c < 80) {
+                        atomicAdd(g1 + off_w2(D) + (r - 64) * kH + (c - 16), v[j]);  // dW2[r - 64][c - 16]
+                    } else if (c == 80) {
+                        atomicAdd(g1 + off_b2(D) + (r - 64), v[j]);  // db2[r - 64]
                     }
                 }
             }
-        }
-        fence_before_sync();
-        __syncthreads();
-    }
-    if (!ok) {
-        on_timeout(s);
-        if (threadIdx.x == 0) atomicAdd(d_theta, __int_as_float(0x7fc00000));  // poison: the gradient is incomplete
-    } else if (started) {
-        // the block's weight gradients: this thread's row of the accumulators
-        float *g1 = d_theta + a.w1;
-        const int r = ln.row;
-#pragma unroll 1
-        for (int c0 = 64 * ln.half; c0 < 64 * ln.half + 64; c0 += 16) {
-            float v[16];
-            tmem_ld16(tm + kB_ACCA + ln.lane_base + (uint32_t)c0, v);
+            if (r < 64) {  // uniform per warp (lane quarters 0 and 1)
+                float v[16];
+                tmem_ld16(tm + kB_ACCB + ln.lane_base + (uint32_t)(16 * ln.half), v);
 #pragma unroll
-            for (int j = 0; j < 16; j++) {
-                const int c = c0 + j;
-                if (r < 64) {
-                    if (c < kO) atomicAdd(g1 + off_w3(D) + c * kH + r, v[j]);  // dW3[c][r]
-                } else if (c >= 16 && c < 80) {
-                    atomicAdd(g1 + off_w2(D) + (r - 64) * kH + (c - 16), v[j]);  // dW2[r - 64][c - 16]
-                } else if (c == 112) {
-                    atomicAdd(g1 + off_b2(D) + (r - 64), v[j]);  // db2[r - 64]
+                for (int j = 0; j < 16; j++) {
+                    const int c = 16 * ln.half + j;
+                    if (c < D) atomicAdd(g1 + r * D + c, v[j]);  // dW1[r][c]
+                }
+                if (ln.half == 0) {
+                    tmem_ld16(tm + kB_ACCB + ln.lane_base + 32u, v);
+                    atomicAdd(g1 + off_b1(D) + r, v[0]);  // db1[r]
                 }
             }
         }
-        if (r >= 64) {  // uniform per warp (lane quarters 2 and 3)
-            float v[16];
-            tmem_ld16(tm + kB_ACCB + ln.lane_base + (uint32_t)(16 * ln.half), v);
-#pragma unroll
-            for (int j = 0; j < 16; j++) {
-                const int c = 16 * ln.half + j;
-                if (c < D) atomicAdd(g1 + (r - 64) * D + c, v[j]);  // dW1[r - 64][c]
-            }
-            if (ln.half == 0) {
-                tmem_ld16(tm + kB_ACCB + ln.lane_base + 32u, v);
-                atomicAdd(g1 + off_b1(D) + (r - 64), v[0]);  // db1[r - 64]
-            }
-        }
         __syncthreads();
-        for (int k = threadIdx.x; k < kO; k += kThreads) atomicAdd(g1 + off_b3(D) + k, db3[k]);
+        for (int q = threadIdx.x; q < kO; q += kBwdThreads) atomicAdd(d_theta + a.w1 + off_b3(D) + q, db3[q]);
     }
-    tmem_free(tm, kBwdCols);
+    tmem_free(tm, 512u);
 }
 
 }  // namespace
@@ -787,7 +918,7 @@ cudaError_t launch_ngp_bwd(const gs_ngp *c, const float *theta, const float *X, 
     int grid = 0;
     cudaError_t e = ngp_grid((const void *)k_ngp_bwd, bwd_smem(), n, 1, &grid);
     if (e != cudaSuccess) return e;
-    k_ngp_bwd<<<grid, kThreads, bwd_smem(), s>>>(a, theta, X, n, d_rgb, d_logit_o, d_log_s, d_quat, d_theta);
+    k_ngp_bwd<<<grid, kBwdThreads, bwd_smem(), s>>>(a, theta, X, n, d_rgb, d_logit_o, d_log_s, d_quat, d_theta);
     return cudaGetLastError();
 }
 
