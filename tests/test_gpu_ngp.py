@@ -146,3 +146,32 @@ def test_joint_calibration_through_the_hash_grid_mlp():
     st, fin = res["start"], res["final"]
     assert st["rot_deg"] > 0.9 and st["trans_cm"] > 9.0 and st["delta_ms"] > 9.0
     assert fin["rot_deg"] < 0.2 and fin["trans_cm"] < 3.0 and fin["delta_ms"] < 3.0, fin
+
+
+def test_ngp_backward_on_coherent_points():
+    """Points in scan order along a smooth curve (like a LiDAR ring): runs of
+    consecutive points share cells at the coarse levels, so the backward
+    sums them in the warp before adding to the table.  Every point has an
+    upstream gradient; the full gradient against the oracle."""
+    cfg = ngp.HashGridConfig(LO, HI, log2_table=14)
+    o, theta = _random_theta(cfg, 7)
+    mlp = ngp.HashGridMLP(cfg)
+    mlp.theta.copy_(torch.from_numpy(theta))
+    n = 2000
+    s = np.linspace(0.0, 1.0, n)
+    X = np.stack([LO[0] + 38.0 * s, LO[1] + 10.0 + 6.0 * np.sin(9.0 * s), LO[2] + 4.0 + np.cos(5.0 * s)], axis=1)
+    X = X.astype(np.float32)
+    rng = np.random.default_rng(8)
+    d = {"rgb": rng.normal(size=(n, 3)), "logit_opacity": rng.normal(size=n),
+         "log_scale": rng.normal(size=(n, 3)), "quat": rng.normal(size=(n, 4))}
+    flagged = ongp.relu_margins(o, theta.astype(np.float64), X) < RELU_FLAG
+    assert flagged.sum() <= n // 10
+    for v in d.values():
+        v[flagged] = 0.0
+    mlp.backward(torch.from_numpy(X).cuda(), {k: torch.from_numpy(v.astype(np.float32)).cuda() for k, v in d.items()})
+    got = mlp.grad.cpu().numpy()
+    ref = ongp.backward(o, theta.astype(np.float64), X, d["rgb"], d["logit_opacity"], d["log_scale"], d["quat"])
+    off = 0
+    for name, numel in cfg.blocks():
+        assert rel_l2(got[off:off + numel], ref[off:off + numel]) <= 1e-4, name
+        off += numel
