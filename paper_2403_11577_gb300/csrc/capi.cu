@@ -11,12 +11,12 @@ namespace gs {
 
 cudaError_t launch_pose_compose(const gs_batch *, const double *, const double *, const int32_t *,
                                 const double *, const double *, float *, double *, cudaStream_t);
-cudaError_t launch_pose_grad(const gs_batch *, int, const double *, double *, const double *, const double *,
-                             double *, double *, double *, bool, cudaStream_t);
+cudaError_t launch_pose_grad(const gs_batch *, int, const double *, double *, double *, const double *,
+                             const double *, double *, double *, double *, bool, cudaStream_t);
 cudaError_t launch_project(const gs_batch *, const float *, const float *, const float *, const float *,
                            const float *, const gs_opts *, uint2 *, float *, float4 *, float4 *, Stats *,
                            cudaStream_t);
-int project_bwd_blocks(const gs_batch *);
+int project_bwd_parts(const gs_batch *);
 cudaError_t launch_project_bwd(const gs_batch *, const float *, const float *, const float *, const float *,
                                const float *, const gs_opts *, const uint2 *, const float4 *, float *, float *,
                                float *, float *, double *, bool, cudaStream_t);
@@ -51,7 +51,7 @@ bool make_layout(const gs_batch *b, Layout *L) {
     L->sort_blocks = (int)std::max(1ll, std::min(st, (long long)kSortBlocksMax));
     long long rt = ((long long)R + kSortTile - 1) / kSortTile;
     L->rec_sort_blocks = (int)std::max(1ll, std::min(rt, (long long)kSortBlocksMax));
-    L->twist_blocks = std::max(1, project_bwd_blocks(b));
+    L->twist_parts = std::max(1, project_bwd_parts(b));
     L->passes = radix_passes(b->num_tiles);
     L->first_buffer = L->passes & 1;
     size_t o = 0;
@@ -75,7 +75,8 @@ bool make_layout(const gs_batch *b, Layout *L) {
     L->order = take(T * 4);
     L->emit_sums = take((size_t)std::max(1, L->emit_blocks) * 8);
     L->sort_hist = take((size_t)kRadix * (std::max(L->sort_blocks, L->rec_sort_blocks) + 1) * 4);  // counts + totals
-    L->twist_part = take(F * (size_t)L->twist_blocks * 6 * 8);
+    L->twist_part = take(F * (size_t)L->twist_parts * 6 * 8);
+    L->twist_mid = take(F * 32 * 6 * 8);  // 32 slices per frame of the twist reduction
     L->twist_frame = take(F * 6 * 8);
     L->loss_part = take((size_t)kLossBlocks * 8);
     L->photo_maps = take((size_t)b->num_pixels * 9 * 4);  // 3 SSIM maps per channel
@@ -372,7 +373,7 @@ gs_status gs_render_bwd(const gs_batch *b, const float *X, const float *quat, co
     if (e == cudaSuccess) e = prof_mark(GS_PROF_RENDER_BWD, false, S(stream));
     if (e != cudaSuccess) return GS_ERR_CUDA;
     if (b->num_gaussians == 0)
-        return cuda_status(cudaMemsetAsync(w + L.twist_part, 0, (size_t)b->num_frames * L.twist_blocks * 6 * 8,
+        return cuda_status(cudaMemsetAsync(w + L.twist_part, 0, (size_t)b->num_frames * L.twist_parts * 6 * 8,
                                            S(stream)));
     e = prof_mark(GS_PROF_PROJECT_BWD, true, S(stream));
     if (e == cudaSuccess)
@@ -388,8 +389,9 @@ gs_status gs_pose_grad(const gs_batch *b, const double *ext, void *ws, double *d
     Layout L;
     if (!batch_ok(b, ws) || !make_layout(b, &L) || !ext || !d_ext || !d_delta) return GS_ERR_INVALID_ARG;
     unsigned char *w = W(ws);
-    return cuda_status(launch_pose_grad(b, L.twist_blocks, (const double *)(w + L.twist_part),
-                                        (double *)(w + L.twist_frame), (const double *)(w + L.pose64), ext, d_ext,
+    return cuda_status(launch_pose_grad(b, L.twist_parts, (const double *)(w + L.twist_part),
+                                        (double *)(w + L.twist_mid), (double *)(w + L.twist_frame),
+                                        (const double *)(w + L.pose64), ext, d_ext,
                                         d_delta, d_xi, accumulate != 0, S(stream)));
 }
 

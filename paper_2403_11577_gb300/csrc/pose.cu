@@ -165,14 +165,19 @@ __global__ void k_pose_compose(const gs_frame *__restrict__ frames, int F, const
     for (int i = 27; i < kPose64Stride; i++) o64[i] = 0.0;
 }
 
-// One block per frame: sum the frame's per-block twist partials (FP64, fixed
-// order) into g_eps[f][6].
+// The frame's twist from its per-warp partials, in FP64 and a fixed order
+// (deterministic): block (f, s) sums slice s of the partials into mid, then
+// one thread per (frame, component) sums the slices.
+constexpr int kTwistSlices = 32;
+
 __global__ void __launch_bounds__(256)
-k_twist_reduce(int nparts, const double *__restrict__ twist_part, double *__restrict__ g_eps) {
+k_twist_reduce(int nparts, const double *__restrict__ twist_part, double *__restrict__ mid) {
     __shared__ double red[256 / 32][6];
-    const int f = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int f = blockIdx.x, sl = blockIdx.y, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int per = (nparts + kTwistSlices - 1) / kTwistSlices;
+    const int lo = min(sl * per, nparts), hi = min(lo + per, nparts);
     double g[6] = {0, 0, 0, 0, 0, 0};
-    for (int b = threadIdx.x; b < nparts; b += blockDim.x) {
+    for (int b = lo + threadIdx.x; b < hi; b += blockDim.x) {
         const double *src = twist_part + ((size_t)f * nparts + b) * 6;
         for (int i = 0; i < 6; i++) g[i] += src[i];
     }
@@ -184,8 +189,17 @@ k_twist_reduce(int nparts, const double *__restrict__ twist_part, double *__rest
     if (threadIdx.x < 6) {
         double s = 0;
         for (int w = 0; w < 256 / 32; w++) s += red[w][threadIdx.x];
-        g_eps[6 * f + threadIdx.x] = s;
+        mid[((size_t)f * kTwistSlices + sl) * 6 + threadIdx.x] = s;
     }
+}
+
+__global__ void k_twist_final(int F, const double *__restrict__ mid, double *__restrict__ g_eps) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= 6 * F) return;
+    const int f = k / 6, i = k % 6;
+    double s = 0;
+    for (int sl = 0; sl < kTwistSlices; sl++) s += mid[((size_t)f * kTwistSlices + sl) * 6 + i];
+    g_eps[k] = s;
 }
 
 // One thread per camera: sum the twists of the camera's frames and map them
@@ -232,10 +246,12 @@ cudaError_t launch_pose_compose(const gs_batch *b, const double *traj_t, const d
     return cudaGetLastError();
 }
 
-cudaError_t launch_pose_grad(const gs_batch *b, int nparts, const double *twist_part, double *g_eps,
+cudaError_t launch_pose_grad(const gs_batch *b, int nparts, const double *twist_part, double *twist_mid,
+                             double *g_eps,
                              const double *pose64, const double *ext, double *d_ext, double *d_delta,
                              double *d_xi, bool acc, cudaStream_t s) {
-    k_twist_reduce<<<b->num_frames, 256, 0, s>>>(nparts, twist_part, g_eps);
+    k_twist_reduce<<<dim3(b->num_frames, kTwistSlices), 256, 0, s>>>(nparts, twist_part, twist_mid);
+    k_twist_final<<<(6 * b->num_frames + 255) / 256, 256, 0, s>>>(b->num_frames, twist_mid, g_eps);
     const int C = b->num_cameras;
     k_pose_grad<<<(C + 31) / 32, 32, 0, s>>>(b->frames_dev, b->num_frames, C, g_eps, pose64, ext, d_ext, d_delta,
                                              d_xi, acc);

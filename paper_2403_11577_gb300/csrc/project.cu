@@ -200,9 +200,23 @@ k_project(const gs_frame *__restrict__ frames, int F, int N, const float *__rest
 
 // ---------------------------------------------------------------- backward
 
-__device__ __forceinline__ float warp_sum(float v) {
-    for (int s = 16; s > 0; s >>= 1) v += __shfl_xor_sync(0xffffffffu, v, s);
-    return v;
+// Sum of six per-lane values over the warp, transposed: the first three
+// butterfly steps halve the values each lane carries (8 slots, the last two
+// zero), the last two finish the sum.  Lane L returns the total of value
+// L / 4 (0..7).
+__device__ __forceinline__ float warp_sum6(const float (&v)[6], int lane) {
+    const float z[8] = {v[0], v[1], v[2], v[3], v[4], v[5], 0.f, 0.f};
+    const bool b16 = lane & 16, b8 = lane & 8, b4 = lane & 4;
+    float a[4];
+#pragma unroll
+    for (int i = 0; i < 4; i++) a[i] = (b16 ? z[i + 4] : z[i]) + __shfl_xor_sync(0xffffffffu, b16 ? z[i] : z[i + 4], 16);
+    float c[2];
+#pragma unroll
+    for (int i = 0; i < 2; i++) c[i] = (b8 ? a[i + 2] : a[i]) + __shfl_xor_sync(0xffffffffu, b8 ? a[i] : a[i + 2], 8);
+    float y = (b4 ? c[1] : c[0]) + __shfl_xor_sync(0xffffffffu, b4 ? c[0] : c[1], 4);
+    y += __shfl_xor_sync(0xffffffffu, y, 2);
+    y += __shfl_xor_sync(0xffffffffu, y, 1);
+    return y;
 }
 
 // Chain the per-record 2D gradients back to the Gaussian parameters (summed
@@ -219,7 +233,6 @@ k_project_bwd(const gs_frame *__restrict__ frames, int F, int N, const float *__
               const float4 *__restrict__ grad2d, float *__restrict__ d_quat, float *__restrict__ d_log_s,
               float *__restrict__ d_logit, float *__restrict__ d_col, double *__restrict__ twist_part,
               int nparts, bool acc) {
-    __shared__ double red[NT / 32][6];
     const int g = blockIdx.x * NT + threadIdx.x;
     const bool active = g < N;
     GaussParams G;
@@ -307,19 +320,14 @@ k_project_bwd(const gs_frame *__restrict__ frames, int F, int N, const float *__
                 tw[5] = (p[0] * dp[1] - p[1] * dp[0]) + (Mm[1] - Mm[3]);
             }
         }
-        // deterministic block reduction of the frame's twist: float within
-        // the warp (32 terms), double across warps and blocks (GB300's FP64
-        // rate is low, so only per-warp partials are widened)
-        for (int i = 0; i < 6; i++) tw[i] = warp_sum(tw[i]);
-        if (lane == 0)
-            for (int i = 0; i < 6; i++) red[warp][i] = (double)tw[i];
-        __syncthreads();
-        if (threadIdx.x < 6) {
-            double s = 0;
-            for (int w = 0; w < NT / 32; w++) s += red[w][threadIdx.x];
-            twist_part[((size_t)f * nparts + blockIdx.x) * 6 + threadIdx.x] = s;
-        }
-        __syncthreads();
+        // the frame's twist summed over the warp in float (32 terms, a fixed
+        // order), one FP64 partial per (frame, warp): no block barrier, so
+        // the next frame's loads overlap this one's reduction (GB300's FP64
+        // rate is low, so only the per-warp partials are widened)
+        const float tot = warp_sum6(tw, lane);
+        if ((lane & 3) == 0 && (lane >> 2) < 6)
+            twist_part[((size_t)f * nparts + (size_t)blockIdx.x * (NT / 32) + warp) * 6 + (lane >> 2)] =
+                (double)tot;
     }
     if (!active) return;
     // colour and opacity
@@ -375,6 +383,9 @@ cudaError_t launch_project(const gs_batch *b, const float *pose32, const float *
 
 int project_bwd_blocks(const gs_batch *b) { return (b->num_gaussians + kProjThreads - 1) / kProjThreads; }
 
+// Twist partials per frame: one per warp of the projection backward.
+int project_bwd_parts(const gs_batch *b) { return project_bwd_blocks(b) * (kProjThreads / 32); }
+
 cudaError_t launch_project_bwd(const gs_batch *b, const float *pose32, const float *X, const float *quat,
                                const float *log_s, const float *logit_o, const gs_opts *o, const uint2 *rect,
                                const float4 *grad2d, float *d_quat, float *d_log_s, float *d_logit,
@@ -383,7 +394,8 @@ cudaError_t launch_project_bwd(const gs_batch *b, const float *pose32, const flo
     if (nb == 0) return cudaSuccess;
     k_project_bwd<kProjThreads><<<nb, kProjThreads, 0, s>>>(b->frames_dev, b->num_frames, b->num_gaussians,
                                                            pose32, X, quat, log_s, logit_o, *o, rect, grad2d,
-                                                           d_quat, d_log_s, d_logit, d_col, twist_part, nb, acc);
+                                                           d_quat, d_log_s, d_logit, d_col, twist_part,
+                                                           nb * (kProjThreads / 32), acc);
     return cudaGetLastError();
 }
 
