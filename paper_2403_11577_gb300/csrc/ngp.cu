@@ -522,6 +522,10 @@ k_ngp_fwd(NgpArgs a, const float *__restrict__ theta, const float *__restrict__ 
 // The roles meet once per tile at a block barrier; inside the chain the
 // consumers synchronise among themselves (named barrier 1).
 constexpr int kBwdThreads = 384, kConsumers = 256;
+// Table-gradient levels the consumers add for their own tile (after the last
+// MMA round, where they would otherwise wait for the producers); the
+// producers add the rest.
+constexpr int kConsumerLevels = 4;
 constexpr int kBwdX = kTile * 128 * 2;  // [H2, later dA1 (64) | dA2 (64)]
 constexpr int kBwdY = kTile * 96 * 2;   // [dO (16) | H1 (64) | 1 (16)]
 constexpr int kBwdE = kTile * 48 * 2;   // [ENC (32) | 1 (16)], two of them
@@ -582,8 +586,8 @@ __device__ __forceinline__ void produce_encoding(const NgpArgs &a, const float *
     }
 }
 
-// Producer: the table gradient of the warp's 32 points (one per lane, in
-// input order) from their dENC rows (32 columns of tensor memory at tdenc,
+// The table gradient of levels l_begin, l_begin + l_step, .. < l_end of the
+// warp's 32 points (one per lane, in input order) from their dENC rows (32 columns of tensor memory at tdenc,
 // the warp's lane quarter).  Per level, lanes whose point lies in the same
 // cell as the previous lane's form a run (coherent inputs such as LiDAR
 // sweeps put many consecutive points in one coarse cell); a segmented scan
@@ -606,7 +610,8 @@ __device__ __forceinline__ void add_vertex_pairs(float2 *tab, const uint32_t (&s
 }
 
 __device__ __forceinline__ void produce_table_grad(const NgpArgs &a, const float *__restrict__ X, long long i,
-                                                   bool live, uint32_t tdenc, float *__restrict__ d_theta) {
+                                                   bool live, uint32_t tdenc, float *__restrict__ d_theta,
+                                                   int l_begin, int l_end, int l_step) {
     float g[32];
     tmem_ld16(tdenc, *reinterpret_cast<float(*)[16]>(g));
     tmem_ld16(tdenc + 16u, *reinterpret_cast<float(*)[16]>(g + 16));
@@ -618,6 +623,7 @@ __device__ __forceinline__ void produce_table_grad(const NgpArgs &a, const float
 #pragma unroll
     for (int l = 0; l < kMaxLevels; l++) {
         if (l >= a.L) break;
+        if (l < l_begin || l >= l_end || (l - l_begin) % l_step != 0) continue;
         uint32_t slot[8];
         float w[8];
         cell_taps(a, l, px, py, pz, slot, w);
@@ -786,6 +792,11 @@ k_ngp_bwd(NgpArgs a, const float *__restrict__ theta, const float *__restrict__ 
                     mma_commit(s.bar);
                 }
                 if (!consumer_wait(s, abort)) break;
+                // this tile's coarse levels: even ones by column half 0, odd ones by half 1
+                if (kConsumerLevels > 0)
+                    produce_table_grad(a, X, i, i < n && live[eb * kTile + ln.row] != 0u,
+                                       tm + ln.lane_base + kB_DENC + 32u * (uint32_t)eb, d_theta, ln.half,
+                                       kConsumerLevels, 2);
             } while (false);
         } else {
             // the next tile's encoding, then the previous tile's table gradient
@@ -794,7 +805,7 @@ k_ngp_bwd(NgpArgs a, const float *__restrict__ theta, const float *__restrict__ 
                 fence_after_sync();
                 const long long ip = base - (long long)gridDim.x * kTile + pt;
                 produce_table_grad(a, X, ip, ip < n && live[(eb ^ 1) * kTile + pt] != 0u,
-                                   tm + ln.lane_base + kB_DENC + 32u * (uint32_t)(eb ^ 1), d_theta);
+                                   tm + ln.lane_base + kB_DENC + 32u * (uint32_t)(eb ^ 1), d_theta, kConsumerLevels, kMaxLevels, 1);
             }
         }
         publish();
@@ -814,7 +825,7 @@ k_ngp_bwd(NgpArgs a, const float *__restrict__ theta, const float *__restrict__ 
             const int eb = (int)((K - 1) & 1);
             const long long ip = last + pt;
             produce_table_grad(a, X, ip, ip < n && live[eb * kTile + pt] != 0u,
-                               tm + ln.lane_base + kB_DENC + 32u * (uint32_t)eb, d_theta);
+                               tm + ln.lane_base + kB_DENC + 32u * (uint32_t)eb, d_theta, kConsumerLevels, kMaxLevels, 1);
         } else {
             // the block's weight gradients: this thread's row of the accumulators
             float *g1 = d_theta + a.w1;
