@@ -70,3 +70,31 @@ def test_header_documents_each_entry_point():
         # a comment block directly precedes every declaration
         m = re.search(r"\*/\s*\n(?:[^\n]*\n)?[^\n]*\b%s\s*\(" % name, text)
         assert m, name
+
+
+def test_ngp_entry_points_validate_on_the_host(lib):
+    """The hash-grid entry points check their configuration and pointers
+    before any device work: the parameter count matches the oracle's layout,
+    and bad configurations, NULL outputs and misaligned gradients are
+    rejected (the pointers below are never dereferenced)."""
+    from oracle import ngp as ongp
+    from paper_2403_11577_gb300 import ngp
+    cfg = ngp.HashGridConfig([-10.0, -8.0, -1.0], [30.0, 12.0, 9.0], levels=6, log2_table=12)
+    o = ongp.NgpConfig(cfg.aabb_min, cfg.aabb_max, levels=6, log2_table=12)
+    assert capi.gs_ngp_param_count(cfg.c()) == o.count()
+    bad = cfg.c()
+    bad.levels = 17
+    assert capi.gs_ngp_param_count(bad) == -1
+    bad = cfg.c()
+    bad.aabb_max[0] = bad.aabb_min[0]  # empty box
+    assert capi.gs_ngp_param_count(bad) == -1
+    p = C.c_void_p
+    ok16, ok8 = p(0x10000), p(0x10008)
+    args = [p(0x20000)] * 4
+    assert lib.gs_ngp_backward(C.byref(cfg.c()), ok16, ok16, C.c_int64(5), *args, ok8, None) == \
+        capi.GS_ERR_INVALID_ARG  # d_theta only 8-byte aligned
+    assert lib.gs_ngp_backward(C.byref(bad), ok16, ok16, C.c_int64(5), *args, ok16, None) == capi.GS_ERR_INVALID_ARG
+    assert lib.gs_ngp_forward(C.byref(cfg.c()), ok16, ok16, C.c_int64(5), None, *args[:3], None) == \
+        capi.GS_ERR_INVALID_ARG  # NULL rgb
+    assert lib.gs_ngp_forward(C.byref(cfg.c()), ok16, ok16, C.c_int64(-1), *args, None) == capi.GS_ERR_INVALID_ARG
+    assert lib.gs_ngp_fault(None) == capi.GS_ERR_INVALID_ARG
