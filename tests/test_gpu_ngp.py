@@ -5,7 +5,7 @@ import pytest
 import torch
 
 from oracle import ngp as ongp
-from paper_2403_11577_gb300 import ngp, scenes
+from paper_2403_11577_gb300 import capi, ngp, scenes
 
 from _util import ensure_built, rel_l2
 
@@ -129,6 +129,7 @@ def test_ngp_on_the_accumulated_cloud():
     for name, numel in cfg.blocks():
         assert rel_l2(got[off:off + numel], ref_g[off:off + numel]) <= 1e-4, name
         off += numel
+    assert capi.gs_ngp_fault() == 0  # no tensor-core wait ran out
 
 
 def test_joint_calibration_through_the_hash_grid_mlp():
