@@ -456,6 +456,57 @@ def test_render_bwd_lidar_frame_sparse_pixels():
     assert rel_l2(g["delta"].cpu().numpy(), og["delta"]) <= GRAD_TOL
 
 
+def test_bench_workload_sampled_forward_and_backward():
+    """The benchmark's workload and launch configuration: 1M LiDAR-anchored
+    Gaussians, eight 1408x376 frames in one batched launch per stage, tile 16,
+    batch 64.  Forward: 80 sampled pixels per frame against the oracle.
+    Backward: dL/dC non-zero on those pixels only, so the oracle's backward
+    over them, summed over the frames, is the exact reference for every
+    gradient (Gaussian attributes, extrinsic, time offset)."""
+    p = scenes.batched_problem(n=1_000_000)
+    opts = render.RenderOptions(tile=16, batch=64)
+    scene, plan, ext, dl = setup(p, opts)
+    plan.forward(scene, ext, dl)
+    st = plan.stats()
+    assert st.status == 0 and st.num_pairs > 30_000_000
+    rng = np.random.default_rng(11)
+    dL = torch.zeros_like(plan.rgb)
+    ref = {k: 0.0 for k in ("quat", "log_scale", "logit_opacity", "rgb", "ext", "delta")}
+    for fi, f in enumerate(p.frames):
+        cam = f.camera
+        pix = np.unique(sample_pixels(rng, cam, 80), axis=0)
+        sc, e, d = p.scenes[f.scene_id], p.ext[f.camera_id], float(p.delta[f.camera_id])
+        rgb_o, T_o, last_o, flags = oracle.render(sc, f, e, d, oracle_opts(opts), pix)
+        # with hundreds of contributors per pixel, a fifth of the pixels have
+        # one whose alpha lies within the flag margin of a threshold
+        ok = flags == 0
+        assert ok.mean() >= 0.5, (~ok).sum()
+        idx = pix[:, 1] * cam.width + pix[:, 0]
+        rgb_g = plan.image(plan.rgb, fi).cpu().numpy().reshape(-1, 3)[idx]
+        T_g = plan.image(plan.T, fi).cpu().numpy().reshape(-1)[idx]
+        gid = last_gaussian_ids(plan, fi)[idx]
+        assert np.abs(rgb_g[ok] - rgb_o[ok]).max() <= COLOUR_TOL
+        assert np.abs(T_g[ok] - T_o[ok]).max() <= COLOUR_TOL
+        np.testing.assert_array_equal(gid[ok], last_o[ok])
+        pix = pix[ok]
+        Wp = rng.normal(size=(len(pix), 3))
+        W = np.zeros((cam.height * cam.width, 3))
+        W[pix[:, 1] * cam.width + pix[:, 0]] = Wp
+        plan.image(dL, fi).copy_(torch.from_numpy(W.astype(np.float32)).view(plan.image(dL, fi).shape))
+        og = oracle.backward(p.scenes[f.scene_id], f, p.ext[f.camera_id], float(p.delta[f.camera_id]), Wp,
+                             oracle_opts(opts), pixels=pix)
+        for k in ref:
+            ref[k] = ref[k] + np.asarray(og[k], np.float64)
+    g = render.empty_grads(scene, p.num_cameras)
+    plan.backward(scene, dL, g, ext)
+    for k in ("quat", "log_scale", "logit_opacity", "rgb"):
+        assert rel_l2(g[k].cpu().numpy(), ref[k]) <= GRAD_TOL, k
+    ge = g["ext"].cpu().numpy()[0]
+    assert rel_l2(ge[:3], ref["ext"][:3]) <= GRAD_TOL
+    assert rel_l2(ge[3:], ref["ext"][3:]) <= GRAD_TOL
+    assert rel_l2(g["delta"].cpu().numpy(), ref["delta"]) <= GRAD_TOL
+
+
 def test_render_bwd_uneven_batch():
     p = scenes.uneven_problem(sizes=(2000, 6000, 3000), frames_per_scene=2,
                               cams=(scenes.Camera(176, 47, 69.0, 69.0, 85.0, 30.0),
