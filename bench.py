@@ -458,10 +458,12 @@ def run_ours(args, world, rank, local):
         nrec = plan.batch.num_records
         tpass = max(1, (int(plan.batch.num_tiles - 1).bit_length() + 7) // 8)
         # bin_sort: record keys (20 B) and 4 depth passes (20 B each), pair
-        # count (12 B) and emission (16 B) per record; per pair the emitted
-        # key/value (8 B), the tile passes (20 B each) and the range scan (4 B)
+        # count (12 B) and emission (16 B) per record, each also reading the
+        # 32 B splat record with exact tiles; per pair the emitted key/value
+        # (8 B), the tile passes (20 B each) and the range scan (4 B)
         nbytes = {1: 44 * scene.n + nrec * (8 + 4 + 32 + 48),
-                  2: nrec * (20 + 4 * 20 + 12 + 16) + st.num_pairs * (8 + 20 * tpass + 4),
+                  2: nrec * (20 + 4 * 20 + 12 + 16 + (64 if opts.exact_tiles else 0))
+                  + st.num_pairs * (8 + 20 * tpass + 4),
                   5: 44 * scene.n + nrec * (8 + 48) + 44 * scene.n}[dom]
         achieved = nbytes / (dom_ms / 1e3) / 1e9
         peak = peaks.get("hbm_gbs", 6800.0)

@@ -110,6 +110,12 @@ typedef struct {
                          clamped to the field of view widened by this
                          fraction of the image size per side (0.15, 3DGS's
                          1.3x half field of view); negative = no clamp */
+    int32_t exact_tiles; /* 1: gs_bin_sort lists a record only for the tiles
+                         of its rectangle that its alpha >= alpha_min
+                         ellipse can meet (row by row, with a margin), read
+                         from the projection's splat records; the image is
+                         the same as with whole rectangles, with fewer pairs.
+                         0: whole rectangles (needs only rect and depth) */
 } gs_opts;
 
 /* A batch of frames planned by gs_batch_init. */
@@ -394,6 +400,8 @@ gs_status gs_voxel_downsample(const float *X, int64_t n, float voxel, int32_t *o
  * acceptable.  Such a caller cannot provide the workspace gs_bin_sort needs.
  * The paper has no counterpart; it is a deployment convenience.
  *
+ * It bins whole rectangles (the caller passes rect and depth, not the
+ * splat records): opts->exact_tiles must be 0, else GS_ERR_UNSUPPORTED.
  * vals and ranges are the same as gs_bin_sort's, bit for bit, and keys are
  * the full 64-bit keys (global tile << 32 | float bits of the depth) whose
  * high halves are gs_bin_sort's workspace keys; the inputs and outputs are
@@ -416,7 +424,7 @@ gs_status gs_voxel_downsample(const float *X, int64_t n, float voxel, int32_t *o
  * before any stream capture.  All calls share the one array and it keeps
  * the last call's contents: calls that overlap on the GPU (different
  * streams, or different host threads) race and corrupt each other.
- * Errors: GS_ERR_INVALID_ARG, GS_ERR_CAPACITY, GS_ERR_CUDA. */
+ * Errors: GS_ERR_INVALID_ARG, GS_ERR_UNSUPPORTED, GS_ERR_CAPACITY, GS_ERR_CUDA. */
 gs_status gs_bin_sort_noalloc(const gs_batch *batch, const gs_opts *opts, const uint32_t *rect,
                               const float *depth, uint64_t *keys, uint32_t *vals, uint32_t *ranges,
                               uint64_t *out_pairs, void *stream);

@@ -28,7 +28,8 @@ class GsFrame(C.Structure):
 class GsOpts(C.Structure):
     _fields_ = [("near_z", C.c_float), ("lowpass", C.c_float), ("alpha_min", C.c_float),
                 ("alpha_max", C.c_float), ("t_min", C.c_float), ("scale_max", C.c_float),
-                ("bg", C.c_float * 3), ("tile", C.c_int32), ("batch", C.c_int32), ("frustum_margin", C.c_float)]
+                ("bg", C.c_float * 3), ("tile", C.c_int32), ("batch", C.c_int32), ("frustum_margin", C.c_float),
+                ("exact_tiles", C.c_int32)]
 
 
 class GsBatch(C.Structure):

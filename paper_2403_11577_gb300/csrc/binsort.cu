@@ -120,6 +120,235 @@ k_pair_scan(unsigned long long *__restrict__ sums, int nb, long long capacity, S
     }
 }
 
+// ---------------------------------------------------- exact tile binning
+//
+// With exact tiles a record is listed only for the tiles of its rectangle
+// that its ellipse P(d) <= F - lmin (P = -(A dx^2 + B dx dy + C dy^2), the
+// splat's base-2 exponent) can meet: in every tile row the pixel centres
+// where a Gaussian reaches alpha_min lie between the x-extremes of the
+// ellipse within the row's y-range, a contiguous run of tiles.  The test
+// uses the ellipse enlarged by 2^-8 |F - lmin| + 2^-14 M (M bounds P's
+// terms over the whole rectangle), four times the margins of the render's
+// band culling, and widens each run by 0.02 px + 2^-10 of its offsets, so
+// every band the render would keep lies in a listed tile: the image is the
+// same, bit for bit, as with whole rectangles.  A degenerate or non-finite
+// ellipse keeps whole rows.
+struct RowSpanner {
+    float mx, my, qb, lim4a, D, ymax, yR, inv2a, full;  // full != 0: whole rows
+};
+
+// The span arithmetic is written with explicitly rounded operations (no
+// contraction into fused multiply-adds), so that the pair count and the
+// emission, separate kernels, compute every span bit for bit alike.
+__device__ __forceinline__ float mul_(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float add_(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float sub_(float a, float b) { return __fsub_rn(a, b); }
+
+__device__ __forceinline__ RowSpanner make_spanner(float4 s0, float4 s1, float lmin, uint2 rc, const gs_frame &fr,
+                                                   int T) {
+    RowSpanner s;
+    s.mx = s0.x;
+    s.my = s0.y;
+    const float qa = -s0.z, qb = -s0.w, qc = -s1.x;
+    s.qb = qb;
+    const float lim0 = sub_(s1.y, lmin);
+    const float x0 = (float)((rc.x & 0xffffu) * (uint32_t)T), x1 = (float)((rc.y & 0xffffu) * (uint32_t)T + T - 1);
+    const float y0 = (float)(fr.row0 + (int)(rc.x >> 16) * T), y1 = (float)(fr.row0 + (int)(rc.y >> 16) * T + T - 1);
+    const float Rx = fmaxf(fabsf(sub_(x0, s.mx)), fabsf(sub_(x1, s.mx)));
+    const float Ry = fmaxf(fabsf(sub_(y0, s.my)), fabsf(sub_(y1, s.my)));
+    const float M = add_(add_(mul_(mul_(qa, Rx), Rx), mul_(mul_(fabsf(qb), Rx), Ry)), mul_(mul_(qc, Ry), Ry));
+    const float lim = add_(add_(lim0, mul_(fabsf(lim0), 0x1p-8f)), mul_(M, 0x1p-14f));
+    s.D = sub_(mul_(mul_(4.f, qa), qc), mul_(qb, qb));
+    const bool ok = qa > 0.f && qc > 0.f && s.D > 0.f && lim > 0.f && isfinite(lim) && isfinite(s.D) &&
+                    isfinite(s.mx) && isfinite(s.my) && isfinite(qb);
+    s.full = ok ? 0.f : 1.f;
+    s.lim4a = mul_(mul_(4.f, qa), lim);
+    s.inv2a = __fdiv_rn(1.f, mul_(2.f, qa));
+    // largest |y| on the ellipse (widened), and the y of its rightmost point
+    // (the leftmost is at -yR)
+    s.ymax = ok ? add_(mul_(__fsqrt_rn(__fdiv_rn(s.lim4a, s.D)), 1.f + 0x1p-12f), 1e-3f) : 0.f;
+    const float xm = ok ? __fsqrt_rn(__fdiv_rn(mul_(mul_(4.f, qc), lim), s.D)) : 0.f;
+    s.yR = ok ? __fdiv_rn(mul_(-qb, xm), mul_(2.f, qc)) : 0.f;
+    return s;
+}
+
+// Tile columns [lo, hi] of tile row ty within the rectangle's columns
+// [rx0, rx1] (lo > hi: none).
+__device__ __forceinline__ void row_span(const RowSpanner &s, int ty, int rx0, int rx1, const gs_frame &fr, int T,
+                                         int &lo, int &hi) {
+    lo = rx0;
+    hi = rx1;
+    if (s.full != 0.f) return;
+    const float ylo = (float)(fr.row0 + ty * T), yhi = (float)min(fr.row0 + ty * T + T - 1, fr.height - 1);
+    const float a = fmaxf(sub_(ylo, s.my), -s.ymax), b = fminf(sub_(yhi, s.my), s.ymax);
+    if (a > b) {
+        lo = 1;
+        hi = 0;
+        return;
+    }
+    // the x-extremes over y in [a, b]: x+(y) is concave, largest at the
+    // clamped y of the rightmost point; x-(y) is its mirror
+    const float yr = fminf(fmaxf(s.yR, a), b), yl = fminf(fmaxf(-s.yR, a), b);
+    const float rr = __fsqrt_rn(fmaxf(0.f, sub_(s.lim4a, mul_(mul_(s.D, yr), yr))));
+    const float rl = __fsqrt_rn(fmaxf(0.f, sub_(s.lim4a, mul_(mul_(s.D, yl), yl))));
+    const float Xb = mul_(add_(mul_(-s.qb, yr), rr), s.inv2a);
+    const float Xa = mul_(sub_(mul_(-s.qb, yl), rl), s.inv2a);
+    const float w = add_(add_(0.02f, mul_(0x1p-10f, add_(fabsf(Xa), fabsf(Xb)))), mul_(0x1p-12f, fabsf(s.mx)));
+    const float xa = fminf(fmaxf(sub_(add_(s.mx, Xa), w), -1e9f), 1e9f);
+    const float xb = fminf(fmaxf(add_(add_(s.mx, Xb), w), -1e9f), 1e9f);
+    lo = max(rx0, (int)floorf(__fdiv_rn(xa, (float)T)));
+    hi = min(rx1, (int)floorf(__fdiv_rn(xb, (float)T)));
+}
+
+// Pairs of each emission block with exact tiles (as k_pair_count); also
+// each record's pairs and non-empty rows, by sorted position, for the
+// emission.
+__global__ void __launch_bounds__(kEmitThreads)
+k_pair_count_exact(const gs_frame *__restrict__ frames, int F, int T, float lmin, const uint2 *__restrict__ rect,
+                   const float4 *__restrict__ splat, long long R, const uint32_t *__restrict__ perm,
+                   unsigned long long *__restrict__ sums, uint2 *__restrict__ rec_pairs) {
+    __shared__ unsigned long long sh[kEmitThreads / 32];
+    const long long base = (long long)blockIdx.x * kEmitItems;
+    unsigned long long c = 0;
+    for (int i = threadIdx.x; i < kEmitItems; i += kEmitThreads) {
+        const long long p = base + i;
+        if (p >= R) continue;
+        const long long r = (long long)perm[p];
+        const uint2 rc = rect[r];
+        uint32_t np = 0, ns = 0;  // pairs and non-empty rows of the record
+        if (rect_count(rc) != 0u) {
+            const gs_frame &fr = frames[frame_of_record(frames, F, r)];
+            const RowSpanner sp = make_spanner(splat[2 * r], splat[2 * r + 1], lmin, rc, fr, T);
+            const int rx0 = (int)(rc.x & 0xffffu), rx1 = (int)(rc.y & 0xffffu);
+            for (int ty = (int)(rc.x >> 16); ty <= (int)(rc.y >> 16); ty++) {
+                int lo, hi;
+                row_span(sp, ty, rx0, rx1, fr, T, lo, hi);
+                if (hi >= lo) {
+                    np += (uint32_t)(hi - lo + 1);
+                    ns++;
+                }
+            }
+        }
+        rec_pairs[p] = make_uint2(np, ns);
+        c += np;
+    }
+    const unsigned long long t = block_sum_u64<kEmitThreads>(c, sh);
+    if (threadIdx.x == 0) sums[blockIdx.x] = t;
+}
+
+// Emission with exact tiles (as k_pair_emit<uint32_t>).  A record's pairs
+// are its rows' runs of tiles, each a segment (first pair, length, first
+// tile, value); the block's segments are staged in shared memory in windows
+// of kSegWindow, and each output pair finds its segment by binary search.
+constexpr int kSegWindow = 4096;
+
+struct Segment {
+    uint32_t off, len, tile0, val;  // off: first pair, relative to the block's first
+};
+
+struct EmitExactSmem {
+    Segment seg[kSegWindow];
+    unsigned long long wsum[kEmitThreads / 32];
+    uint32_t ssum[kEmitThreads / 32];
+    uint32_t nseg;
+};
+
+__global__ void __launch_bounds__(kEmitThreads)
+k_pair_emit_exact(const gs_frame *__restrict__ frames, int F, int T, float lmin, const uint2 *__restrict__ rect,
+                  const float4 *__restrict__ splat, long long R, const uint32_t *__restrict__ perm,
+                  const unsigned long long *__restrict__ sums, const uint2 *__restrict__ rec_pairs,
+                  const Stats *__restrict__ stats, uint32_t *__restrict__ keys, uint32_t *__restrict__ vals) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    EmitExactSmem &S = *reinterpret_cast<EmitExactSmem *>(smem_raw);
+    if (stats->num_pairs == 0) return;  // nothing to emit, or overflow
+    const long long base = (long long)blockIdx.x * kEmitItems;
+    constexpr int PER = kEmitItems / kEmitThreads;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // this thread's records: pairs and non-empty rows (from the count)
+    unsigned long long npairs = 0;
+    uint32_t nsegs = 0;
+    for (int j = 0; j < PER; j++) {
+        const long long p = base + threadIdx.x * PER + j;
+        if (p >= R) continue;
+        const uint2 c = rec_pairs[p];
+        npairs += c.x;
+        nsegs += c.y;
+    }
+    // exclusive prefixes of pairs and segments over the block's threads
+    unsigned long long pin = npairs;
+    uint32_t sin = nsegs;
+    for (int sft = 1; sft < 32; sft <<= 1) {
+        const unsigned long long v = __shfl_up_sync(0xffffffffu, pin, sft);
+        const uint32_t u = __shfl_up_sync(0xffffffffu, sin, sft);
+        if (lane >= sft) {
+            pin += v;
+            sin += u;
+        }
+    }
+    if (lane == 31) {
+        S.wsum[warp] = pin;
+        S.ssum[warp] = sin;
+    }
+    __syncthreads();
+    unsigned long long pre_p = 0;
+    uint32_t pre_s = 0;
+    for (int w = 0; w < warp; w++) {
+        pre_p += S.wsum[w];
+        pre_s += S.ssum[w];
+    }
+    const unsigned long long my_p = pre_p + pin - npairs;  // first pair of this thread's records
+    const uint32_t my_s = pre_s + sin - nsegs;             // and first segment
+    if (threadIdx.x == kEmitThreads - 1) S.nseg = pre_s + sin;
+    __syncthreads();
+    const uint32_t nseg_all = S.nseg;
+    const unsigned long long gbase = sums[blockIdx.x], npairs_all = stats->num_pairs;
+    for (uint32_t w0 = 0; w0 < nseg_all; w0 += kSegWindow) {
+        const uint32_t w1 = min(nseg_all, w0 + (uint32_t)kSegWindow);
+        // the owners write their segments that fall in [w0, w1)
+        if (nsegs > 0 && my_s < w1 && my_s + nsegs > w0) {
+            unsigned long long po = my_p;
+            uint32_t si = my_s;
+            for (int j = 0; j < PER && si < w1; j++) {
+                const long long p = base + threadIdx.x * PER + j;
+                if (p >= R || rec_pairs[p].y == 0u) continue;
+                const long long r = (long long)perm[p];
+                const uint2 rc = rect[r];
+                const gs_frame &fr = frames[frame_of_record(frames, F, r)];
+                const RowSpanner sp = make_spanner(splat[2 * r], splat[2 * r + 1], lmin, rc, fr, T);
+                const int rx0 = (int)(rc.x & 0xffffu), rx1 = (int)(rc.y & 0xffffu);
+                const uint32_t val = (uint32_t)(r - fr.record_offset);
+                for (int ty = (int)(rc.x >> 16); ty <= (int)(rc.y >> 16) && si < w1; ty++) {
+                    int a, b;
+                    row_span(sp, ty, rx0, rx1, fr, T, a, b);
+                    if (b < a) continue;
+                    if (si >= w0)
+                        S.seg[si - w0] = {(uint32_t)po, (uint32_t)(b - a + 1),
+                                          (uint32_t)fr.tile_offset + (uint32_t)ty * (uint32_t)fr.tiles_x + (uint32_t)a,
+                                          val};
+                    po += (unsigned long long)(b - a + 1);
+                    si++;
+                }
+            }
+        }
+        __syncthreads();
+        const uint32_t n = w1 - w0;
+        const uint32_t o_lo = S.seg[0].off, o_hi = S.seg[n - 1].off + S.seg[n - 1].len;
+        for (uint32_t o = o_lo + threadIdx.x; o < o_hi; o += kEmitThreads) {
+            int lo = 0, hi = (int)n - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (S.seg[mid].off <= o) lo = mid; else hi = mid - 1;
+            }
+            const Segment sg = S.seg[lo];
+            if (gbase + o < npairs_all) {  // always true when the count agrees (same arithmetic)
+                keys[gbase + o] = sg.tile0 + (o - sg.off);
+                vals[gbase + o] = sg.val;
+            }
+        }
+        __syncthreads();
+    }
+}
+
 // Key of a pair: the global tile (K = uint32_t, pairs emitted in depth order)
 // or (global tile << 32) | depth bits (K = unsigned long long, full key).
 template <typename K>
@@ -473,8 +702,12 @@ cudaError_t scatter_smem_attr() {
 
 }  // namespace
 
-cudaError_t launch_bin_sort(const gs_batch *b, const Layout &L, unsigned char *ws, cudaStream_t s, int sms) {
+cudaError_t launch_bin_sort(const gs_batch *b, const gs_opts *o, const Layout &L, unsigned char *ws, cudaStream_t s,
+                            int sms) {
     (void)sms;
+    const bool exact = o->exact_tiles != 0;
+    const float lmin = log2f(o->alpha_min);
+    const float4 *splat = reinterpret_cast<const float4 *>(ws + L.splat);
     Stats *stats = reinterpret_cast<Stats *>(ws + L.stats);
     const uint2 *rect = reinterpret_cast<const uint2 *>(ws + L.rect);
     const float *depth = reinterpret_cast<const float *>(ws + L.depth);
@@ -489,6 +722,9 @@ cudaError_t launch_bin_sort(const gs_batch *b, const Layout &L, unsigned char *w
     uint2 *ranges = reinterpret_cast<uint2 *>(ws + L.ranges);
     const long long R = b->num_records;
     cudaError_t e = scatter_smem_attr<uint32_t>();
+    if (e == cudaSuccess && exact)
+        e = cudaFuncSetAttribute(k_pair_emit_exact, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sizeof(EmitExactSmem));
     if (e != cudaSuccess) return e;
     if (L.emit_blocks > 0) {
         // stage 1: stable depth order of the records (4 passes, ends in buffer 0)
@@ -497,12 +733,22 @@ cudaError_t launch_bin_sort(const gs_batch *b, const Layout &L, unsigned char *w
             e = radix_pass(rkeys[p & 1], rvals[p & 1], rkeys[(p + 1) & 1], rvals[(p + 1) & 1], &stats->num_records,
                            8 * p, L.rec_sort_blocks, hist, s);
         if (e != cudaSuccess) return e;
-        // stage 2: pairs emitted in that order
-        k_pair_count<<<L.emit_blocks, kEmitThreads, 0, s>>>(rect, R, rvals[0], sums);
-        k_pair_scan<<<1, 1024, 0, s>>>(sums, L.emit_blocks, b->pair_capacity, stats);
-        k_pair_emit<uint32_t><<<L.emit_blocks, kEmitThreads, 0, s>>>(b->frames_dev, b->num_frames, rect, depth, R,
-                                                                     rvals[0], sums, stats, keys[L.first_buffer],
-                                                                     vals[L.first_buffer]);
+        // stage 2: pairs emitted in that order (exact tiles or whole rectangles)
+        if (exact) {
+            uint2 *rec_pairs = reinterpret_cast<uint2 *>(ws + L.rec_pairs);
+            k_pair_count_exact<<<L.emit_blocks, kEmitThreads, 0, s>>>(b->frames_dev, b->num_frames, b->tile, lmin,
+                                                                      rect, splat, R, rvals[0], sums, rec_pairs);
+            k_pair_scan<<<1, 1024, 0, s>>>(sums, L.emit_blocks, b->pair_capacity, stats);
+            k_pair_emit_exact<<<L.emit_blocks, kEmitThreads, sizeof(EmitExactSmem), s>>>(
+                b->frames_dev, b->num_frames, b->tile, lmin, rect, splat, R, rvals[0], sums, rec_pairs, stats,
+                keys[L.first_buffer], vals[L.first_buffer]);
+        } else {
+            k_pair_count<<<L.emit_blocks, kEmitThreads, 0, s>>>(rect, R, rvals[0], sums);
+            k_pair_scan<<<1, 1024, 0, s>>>(sums, L.emit_blocks, b->pair_capacity, stats);
+            k_pair_emit<uint32_t><<<L.emit_blocks, kEmitThreads, 0, s>>>(b->frames_dev, b->num_frames, rect, depth,
+                                                                         R, rvals[0], sums, stats,
+                                                                         keys[L.first_buffer], vals[L.first_buffer]);
+        }
     } else {
         e = cudaMemsetAsync(&stats->num_pairs, 0, sizeof(unsigned long long), s);
     }
@@ -714,6 +960,7 @@ extern "C" gs_status gs_bin_sort_noalloc(const gs_batch *b, const gs_opts *o, co
     if (!b || !o || !b->frames_dev || b->num_frames <= 0 || b->num_tiles <= 0 || o->tile != b->tile || !keys ||
         !vals || !ranges || !out_pairs || (b->num_records > 0 && (!rect || !depth)))
         return GS_ERR_INVALID_ARG;
+    if (o->exact_tiles != 0) return GS_ERR_UNSUPPORTED;  // only rectangles are passed in
     if (b->pair_capacity > kNoAllocMaxPairs || b->num_records > kNoAllocMaxRecords) return GS_ERR_CAPACITY;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     NoAllocScratch *sc = nullptr;

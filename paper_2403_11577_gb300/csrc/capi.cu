@@ -20,7 +20,7 @@ int project_bwd_parts(const gs_batch *);
 cudaError_t launch_project_bwd(const gs_batch *, const float *, const float *, const float *, const float *,
                                const float *, const gs_opts *, const uint2 *, const float4 *, float *, float *,
                                float *, float *, double *, bool, cudaStream_t);
-cudaError_t launch_bin_sort(const gs_batch *, const Layout &, unsigned char *, cudaStream_t, int);
+cudaError_t launch_bin_sort(const gs_batch *, const gs_opts *, const Layout &, unsigned char *, cudaStream_t, int);
 cudaError_t launch_render_fwd(const gs_batch *, const gs_opts *, const uint32_t *, const uint2 *, const uint32_t *,
                               const float4 *, const float *, Stats *, float *, float *, int32_t *, cudaStream_t);
 cudaError_t launch_render_bwd(const gs_batch *, const gs_opts *, const uint32_t *, const uint2 *, const uint32_t *,
@@ -74,6 +74,7 @@ bool make_layout(const gs_batch *b, Layout *L) {
     L->ranges = take(T * 8);
     L->order = take(T * 4);
     L->emit_sums = take((size_t)std::max(1, L->emit_blocks) * 8);
+    L->rec_pairs = take(R * 8);  // exact tiles: pairs and non-empty rows per sorted record
     L->sort_hist = take((size_t)kRadix * (std::max(L->sort_blocks, L->rec_sort_blocks) + 1) * 4);  // counts + totals
     L->twist_part = take(F * (size_t)L->twist_parts * 6 * 8);
     L->twist_mid = take(F * 32 * 6 * 8);  // 32 slices per frame of the twist reduction
@@ -103,6 +104,7 @@ bool opts_ok(const gs_batch *b, const gs_opts *o) {
     if (!(o->batch == 64 || o->batch == 128 || o->batch == 256)) return false;
     if (!(o->alpha_min > 0.f) || !(o->alpha_max > o->alpha_min) || !(o->alpha_max < 1.f)) return false;
     if (!(o->t_min >= 0.f) || !(o->near_z > 0.f) || !(o->lowpass >= 0.f) || !(o->scale_max > 0.f)) return false;
+    if (o->exact_tiles != 0 && o->exact_tiles != 1) return false;
     return true;
 }
 
@@ -257,7 +259,7 @@ gs_status gs_bin_sort(const gs_batch *b, const gs_opts *o, void *ws, void *strea
     Layout L;
     if (!batch_ok(b, ws) || !opts_ok(b, o) || !make_layout(b, &L)) return GS_ERR_INVALID_ARG;
     cudaError_t e = prof_mark(GS_PROF_BIN_SORT, true, S(stream));
-    if (e == cudaSuccess) e = launch_bin_sort(b, L, W(ws), S(stream), 0);
+    if (e == cudaSuccess) e = launch_bin_sort(b, o, L, W(ws), S(stream), 0);
     if (e == cudaSuccess) e = prof_mark(GS_PROF_BIN_SORT, false, S(stream));
     return cuda_status(e);
 }

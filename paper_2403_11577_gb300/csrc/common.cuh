@@ -37,7 +37,7 @@ struct Stats {
 
 struct Layout {
     size_t stats, pose32, pose64, rect, depth, splat, grad2d, keys[2], vals[2], rec_keys[2], rec_vals[2], ranges,
-        order, emit_sums, sort_hist, twist_part, twist_mid, twist_frame, loss_part, photo_maps, photo_part, total;
+        order, emit_sums, rec_pairs, sort_hist, twist_part, twist_mid, twist_frame, loss_part, photo_maps, photo_part, total;
     int emit_blocks;     // blocks of the pair count / emit kernels
     int sort_blocks;     // blocks of the radix passes over pairs
     int rec_sort_blocks; // blocks of the radix passes over records

@@ -30,6 +30,7 @@ class RenderOptions:
     tile: int = 16
     batch: int = 64
     frustum_margin: float = 0.15
+    exact_tiles: bool = True  # bin each Gaussian only to the tiles its ellipse meets
 
     def c(self) -> capi.GsOpts:
         o = capi.GsOpts()
@@ -37,6 +38,7 @@ class RenderOptions:
         o.alpha_max, o.t_min, o.scale_max = self.alpha_max, self.t_min, self.scale_max
         o.bg = (C.c_float * 3)(*self.bg)
         o.tile, o.batch, o.frustum_margin = self.tile, self.batch, self.frustum_margin
+        o.exact_tiles = int(bool(self.exact_tiles))
         return o
 
 

@@ -125,7 +125,8 @@ def _write_records(plan, rect, depth):
 def _bin_plan(frames_wh, counts, tile=16, cap=None):
     frames = [dict(width=w, height=h, fx=100.0, fy=100.0, cx=w / 2, cy=h / 2, camera_id=0, traj_id=0,
                    gauss_offset=0, gauss_count=c, timestamp=0.0) for (w, h), c in zip(frames_wh, counts)]
-    opts = render.RenderOptions(tile=tile)
+    # synthetic records are rectangles and depths only (no splat): whole-rectangle binning
+    opts = render.RenderOptions(tile=tile, exact_tiles=False)
     return render.Plan(frames, max(counts), 1, 1, opts, cap if cap is not None else 4_000_000)
 
 
@@ -310,6 +311,70 @@ def test_crop_is_the_bottom_of_the_full_render(row0):
     assert np.abs(got[ok] - rgb_o[ok]).max() <= COLOUR_TOL
 
 
+def _tile_lists(plan):
+    """{tile: [Gaussian ids in list order]} of the plan's sorted pairs."""
+    P = int(plan.stats().num_pairs)
+    vals = plan.ws_view(capi.WS_VALS, torch.int32, max(P, 1)).cpu().numpy().view(np.uint32)
+    ranges = plan.ws_view(capi.WS_RANGES, torch.int32, 2 * plan.batch.num_tiles).cpu().numpy().view(np.uint32)
+    ranges = ranges.reshape(-1, 2)
+    return {t: vals[a:b] for t, (a, b) in enumerate(ranges) if b > a}
+
+
+@pytest.mark.parametrize("tile,row0", [(16, 0), (8, 0), (32, 0), (16, 188)])
+def test_exact_tiles_same_image_fewer_pairs(tile, row0):
+    """Exact tile binning (each Gaussian listed only for the tiles its
+    alpha >= alpha_min ellipse can meet) against whole rectangles on the
+    full LiDAR frame: the same image bit for bit (colour, transmittance,
+    last Gaussian of every pixel), the same gradients, fewer pairs, and
+    every tile's list an in-order subsequence of its rectangle list.  Every
+    dropped (tile, Gaussian) pair is checked in FP64 with the oracle's
+    projection: no pixel centre of that tile reaches alpha_min."""
+    p = scenes.lidar_frame_problem()
+    p.frames[0].row0 = row0
+    out = {}
+    for exact in (False, True):
+        opts = render.RenderOptions(tile=tile, exact_tiles=exact)
+        scene, plan, ext, dl = setup(p, opts)
+        plan.forward(scene, ext, dl)
+        assert plan.stats().status == 0
+        dL = torch.from_numpy(np.random.default_rng(3).normal(size=tuple(plan.rgb.shape)).astype(np.float32)).cuda()
+        g = render.empty_grads(scene, 1)
+        plan.backward(scene, dL, g, ext)
+        out[exact] = dict(rgb=plan.rgb.cpu().numpy(), T=plan.T.cpu().numpy(), ids=last_gaussian_ids(plan, 0),
+                          pairs=int(plan.stats().num_pairs), lists=_tile_lists(plan),
+                          g={k: g[k].cpu().numpy() for k in ("quat", "log_scale", "logit_opacity", "rgb", "ext",
+                                                              "delta")})
+    r, e = out[False], out[True]
+    np.testing.assert_array_equal(e["rgb"], r["rgb"])
+    np.testing.assert_array_equal(e["T"], r["T"])
+    np.testing.assert_array_equal(e["ids"], r["ids"])
+    for k in r["g"]:
+        assert rel_l2(e["g"][k], r["g"][k]) <= 1e-5, k
+    assert e["pairs"] < 0.9 * r["pairs"], (e["pairs"], r["pairs"])
+    dropped = []
+    for t, lst in r["lists"].items():
+        sub = e["lists"].get(t, np.zeros(0, np.uint32))
+        keep = np.isin(lst, sub)
+        np.testing.assert_array_equal(lst[keep], sub)  # an in-order subsequence
+        dropped += [(t, int(gid)) for gid in lst[~keep]]
+    assert len(dropped) == r["pairs"] - e["pairs"]
+    # FP64: the dropped Gaussians reach no pixel centre of their tile at alpha >= alpha_min
+    f, cam = p.frames[0], p.frames[0].camera
+    R, t = oracle.frame_pose(p.scenes[0], p.ext[0], float(p.delta[0]), f.timestamp)
+    pr = oracle.project(p.scenes[0], cam, R, t, oracle_opts(render.RenderOptions(tile=tile)), tile)
+    tiles_x = (cam.width + tile - 1) // tile
+    rng = np.random.default_rng(4)
+    for k in rng.choice(len(dropped), min(3000, len(dropped)), replace=False):
+        tt, gid = dropped[k]
+        ty, tx = divmod(tt, tiles_x)
+        xs = np.arange(tx * tile, min(tx * tile + tile, cam.width)) - pr["mean"][gid][0]
+        ys = np.arange(row0 + ty * tile, min(row0 + ty * tile + tile, cam.height)) - pr["mean"][gid][1]
+        X, Y = np.meshgrid(xs, ys)
+        a, b, c = pr["conic"][gid]
+        alpha = pr["opacity"][gid] * np.exp(-0.5 * (a * X * X + 2 * b * X * Y + c * Y * Y))
+        assert alpha.max() < 1.0 / 255.0, (tt, gid, alpha.max())
+
+
 def test_render_fwd_deterministic():
     p = _tiny(128, 96, seed=4, n=500)
     scene, plan, ext, dl = setup(p)
@@ -468,7 +533,7 @@ def test_bench_workload_sampled_forward_and_backward():
     scene, plan, ext, dl = setup(p, opts)
     plan.forward(scene, ext, dl)
     st = plan.stats()
-    assert st.status == 0 and st.num_pairs > 30_000_000
+    assert st.status == 0 and st.num_pairs > 20_000_000
     rng = np.random.default_rng(11)
     dL = torch.zeros_like(plan.rgb)
     ref = {k: 0.0 for k in ("quat", "log_scale", "logit_opacity", "rgb", "ext", "delta")}

@@ -20,7 +20,8 @@ pytestmark = pytest.mark.gpu
 def _plan(frames_wh, counts, cap):
     frames = [dict(width=w, height=h, fx=100.0, fy=100.0, cx=w / 2, cy=h / 2, camera_id=0, traj_id=0,
                    gauss_offset=0, gauss_count=c, timestamp=0.0) for (w, h), c in zip(frames_wh, counts)]
-    return render.Plan(frames, max(counts), 1, 1, render.RenderOptions(tile=16), cap)
+    # the allocation-free entry point bins whole rectangles (it is passed no splat records)
+    return render.Plan(frames, max(counts), 1, 1, render.RenderOptions(tile=16, exact_tiles=False), cap)
 
 
 def _records(plan, seed, frames_wh, counts):
