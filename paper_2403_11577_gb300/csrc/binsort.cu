@@ -11,8 +11,11 @@
 // 2. k_pair_count / k_pair_scan / k_pair_emit over the records in that
 //    order: every record emits one pair per tile of its rectangle (emission
 //    is cooperative: threads stride over the block's output range and find
-//    their record by binary search).  The pairs are thus already in
-//    (depth, record) order; their key is the global tile alone.
+//    their record by binary search).  With exact tiles (gs_opts.exact_tiles)
+//    k_pair_count_exact / k_pair_emit_exact emit only the tiles of each
+//    rectangle row that the record's ellipse can meet (see "exact tile
+//    binning" below).  The pairs are thus already in (depth, record) order;
+//    their key is the global tile alone.
 // 3. LSD passes over the tile id (2 for up to 65,536 tiles): a stable sort
 //    by tile keeps the depth order inside each tile, so the result is the
 //    full-key order bit for bit, with a fraction of the traffic.
