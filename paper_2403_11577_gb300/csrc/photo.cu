@@ -20,7 +20,7 @@
 // along rows, then along columns), and the three maps A1 = S_mu - 2 mu_a S_aa -
 // mu_b S_ab, A2 = S_aa, A3 = S_ab are written to the workspace (planar:
 // map (3 ch + k) holds A_{k+1} of channel ch for every pixel) with FP64
-// per-block partial sums of SSIM and |a - b|.  k_ssim_bwd filters the maps
+// per-block partial sums of SSIM and |a - b| (float within a warp).  k_ssim_bwd filters the maps
 // the same way and writes the gradient of L_photo; k_photo_final reduces the
 // partials in a fixed order (deterministic).
 #include <cmath>
@@ -84,7 +84,7 @@ k_ssim_fwd(const gs_frame *__restrict__ frames, int F, long long P, const float 
     const TileGeom g = tile_geom<TR>(frames, F, blockIdx.x);
     const long long pix0 = g.fr->pixel_offset;
     const float C1 = 0.01f * 0.01f, C2 = 0.03f * 0.03f;
-    double ssim_acc = 0.0, l1_acc = 0.0;
+    float ssim_acc = 0.f, l1_acc = 0.f;  // at most 3 values per thread
     for (int i = threadIdx.x; i < E * E; i += kPhotoThreads) {
         const int rr = g.r0 - kWin + i / E, cc = g.c0 - kWin + i % E;
         const bool in = rr >= 0 && rr < g.R && cc >= 0 && cc < g.W;
@@ -96,24 +96,40 @@ k_ssim_fwd(const gs_frame *__restrict__ frames, int F, long long P, const float 
         }
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < 3 * E * TR; i += kPhotoThreads) {
-        const int ch = i / (E * TR), j = i % (E * TR);
-        const int r = j / TR, c = j % TR;
-        float sa = 0.f, sb = 0.f, saa = 0.f, sbb = 0.f, sab = 0.f;
+    // row filter: each thread two adjacent columns of one channel row, from
+    // the 12 staged values of a and of b they share (float2 loads; E, TR even)
+    for (int i = threadIdx.x; i < 3 * E * (TR / 2); i += kPhotoThreads) {
+        const int ch = i / (E * (TR / 2)), j = i % (E * (TR / 2));
+        const int r = j / (TR / 2), c = 2 * (j % (TR / 2));
+        float va[2 * kWin + 2], vb[2 * kWin + 2];
+        const float2 *ra = reinterpret_cast<const float2 *>(&S.in[ch][r][c]);
+        const float2 *rb = reinterpret_cast<const float2 *>(&S.in[3 + ch][r][c]);
 #pragma unroll
-        for (int k = 0; k < 2 * kWin + 1; k++) {
-            const float a = S.in[ch][r][c + k], b = S.in[3 + ch][r][c + k], w = G.w[k];
-            sa = fmaf(w, a, sa);
-            sb = fmaf(w, b, sb);
-            saa = fmaf(w * a, a, saa);
-            sbb = fmaf(w * b, b, sbb);
-            sab = fmaf(w * a, b, sab);
+        for (int q = 0; q < kWin + 1; q++) {
+            const float2 ta = ra[q], tb = rb[q];
+            va[2 * q] = ta.x;
+            va[2 * q + 1] = ta.y;
+            vb[2 * q] = tb.x;
+            vb[2 * q + 1] = tb.y;
         }
-        S.h[5 * ch][r][c] = sa;
-        S.h[5 * ch + 1][r][c] = sb;
-        S.h[5 * ch + 2][r][c] = saa;
-        S.h[5 * ch + 3][r][c] = sbb;
-        S.h[5 * ch + 4][r][c] = sab;
+#pragma unroll
+        for (int o = 0; o < 2; o++) {
+            float sa = 0.f, sb = 0.f, saa = 0.f, sbb = 0.f, sab = 0.f;
+#pragma unroll
+            for (int k = 0; k < 2 * kWin + 1; k++) {
+                const float a = va[k + o], b = vb[k + o], w = G.w[k];
+                sa = fmaf(w, a, sa);
+                sb = fmaf(w, b, sb);
+                saa = fmaf(w * a, a, saa);
+                sbb = fmaf(w * b, b, sbb);
+                sab = fmaf(w * a, b, sab);
+            }
+            S.h[5 * ch][r][c + o] = sa;
+            S.h[5 * ch + 1][r][c + o] = sb;
+            S.h[5 * ch + 2][r][c + o] = saa;
+            S.h[5 * ch + 3][r][c + o] = sbb;
+            S.h[5 * ch + 4][r][c + o] = sab;
+        }
     }
     __syncthreads();
     for (int i = threadIdx.x; i < 3 * TR * TR; i += kPhotoThreads) {
@@ -143,17 +159,19 @@ k_ssim_fwd(const gs_frame *__restrict__ frames, int F, long long P, const float 
         maps[(3 * ch) * P + p] = S_mu - 2.f * ma * S_aa - mb * S_ab;
         maps[(3 * ch + 1) * P + p] = S_aa;
         maps[(3 * ch + 2) * P + p] = S_ab;
-        ssim_acc += (double)ssim;
-        l1_acc += (double)fabsf(S.in[ch][r + kWin][c + kWin] - S.in[3 + ch][r + kWin][c + kWin]);
+        ssim_acc += ssim;
+        l1_acc += fabsf(S.in[ch][r + kWin][c + kWin] - S.in[3 + ch][r + kWin][c + kWin]);
     }
+    // summed over the warp in float (96 terms), widened per warp: GB300's
+    // FP64 rate is low, and per-pixel FP64 adds kept its FP64 pipe busy
     for (int s = 16; s > 0; s >>= 1) {
         ssim_acc += __shfl_xor_sync(0xffffffffu, ssim_acc, s);
         l1_acc += __shfl_xor_sync(0xffffffffu, l1_acc, s);
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (lane == 0) {
-        S.red[0][warp] = ssim_acc;
-        S.red[1][warp] = l1_acc;
+        S.red[0][warp] = (double)ssim_acc;
+        S.red[1][warp] = (double)l1_acc;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -185,40 +203,57 @@ k_ssim_bwd(const gs_frame *__restrict__ frames, int F, long long P, const float 
         for (int m = 0; m < 9; m++) S.in[m][i / E][i % E] = in ? maps[m * P + p] : 0.f;
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < 3 * E * TR; i += kPhotoThreads) {
-        const int ch = i / (E * TR), j = i % (E * TR);
-        const int r = j / TR, c = j % TR;
-        float s1 = 0.f, s2 = 0.f, s3 = 0.f;
+    // row filter: each thread two adjacent columns of one map row, from the
+    // 12 staged values they share (float2 loads; E and TR are even)
+    for (int i = threadIdx.x; i < 9 * E * (TR / 2); i += kPhotoThreads) {
+        const int m = i / (E * (TR / 2)), j = i % (E * (TR / 2));
+        const int r = j / (TR / 2), c = 2 * (j % (TR / 2));
+        float v[2 * kWin + 2];
+        const float2 *row = reinterpret_cast<const float2 *>(&S.in[m][r][c]);
+#pragma unroll
+        for (int q = 0; q < kWin + 1; q++) {
+            const float2 t = row[q];
+            v[2 * q] = t.x;
+            v[2 * q + 1] = t.y;
+        }
+        float s0 = 0.f, s1 = 0.f;
 #pragma unroll
         for (int k = 0; k < 2 * kWin + 1; k++) {
-            const float w = G.w[k];
-            s1 = fmaf(w, S.in[3 * ch][r][c + k], s1);
-            s2 = fmaf(w, S.in[3 * ch + 1][r][c + k], s2);
-            s3 = fmaf(w, S.in[3 * ch + 2][r][c + k], s3);
+            s0 = fmaf(G.w[k], v[k], s0);
+            s1 = fmaf(G.w[k], v[k + 1], s1);
         }
-        S.h[3 * ch][r][c] = s1;
-        S.h[3 * ch + 1][r][c] = s2;
-        S.h[3 * ch + 2][r][c] = s3;
+        *reinterpret_cast<float2 *>(&S.h[m][r][c]) = make_float2(s0, s1);
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < 3 * TR * TR; i += kPhotoThreads) {
-        const int ch = i / (TR * TR), j = i % (TR * TR);
-        const int r = j / TR, c = j % TR;
-        const int rr = g.r0 + r, cc = g.c0 + c;
-        if (rr >= g.R || cc >= g.W) continue;
-        float g1 = 0.f, g2 = 0.f, g3 = 0.f;
+    // column filter: each thread two adjacent rows of one pixel column and
+    // channel, from the 12 row-filtered values they share
+    for (int i = threadIdx.x; i < 3 * (TR / 2) * TR; i += kPhotoThreads) {
+        const int ch = i / ((TR / 2) * TR), j = i % ((TR / 2) * TR);
+        const int r = 2 * (j / TR), c = j % TR;
+        float gg[3][2];
 #pragma unroll
-        for (int k = 0; k < 2 * kWin + 1; k++) {
-            const float w = G.w[k];
-            g1 = fmaf(w, S.h[3 * ch][r + k][c], g1);
-            g2 = fmaf(w, S.h[3 * ch + 1][r + k][c], g2);
-            g3 = fmaf(w, S.h[3 * ch + 2][r + k][c], g3);
+        for (int m = 0; m < 3; m++) {
+            float s0 = 0.f, s1 = 0.f, prev = S.h[3 * ch + m][r][c];
+#pragma unroll
+            for (int k = 0; k < 2 * kWin + 1; k++) {
+                const float nxt = S.h[3 * ch + m][r + k + 1][c];
+                s0 = fmaf(G.w[k], prev, s0);
+                s1 = fmaf(G.w[k], nxt, s1);
+                prev = nxt;
+            }
+            gg[m][0] = s0;
+            gg[m][1] = s1;
         }
-        const long long v = 3 * (pix0 + (long long)rr * g.W + cc) + ch;
-        const float a = x[v], b = y[v];
-        const float d_ssim = (g1 + 2.f * a * g2 + b * g3) * inv_n;  // d(mean SSIM)/da
-        const float d_l1 = (a > b ? inv_n : (a < b ? -inv_n : 0.f));
-        grad[v] = scale * ((1.f - lambda1) * d_l1 - lambda1 * d_ssim);
+#pragma unroll
+        for (int q = 0; q < 2; q++) {
+            const int rr = g.r0 + r + q, cc = g.c0 + c;
+            if (rr >= g.R || cc >= g.W) continue;
+            const long long v = 3 * (pix0 + (long long)rr * g.W + cc) + ch;
+            const float a = x[v], b = y[v];
+            const float d_ssim = (gg[0][q] + 2.f * a * gg[1][q] + b * gg[2][q]) * inv_n;  // d(mean SSIM)/da
+            const float d_l1 = (a > b ? inv_n : (a < b ? -inv_n : 0.f));
+            grad[v] = scale * ((1.f - lambda1) * d_l1 - lambda1 * d_ssim);
+        }
     }
 }
 
