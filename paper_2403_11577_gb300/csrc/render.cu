@@ -3,7 +3,7 @@
 //
 // One block per (frame, tile) work item of the whole batch, taken in the
 // heavy-first order gs_bin_sort computes (longest lists first).  Each warp
-// owns a compact full-width band of the tile and walks the tile's
+// owns a compact, near-square band of the tile and walks the tile's
 // depth-sorted list on its own (no block-wide barrier inside the loop): it
 // loads chunks of batch/2 entries (prefetching the next chunk into registers
 // while it uses the current one), keeps the entries that can reach
@@ -14,8 +14,8 @@
 // The heaviest tiles (up to two per SM, the head of the heavy-first order)
 // bound the kernel's duration: a band of a tile near the vanishing point
 // walks tens of thousands of entries alone.  Each of them is split into two
-// work items (upper and lower half) with bands of half the height and half
-// the pixels per thread, which halves the Gaussians a warp composites and so
+// work items (upper and lower half) with bands of half the pixels (half the
+// pixels per thread), which halves the Gaussians a warp composites and so
 // that tile's critical path.  The work items of one launch are: the halves
 // of the heavy tiles first (blocks are dispatched in index order, so they
 // start first), then every other tile whole.  The image does not depend on
@@ -59,17 +59,27 @@ namespace gs {
 
 namespace {
 
-// Pixels per thread: 2 at tiles 8 and 16 (bands 8x8 and 16x4), 4 at 32
-// (32x4); half of that in the halves of heavy tiles (bands 8x4, 16x2, 32x2).
+// Pixels per thread: 2 at tiles 8 and 16, 4 at 32; half of that in the
+// halves of heavy tiles.
 __host__ __device__ constexpr int pix_per_thread(int tile) { return tile == 32 ? 4 : 2; }
 
 // A work item of TILE-wide rows for NT threads at PPT pixels per thread.
+// A warp's band holds 32 * PPT pixels in the squarest shape the tile allows:
+// 8x4 (32 pixels), 8x8 (64) or 16x8 (128).  Of two bands of equal area the
+// squarer one has the shorter border, so fewer Gaussians reach it without
+// compositing any of its pixels (on the 1M-Gaussian drive frames, 8x8 keeps
+// 6-7% fewer (band, Gaussian) pairs than 16x4, and 8x4 12% fewer than 16x2).
+// Lane l holds column l mod BW of its band and the PPT vertically adjacent
+// rows from (l / BW) * PPT; the bands fill the item row of bands by row.
 template <int TILE, int PPT, int NT>
 struct Cfg {
-    static constexpr int NW = NT / 32;            // warps per block
-    static constexpr int RPW = 32 * PPT / TILE;   // pixel rows of a warp's band
-    static constexpr int ROWS = NW * RPW;         // pixel rows of the item
-    static_assert(NT % 32 == 0 && (32 * PPT) % TILE == 0 && ROWS <= TILE, "a warp owns full-width rows");
+    static constexpr int NW = NT / 32;                   // warps per block
+    static constexpr int BW = 32 * PPT >= 128 ? 16 : 8;  // band width
+    static constexpr int BH = 32 * PPT / BW;             // band height
+    static constexpr int BPR = TILE / BW;                // bands per row of bands
+    static constexpr int ROWS = NW / BPR * BH;           // pixel rows of the item
+    static_assert(NT % 32 == 0 && TILE % BW == 0 && 32 % BW == 0 && NW % BPR == 0 && ROWS <= TILE,
+                  "the bands tile the work item");
 };
 
 template <int TILE>
@@ -163,14 +173,19 @@ struct alignas(16) Staged {
 };
 
 // Band of warp `warp` in the work item starting at row rbase of the tile
-// whose first image row is y_tile, clipped to the image.
-template <int TILE, int RPW>
-__device__ __forceinline__ void band_of(int tx, int y_tile, int rbase, int warp, int W, int H, float &xlo, float &xhi,
-                                        float &ylo, float &yhi) {
-    xlo = (float)(tx * TILE);
-    xhi = (float)min(tx * TILE + TILE - 1, W - 1);
-    ylo = (float)(y_tile + rbase + warp * RPW);
-    yhi = (float)min(y_tile + rbase + warp * RPW + RPW - 1, H - 1);
+// whose first image row is y_tile, clipped to the image, and the image
+// column u and first image row v0 of the lane's pixels.
+template <int TILE, class C, int PPT>
+__device__ __forceinline__ void band_of(int tx, int y_tile, int rbase, int warp, int lane, int W, int H, float &xlo,
+                                        float &xhi, float &ylo, float &yhi, int &u, int &v0) {
+    const int x0 = tx * TILE + (warp % C::BPR) * C::BW;
+    const int y0 = y_tile + rbase + (warp / C::BPR) * C::BH;
+    xlo = (float)x0;
+    xhi = (float)min(x0 + C::BW - 1, W - 1);
+    ylo = (float)y0;
+    yhi = (float)min(y0 + C::BH - 1, H - 1);
+    u = x0 + lane % C::BW;
+    v0 = y0 + (lane / C::BW) * PPT;
 }
 
 // Compact the chunk's kept entries, in order, into the warp's slot; returns
@@ -207,7 +222,9 @@ __device__ __forceinline__ void fwd_item(int t, int rbase, Staged *st_all, unsig
                                          const RenderParams &rp, Stats *__restrict__ stats,
                                          float *__restrict__ out_rgb, float *__restrict__ out_T,
                                          int32_t *__restrict__ out_last) {
-    constexpr int RPW = Cfg<TILE, PPT, NT>::RPW, CH = BATCH / 2, PER = CH / 32;
+    using C = Cfg<TILE, PPT, NT>;
+    constexpr int CH = BATCH / 2, PER = CH / 32;
+    static_assert(C::ROWS * (PPT == pix_per_thread(TILE) ? 1 : 2) == TILE, "a work item is a tile or half of one");
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     Staged *st = st_all + warp * CH;
     const int f = frame_of_tile(frames, F, t);
@@ -217,9 +234,8 @@ __device__ __forceinline__ void fwd_item(int t, int rbase, Staged *st_all, unsig
     const int tx = lt % fr.tiles_x, ty = lt / fr.tiles_x;
     const int y_tile = fr.row0 + ty * TILE;  // image row of the tile's first row (frames may be cropped)
     float xlo, xhi, ylo, yhi;
-    band_of<TILE, RPW>(tx, y_tile, rbase, warp, W, H, xlo, xhi, ylo, yhi);
-    const int u = tx * TILE + (int)threadIdx.x % TILE;
-    const int v0 = y_tile + rbase + ((int)threadIdx.x / TILE) * PPT;  // first image row of the thread's pixels
+    int u, v0;  // the thread's image column and first image row
+    band_of<TILE, C, PPT>(tx, y_tile, rbase, warp, lane, W, H, xlo, xhi, ylo, yhi, u, v0);
     const float px = (float)u;
     float py[PPT], T[PPT], c0[PPT], c1[PPT], c2[PPT];
     int last[PPT];
@@ -379,7 +395,9 @@ __device__ __forceinline__ void bwd_item(int t, int rbase, Staged *st_all, unsig
                                          const RenderParams &rp, Stats *__restrict__ stats,
                                          const float *__restrict__ in_T, const int32_t *__restrict__ in_last,
                                          const float *__restrict__ dL_drgb, float4 *__restrict__ grad2d) {
-    constexpr int RPW = Cfg<TILE, PPT, NT>::RPW, CH = BATCH / 2, PER = CH / 32;
+    using C = Cfg<TILE, PPT, NT>;
+    constexpr int CH = BATCH / 2, PER = CH / 32;
+    static_assert(C::ROWS * (PPT == pix_per_thread(TILE) ? 1 : 2) == TILE, "a work item is a tile or half of one");
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     Staged *st = st_all + warp * CH;
     const int f = frame_of_tile(frames, F, t);
@@ -389,9 +407,8 @@ __device__ __forceinline__ void bwd_item(int t, int rbase, Staged *st_all, unsig
     const int tx = lt % fr.tiles_x, ty = lt / fr.tiles_x;
     const int y_tile = fr.row0 + ty * TILE;
     float xlo, xhi, ylo, yhi;
-    band_of<TILE, RPW>(tx, y_tile, rbase, warp, W, H, xlo, xhi, ylo, yhi);
-    const int u = tx * TILE + (int)threadIdx.x % TILE;
-    const int v0 = y_tile + rbase + ((int)threadIdx.x / TILE) * PPT;
+    int u, v0;
+    band_of<TILE, C, PPT>(tx, y_tile, rbase, warp, lane, W, H, xlo, xhi, ylo, yhi, u, v0);
     const float px = (float)u;
     if (threadIdx.x == 0) s_eval = 0;
     // the range of this tile; a pixel's start position never exceeds it

@@ -245,10 +245,11 @@ def _lidar_grads(tile, batch, W):
 
 
 def test_render_band_shapes_agree_on_lidar_frame():
-    """Full-size LiDAR frame of anisotropic Gaussians: every tile edge culls
-    with its own band shape (8x8, 16x4, 32x4), yet the
-    image is the same bit for bit, the forward composites exactly the pairs
-    the backward revisits, and the gradients agree to rounding."""
+    """Full-size LiDAR frame of anisotropic Gaussians: every tile size culls
+    with its own band shapes (8x8 bands at tiles 8 and 16, 16x8 at 32; 8x4,
+    8x4 and 8x8 in the halves of heavy tiles), yet the image is the same bit
+    for bit, the forward composites exactly the pairs the backward revisits,
+    and the gradients agree to rounding."""
     cam = scenes.lidar_frame_problem().frames[0].camera
     W = np.random.default_rng(11).normal(size=(cam.height * cam.width, 3)).astype(np.float32)
     ref, gref = _lidar_grads(16, 64, W)
