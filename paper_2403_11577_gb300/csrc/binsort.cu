@@ -199,8 +199,12 @@ __device__ __forceinline__ void row_span(const RowSpanner &s, int ty, int rx0, i
     const float w = add_(add_(0.02f, mul_(0x1p-10f, add_(fabsf(Xa), fabsf(Xb)))), mul_(0x1p-12f, fabsf(s.mx)));
     const float xa = fminf(fmaxf(sub_(add_(s.mx, Xa), w), -1e9f), 1e9f);
     const float xb = fminf(fmaxf(add_(add_(s.mx, Xb), w), -1e9f), 1e9f);
-    lo = max(rx0, (int)floorf(__fdiv_rn(xa, (float)T)));
-    hi = min(rx1, (int)floorf(__fdiv_rn(xb, (float)T)));
+    // T is 8, 16 or 32: x / T and x * (1 / T) are the same real number
+    // (a power-of-two scaling), so the rounded product equals the rounded
+    // quotient bit for bit
+    const float invT = T == 8 ? 0.125f : (T == 16 ? 0.0625f : 0.03125f);
+    lo = max(rx0, (int)floorf(mul_(xa, invT)));
+    hi = min(rx1, (int)floorf(mul_(xb, invT)));
 }
 
 // Pairs of each emission block with exact tiles (as k_pair_count); also
@@ -334,19 +338,46 @@ k_pair_emit_exact(const gs_frame *__restrict__ frames, int F, int T, float lmin,
             }
         }
         __syncthreads();
-        const uint32_t n = w1 - w0;
+        const int n = (int)(w1 - w0);
         const uint32_t o_lo = S.seg[0].off, o_hi = S.seg[n - 1].off + S.seg[n - 1].len;
-        for (uint32_t o = o_lo + threadIdx.x; o < o_hi; o += kEmitThreads) {
-            int lo = 0, hi = (int)n - 1;
+        // Each warp expands a contiguous run of 32-pair groups.  One binary
+        // search finds the segment s0 holding the run's first pair; in every
+        // group lane k then checks candidate s0 + 1 + k, whose start lies d
+        // pairs after the group's first pair (segments are non-empty and in
+        // pair order, so the starts within the next 32 pairs are exactly the
+        // first candidates).  The starts with d < 32 form a bit mask, lane l's
+        // segment is s0 plus the starts in (0, l], and the next group's s0
+        // adds every start with d <= 32.
+        constexpr int NW = kEmitThreads / 32;
+        const uint32_t ngroups = (o_hi - o_lo + 31u) >> 5;
+        const uint32_t per = (ngroups + NW - 1) / NW;
+        const uint32_t g0 = min(ngroups, (uint32_t)warp * per), g1 = min(ngroups, g0 + per);
+        int s0 = 0;
+        if (g0 < g1) {
+            const uint32_t o0 = o_lo + (g0 << 5);
+            int lo = 0, hi = n - 1;
             while (lo < hi) {
                 const int mid = (lo + hi + 1) >> 1;
-                if (S.seg[mid].off <= o) lo = mid; else hi = mid - 1;
+                if (S.seg[mid].off <= o0) lo = mid; else hi = mid - 1;
             }
-            const Segment sg = S.seg[lo];
-            if (gbase + o < npairs_all) {  // always true when the count agrees (same arithmetic)
-                keys[gbase + o] = sg.tile0 + (o - sg.off);
-                vals[gbase + o] = sg.val;
+            s0 = lo;
+        }
+        for (uint32_t g = g0; g < g1; g++) {
+            const uint32_t o0 = o_lo + (g << 5);
+            const int c = s0 + 1 + lane;
+            const uint32_t d = c < n ? S.seg[c].off - o0 : 64u;
+            const uint32_t starts = __reduce_or_sync(0xffffffffu, d < 32u ? 1u << d : 0u);
+            const bool at32 = __any_sync(0xffffffffu, d == 32u);
+            const int sl = s0 + __popc(starts & (0xffffffffu >> (31 - lane)));
+            const uint32_t o = o0 + (uint32_t)lane;
+            if (o < o_hi) {
+                const Segment sg = S.seg[sl];
+                if (gbase + o < npairs_all) {  // always true when the count agrees (same arithmetic)
+                    keys[gbase + o] = sg.tile0 + (o - sg.off);
+                    vals[gbase + o] = sg.val;
+                }
             }
+            s0 += __popc(starts) + (at32 ? 1 : 0);
         }
         __syncthreads();
     }
