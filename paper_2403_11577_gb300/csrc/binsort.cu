@@ -246,7 +246,7 @@ k_pair_count_exact(const gs_frame *__restrict__ frames, int F, int T, float lmin
 // Emission with exact tiles (as k_pair_emit<uint32_t>).  A record's pairs
 // are its rows' runs of tiles, each a segment (first pair, length, first
 // tile, value); the block's segments are staged in shared memory in windows
-// of kSegWindow, and each output pair finds its segment by binary search.
+// of kSegWindow, and the warps expand them into pairs 32 at a time.
 constexpr int kSegWindow = 4096;
 
 struct Segment {
