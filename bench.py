@@ -37,6 +37,16 @@ import numpy as np  # noqa: E402
 
 METRIC = "calib iters/s (fwd+bwd, 8×1408×376, 1M Gaussians) batched vs per-frame"
 WORKLOAD = "1M LiDAR-anchored Gaussians (50 synthetic 64-beam sweeps, 10 m/s drive), 8 frames 1408x376"
+
+
+def workload_label(n, frames):
+    """The batched workload's description for a run at n Gaussians and
+    `frames` frames (the headline label at the defaults)."""
+    if n == 1_000_000 and frames == 8:
+        return WORKLOAD
+    ns = "%gM" % (n / 1e6) if n >= 1_000_000 else "%gK" % (n / 1e3)
+    return ("%s LiDAR-anchored Gaussians (50 synthetic 64-beam sweeps, 10 m/s drive), %d frame%s 1408x376"
+            % (ns, frames, "" if frames == 1 else "s"))
 # Arithmetic per composited (pixel, Gaussian) pair, i.e. per pair with
 # alpha >= alpha_min before the pixel stops (Eq. 5), comparisons not counted.
 # Forward: dx, dy (2), exponent (7), + log2 o (1), 2^e and the alpha clamp (2),
@@ -534,7 +544,8 @@ def run_ours(args, world, rank, local):
         "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max * 1e3 / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD if args.workload == "batched" else UNEVEN, "gaussians": scene.n,
+        "config": {"workload": (workload_label(scene.n, plan.batch.num_frames) if args.workload == "batched"
+                                else UNEVEN), "gaussians": scene.n,
                    "frames": plan.batch.num_frames,
                    "image": "1408x376" if args.workload == "batched" else "704x188/1408x376/1920x1080",
                    "tile": opts.tile, "batch": opts.batch,
@@ -559,8 +570,8 @@ def run_ours(args, world, rank, local):
         out["cpu_baseline"] = {"value": 1.0 / secs, "unit": "iters/s", "cores": 1, "kind": "oracle",
                                "sample": "FP64 oracle on frames 0 and %d: projection + global depth sort, "
                                          "forward and backward of %d sampled pixels each (%.1f s of CPU); "
-                                         "extrapolated to 8 frames x 529,408 pixels" %
-                                         (len(problem.frames) // 2, args.cpu_pixels, sample)}
+                                         "extrapolated to %d frames x 529,408 pixels" %
+                                         (len(problem.frames) // 2, args.cpu_pixels, sample, len(problem.frames))}
     return out
 
 
@@ -582,11 +593,12 @@ def run_reference(args, world, rank):
     return {"metric": METRIC, "value": v, "unit": "iters/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": secs * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": WORKLOAD, "gaussians": problem.scenes[0].n, "frames": fr, "image": "1408x376"},
+            "config": {"workload": workload_label(problem.scenes[0].n, fr), "gaussians": problem.scenes[0].n,
+                       "frames": fr, "image": "1408x376"},
             "cpu_baseline": {"value": v, "unit": "iters/s", "cores": 1, "kind": "oracle",
                              "sample": "per step: one frame's projection + global sort, forward and backward of 8 "
-                                       "sampled pixels, extrapolated to 8 frames x 529,408 pixels (%.1f s CPU total)"
-                                       % sample_total},
+                                       "sampled pixels, extrapolated to %d frames x 529,408 pixels (%.1f s CPU total)"
+                                       % (fr, sample_total)},
             "e2e": {"value": v, "unit": "iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
