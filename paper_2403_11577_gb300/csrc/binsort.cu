@@ -570,18 +570,32 @@ k_radix_scatter(const K *__restrict__ kin, const uint32_t *__restrict__ vin, K *
     }
     __syncthreads();
     const uint32_t lt_mask = (1u << lane) - 1u;
+    // warp w owns items [w*32*ITEMS, (w+1)*32*ITEMS) of each tile, in index
+    // order; the next tile's keys and values are loaded while this one is
+    // staged and written
+    K kn[kSortItems];
+    uint32_t vn[kSortItems];
+#pragma unroll
+    for (int r = 0; r < kSortItems; r++) {
+        const long long idx = c.lo + (long long)warp * 32 * kSortItems + r * 32 + lane;
+        const bool valid = idx < c.hi;
+        kn[r] = valid ? kin[idx] : K(0);
+        vn[r] = valid ? vin[idx] : 0u;
+    }
     for (long long t0 = c.lo; t0 < c.hi; t0 += kSortTile) {
         for (int i = lane; i < kRadix; i += 32) S.wcnt[warp][i] = 0;
         __syncwarp();
         K k[kSortItems];
         uint32_t v[kSortItems], dg[kSortItems], rk[kSortItems];
-        // warp w owns items [w*32*ITEMS, (w+1)*32*ITEMS) of the tile, in index order
+#pragma unroll
+        for (int r = 0; r < kSortItems; r++) {
+            k[r] = kn[r];
+            v[r] = vn[r];
+        }
 #pragma unroll
         for (int r = 0; r < kSortItems; r++) {
             const long long idx = t0 + (long long)warp * 32 * kSortItems + r * 32 + lane;
             const bool valid = idx < c.hi;
-            k[r] = valid ? kin[idx] : K(0);
-            v[r] = valid ? vin[idx] : 0u;
             const uint32_t d = (uint32_t)(k[r] >> shift) & (kRadix - 1);
             dg[r] = valid ? d : kRadix;  // kRadix marks an empty slot
             const uint32_t key = valid ? d : (uint32_t)(kRadix + lane);
@@ -592,6 +606,15 @@ k_radix_scatter(const K *__restrict__ kin, const uint32_t *__restrict__ vin, K *
             if (valid && before == 0) S.wcnt[warp][d] = base + (uint32_t)__popc(peers);
             __syncwarp();
             rk[r] = base + before;
+        }
+        if (t0 + kSortTile < c.hi) {
+#pragma unroll
+            for (int r = 0; r < kSortItems; r++) {
+                const long long idx = t0 + kSortTile + (long long)warp * 32 * kSortItems + r * 32 + lane;
+                const bool valid = idx < c.hi;
+                kn[r] = valid ? kin[idx] : K(0);
+                vn[r] = valid ? vin[idx] : 0u;
+            }
         }
         __syncthreads();
         // per digit: exclusive prefix over warps and the tile count
