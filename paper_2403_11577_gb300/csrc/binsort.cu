@@ -27,8 +27,9 @@
 // Each radix pass: k_radix_hist (per-block digit counts) -> k_radix_colscan
 // (per-digit prefix over blocks, digit totals) -> k_radix_scatter (stable:
 // per-warp ranking with match_any in index order, per-tile prefix over
-// warps, staging in shared memory by digit, coalesced writes); each block
-// owns one contiguous chunk of the input.  No kernel waits on another
+// warps, staging in shared memory by digit, coalesced writes; the next
+// tile's keys and values are loaded into registers while the current tile is
+// staged and written); each block owns one contiguous chunk of the input.  No kernel waits on another
 // block; there are no spin loops.
 #include <algorithm>
 
