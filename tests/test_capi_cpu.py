@@ -15,6 +15,17 @@ def lib():
     return capi.lib()
 
 
+def _no_device():
+    import torch
+    return not torch.cuda.is_available()
+
+
+# the validation tests pass pointers that are never meant to be dereferenced;
+# they run only where no device can be reached, so that a check removed by
+# mistake cannot turn into a kernel launch on a fake address
+host_only = pytest.mark.skipif(not _no_device(), reason="fake pointers: host-only validation test")
+
+
 def test_exports_every_declared_symbol(lib):
     declared = capi.declared_symbols()
     assert len(declared) >= 14
@@ -72,6 +83,7 @@ def test_header_documents_each_entry_point():
         assert m, name
 
 
+@host_only
 def test_ngp_entry_points_validate_on_the_host(lib):
     """The hash-grid entry points check their configuration and pointers
     before any device work: the parameter count matches the oracle's layout,
@@ -98,3 +110,79 @@ def test_ngp_entry_points_validate_on_the_host(lib):
         capi.GS_ERR_INVALID_ARG  # NULL rgb
     assert lib.gs_ngp_forward(C.byref(cfg.c()), ok16, ok16, C.c_int64(-1), *args, None) == capi.GS_ERR_INVALID_ARG
     assert lib.gs_ngp_fault(None) == capi.GS_ERR_INVALID_ARG
+
+
+@host_only
+def test_entry_points_validate_on_the_host(lib):
+    """Every batch entry point rejects a missing batch, a misaligned
+    workspace, options that disagree with the batch or lie outside their
+    documented ranges, and NULL required pointers with GS_ERR_INVALID_ARG
+    before any device work; the allocation-free sort answers exact tiles with
+    GS_ERR_UNSUPPORTED and an oversized batch with GS_ERR_CAPACITY.  The
+    pointers below are never dereferenced."""
+    from paper_2403_11577_gb300 import render
+    P = C.c_void_p
+    INV = capi.GS_ERR_INVALID_ARG
+    b = capi.GsBatch()
+    b.frames_dev = 0x1000
+    b.num_frames, b.num_cameras, b.num_trajs, b.num_gaussians = 2, 1, 1, 100
+    b.tile, b.num_tiles = 16, 2 * 4 * 3
+    b.num_records, b.num_pixels, b.pair_capacity = 200, 2 * 64 * 48, 10_000
+    ws, bad_ws, ptr = P(0x100000), P(0x100008), P(0x200000)
+
+    def opts(**kw):
+        o = render.RenderOptions().c()
+        for k, v in kw.items():
+            setattr(o, k, v)
+        return o
+
+    ok = opts()
+    B, O = C.byref(b), C.byref(ok)
+    # batch and workspace
+    assert lib.gs_reset_status(None, ws, None) == INV
+    assert lib.gs_reset_status(B, bad_ws, None) == INV
+    assert lib.gs_read_stats(B, ws, None, None) == INV
+    nb = capi.GsBatch.from_buffer_copy(b)
+    nb.frames_dev = None
+    assert lib.gs_bin_sort(C.byref(nb), O, ws, None) == INV
+    # options
+    for bad in (opts(tile=8), opts(batch=100), opts(exact_tiles=2), opts(alpha_max=1.0), opts(alpha_min=0.0),
+                opts(near_z=0.0), opts(scale_max=0.0), opts(t_min=-1.0)):
+        assert lib.gs_bin_sort(B, C.byref(bad), ws, None) == INV
+        assert lib.gs_project(B, ptr, ptr, ptr, ptr, C.byref(bad), ws, None) == INV
+    assert lib.gs_project(B, ptr, ptr, ptr, ptr, None, ws, None) == INV
+    # required pointers
+    assert lib.gs_pose_compose(B, None, ptr, ptr, ptr, ptr, ws, None) == INV
+    assert lib.gs_pose_compose(B, ptr, ptr, ptr, ptr, ptr, bad_ws, None) == INV
+    assert lib.gs_project(B, None, ptr, ptr, ptr, O, ws, None) == INV
+    assert lib.gs_render_fwd(B, ptr, O, ws, ptr, ptr, None, None) == INV
+    assert lib.gs_render_fwd(B, None, O, ws, ptr, ptr, ptr, None) == INV
+    assert lib.gs_loss_l1(B, ptr, ptr, -1, 1.0, ptr, ptr, ws, None) == INV
+    assert lib.gs_loss_l1(B, ptr, None, 10, 1.0, ptr, ptr, ws, None) == INV
+    assert lib.gs_loss_photo(B, ptr, ptr, 1.5, 1.0, ptr, ptr, ws, None) == INV
+    assert lib.gs_loss_photo(B, ptr, ptr, 0.2, 1.0, None, ptr, ws, None) == INV
+    # X, quat, log_scale, logit_opacity, colors, opts, ws, out_T, out_last, dL_drgb, d_quat, d_log_scale,
+    # d_logit_opacity, d_colors
+    bwd = [ptr] * 5 + [O, ws, ptr, ptr, ptr] + [ptr] * 4
+    for i in (0, 4, 7, 8, 9, 10, 13):
+        args = list(bwd)
+        args[i] = None
+        assert lib.gs_render_bwd(B, *args, 0, None) == INV, i
+    assert lib.gs_pose_grad(B, ptr, ws, ptr, None, None, 0, None) == INV
+    assert lib.gs_pose_grad(B, None, ws, ptr, ptr, None, 0, None) == INV
+    assert lib.gs_profile_events(99, None, None) == INV
+    assert lib.gs_profile_events(capi.GS_PROF_RENDER_BWD, None, None) == INV
+    # voxel downsampling
+    scratch = P(0x300000)
+    for n, v, s in ((-1, 0.1, scratch), (10, 0.0, scratch), (10, float("nan"), scratch), (10, float("inf"), scratch),
+                    (10, 0.1, P(0x300010))):
+        assert lib.gs_voxel_downsample(ptr, n, v, ptr, ptr, s, None) == INV, (n, v)
+    assert lib.gs_voxel_downsample(ptr, 10, 0.1, ptr, None, scratch, None) == INV
+    # allocation-free sort
+    assert lib.gs_bin_sort_noalloc(B, O, ptr, ptr, None, ptr, ptr, ptr, None) == INV
+    assert lib.gs_bin_sort_noalloc(B, C.byref(opts(exact_tiles=1)), ptr, ptr, ptr, ptr, ptr, ptr, None) == \
+        capi.GS_ERR_UNSUPPORTED
+    big = capi.GsBatch.from_buffer_copy(b)
+    big.pair_capacity = 1 << 22
+    assert lib.gs_bin_sort_noalloc(C.byref(big), C.byref(opts(exact_tiles=0)), ptr, ptr, ptr, ptr, ptr, ptr,
+                                   None) == capi.GS_ERR_CAPACITY
