@@ -535,3 +535,42 @@ def test_voxel_downsample_drops_non_finite_and_far_points():
                   [3e6, 0, 0], [-0.05, 0.0, 0.0]], np.float32)
     np.testing.assert_array_equal(oracle.voxel_downsample(X, 0.1), [0, 5])
     assert len(oracle.voxel_downsample(X[[1, 3]], 0.1)) == 0
+
+
+def _rect_cases(seed=21, n=80):
+    rng = np.random.default_rng(seed)
+    X = np.stack([rng.uniform(-1.2, 1.2, n), rng.uniform(-0.9, 0.9, n), rng.uniform(2.0, 5.0, n)], 1)
+    q = rng.normal(size=(n, 4))
+    ls = np.log(rng.uniform(0.08, 0.4, (n, 3)))
+    op = np.exp(-rng.uniform(np.log(1.2), np.log(40.0), n))  # opacity 0.025..0.83, log-uniform
+    lo = np.log(op / (1 - op))
+    sc = scenes.Scene(X, q, ls, lo, np.ones((n, 3)), np.array([0.0]), np.zeros((1, 3)), np.array([[1.0, 0, 0, 0]]))
+    cam = scenes.Camera(320, 240, 200.0, 200.0, 159.5, 119.5)
+    return sc, cam
+
+
+def test_tile_rect_holds_every_pixel_that_reaches_alpha_min():
+    """Reading 8 by brute force: for anisotropic Gaussians of every
+    orientation and opacities from 0.025 to 0.83, every pixel centre where
+    opacity * exp(-1/2 d^T conic d) >= alpha_min lies in a tile of the
+    Gaussian's rectangle, and the rectangle reaches at most one tile beyond
+    the tiles of those pixels on each side.  Its extent is therefore the
+    alpha = alpha_min ellipse: a fixed number of sigmas, or an extent that
+    ignores the opacity, fails one of the two bounds."""
+    sc, cam = _rect_cases()
+    T = 16
+    pr = oracle.project(sc, cam, np.eye(3), np.zeros(3), oracle.Opts(), T)
+    u, v = np.meshgrid(np.arange(cam.width, dtype=np.float64), np.arange(cam.height, dtype=np.float64))
+    tight = 0
+    for g in np.nonzero(pr["valid"])[0]:
+        a, b, c = pr["conic"][g]
+        dx, dy = u - pr["mean"][g][0], v - pr["mean"][g][1]
+        alpha = pr["opacity"][g] * np.exp(-0.5 * (a * dx * dx + c * dy * dy) - b * dx * dy)
+        hit = alpha >= 1.0 / 255.0
+        x0, y0, x1, y1 = pr["rect"][g]
+        tx, ty = (u[hit] // T).astype(int), (v[hit] // T).astype(int)
+        assert np.all((tx >= x0) & (tx <= x1) & (ty >= y0) & (ty <= y1)), g
+        if hit.any():
+            assert x0 >= tx.min() - 1 and x1 <= tx.max() + 1 and y0 >= ty.min() - 1 and y1 <= ty.max() + 1, g
+            tight += 1
+    assert tight >= 60
