@@ -32,6 +32,7 @@
 // staged and written); each block owns one contiguous chunk of the input.  No kernel waits on another
 // block; there are no spin loops.
 #include <algorithm>
+#include <atomic>
 
 #include "common.cuh"
 
@@ -978,12 +979,19 @@ struct NoAllocScratch {
     uint32_t hist[kRadix * (kNoAllocSortBlocks + 1)];  // counts, then digit totals
 };
 
+// The size the header documents (12.9 MB).
+static_assert(sizeof(NoAllocScratch) == 12878912, "update the documented scratch size");
+
 static __device__ __align__(256) unsigned char g_noalloc_scratch[sizeof(NoAllocScratch)];
 
 namespace {
 
 constexpr int kMaxDevices = 64;
-void *g_noalloc_ptr[kMaxDevices] = {};
+// Per-device cache of the array's device address.  Host threads may call
+// concurrently: a lookup is idempotent (every thread finds the same address),
+// so racing first calls only repeat it, and the atomics make the publication
+// itself well defined.
+std::atomic<void *> g_noalloc_ptr[kMaxDevices] = {};
 
 // Device address of the scratch array on the current device, looked up once
 // per device (the host-side symbol is only a stand-in for it).
@@ -992,14 +1000,42 @@ cudaError_t noalloc_scratch(NoAllocScratch **out) {
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-    if (!g_noalloc_ptr[dev]) {
-        void *p = nullptr;
+    void *p = g_noalloc_ptr[dev].load(std::memory_order_acquire);
+    if (!p) {
         e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess) return e;
-        g_noalloc_ptr[dev] = p;
+        g_noalloc_ptr[dev].store(p, std::memory_order_release);
     }
-    *out = reinterpret_cast<NoAllocScratch *>(g_noalloc_ptr[dev]);
+    *out = reinterpret_cast<NoAllocScratch *>(p);
     return cudaSuccess;
+}
+
+// Rectangles come from the caller here: a non-empty one must lie within its
+// frame's tiles (x1 < tiles_x, y1 < tiles_y), else its pairs would name
+// tiles of the next tile row or frame, or none at all.  Counts the offenders
+// into st->reserved (zeroed before the call).
+__global__ void k_noalloc_check_rects(const gs_frame *__restrict__ frames, int F, const uint2 *__restrict__ rect,
+                                      long long R, Stats *__restrict__ st) {
+    const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    bool bad = false;
+    if (r < R) {
+        const uint2 rc = rect[r];
+        if (rect_count(rc)) {
+            const gs_frame &fr = frames[frame_of_record(frames, F, r)];
+            bad = (rc.y & 0xffffu) >= (uint32_t)fr.tiles_x || (rc.y >> 16) >= (uint32_t)fr.tiles_y;
+        }
+    }
+    const unsigned n = __popc(__ballot_sync(0xffffffffu, bad));
+    if ((threadIdx.x & 31) == 0 && n) atomicAdd(&st->reserved, n);
+}
+
+// After the pair scan: with any rectangle outside its frame the call writes
+// no pair (as after an overflow) and reports UINT64_MAX pairs requested.
+__global__ void k_noalloc_gate(Stats *__restrict__ st) {
+    if (st->reserved) {
+        st->num_pairs = 0;
+        st->raw_pairs = ~0ull;
+    }
 }
 
 __global__ void k_noalloc_counts(const Stats *__restrict__ st, unsigned long long *__restrict__ out) {
@@ -1018,6 +1054,10 @@ extern "C" gs_status gs_bin_sort_noalloc(const gs_batch *b, const gs_opts *o, co
     if (!b || !o || !b->frames_dev || b->num_frames <= 0 || b->num_tiles <= 0 || o->tile != b->tile || !keys ||
         !vals || !ranges || !out_pairs || (b->num_records > 0 && (!rect || !depth)))
         return GS_ERR_INVALID_ARG;
+    // the kernels read rect and write ranges as uint2 and keys as uint64
+    auto mis = [](const void *p, uintptr_t a) { return ((uintptr_t)p & (a - 1)) != 0; };
+    if (mis(rect, 8) || mis(ranges, 8) || mis(keys, 8) || mis(out_pairs, 8) || mis(depth, 4) || mis(vals, 4))
+        return GS_ERR_INVALID_ARG;
     if (o->exact_tiles != 0) return GS_ERR_UNSUPPORTED;  // only rectangles are passed in
     if (b->pair_capacity > kNoAllocMaxPairs || b->num_records > kNoAllocMaxRecords) return GS_ERR_CAPACITY;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
@@ -1033,8 +1073,11 @@ extern "C" gs_status gs_bin_sort_noalloc(const gs_batch *b, const gs_opts *o, co
     int cur = passes & 1;  // the last pass ends in the caller's buffers
     cudaError_t e = cudaMemsetAsync(&sc->stats, 0, sizeof(Stats), s);  // counters start at zero
     if (e == cudaSuccess && emit_blocks > 0) {
+        k_noalloc_check_rects<<<(unsigned)((b->num_records + 255) / 256), 256, 0, s>>>(
+            b->frames_dev, b->num_frames, r2, b->num_records, &sc->stats);
         k_pair_count<<<emit_blocks, kEmitThreads, 0, s>>>(r2, b->num_records, nullptr, sc->emit_sums);
         k_pair_scan<<<1, 1024, 0, s>>>(sc->emit_sums, emit_blocks, b->pair_capacity, &sc->stats);
+        k_noalloc_gate<<<1, 1, 0, s>>>(&sc->stats);
         k_pair_emit<unsigned long long><<<emit_blocks, kEmitThreads, 0, s>>>(
             b->frames_dev, b->num_frames, r2, depth, b->num_records, nullptr, sc->emit_sums, &sc->stats, kb[cur],
             vb[cur]);

@@ -118,8 +118,9 @@ def test_entry_points_validate_on_the_host(lib):
     workspace, options that disagree with the batch or lie outside their
     documented ranges, and NULL required pointers with GS_ERR_INVALID_ARG
     before any device work; the allocation-free sort answers exact tiles with
-    GS_ERR_UNSUPPORTED and an oversized batch with GS_ERR_CAPACITY.  The
-    pointers below are never dereferenced."""
+    GS_ERR_UNSUPPORTED, an oversized batch with GS_ERR_CAPACITY and a
+    misaligned buffer with GS_ERR_INVALID_ARG.  The pointers below are never
+    dereferenced."""
     from paper_2403_11577_gb300 import render
     P = C.c_void_p
     INV = capi.GS_ERR_INVALID_ARG
@@ -186,3 +187,11 @@ def test_entry_points_validate_on_the_host(lib):
     big.pair_capacity = 1 << 22
     assert lib.gs_bin_sort_noalloc(C.byref(big), C.byref(opts(exact_tiles=0)), ptr, ptr, ptr, ptr, ptr, ptr,
                                    None) == capi.GS_ERR_CAPACITY
+    # rect, keys, ranges and out_pairs are read or written as 8-byte words,
+    # depth and vals as 4-byte words: a pointer off that boundary is refused
+    o0 = C.byref(opts(exact_tiles=0))
+    args = [ptr] * 6  # rect, depth, keys, vals, ranges, out_pairs
+    for i, off in ((0, 4), (1, 2), (2, 4), (3, 2), (4, 4), (5, 4)):
+        a = list(args)
+        a[i] = P(0x200000 + off)
+        assert lib.gs_bin_sort_noalloc(B, o0, *a, None) == INV, i

@@ -4,8 +4,9 @@ workspace, against the workspace entry point gs_bin_sort on the same
 records: values, tile ranges and pair counts must be identical, and the
 full 64-bit keys must be the workspace's tile keys over the depth bits of
 each pair's record (the sort is integer work, compared bit for bit), on two
-calls in a row with different inputs.  This file is collected last on
-purpose."""
+calls in a row with different inputs.  Requests beyond the pair capacity and
+rectangles outside their frame write nothing and report it, and the shared
+scratch serves the next call.  This file is collected last on purpose."""
 import numpy as np
 import pytest
 import torch
@@ -82,3 +83,76 @@ def test_bin_sort_noalloc_rejects_oversized_batches():
     with pytest.raises(capi.GsError, match="status 2"):
         capi.gs_bin_sort_noalloc(plan.batch, plan.copts, x.view(torch.int32), x.view(torch.float32)[:1], x,
                                  x.view(torch.int32), x.view(torch.int32), x[:2])
+
+
+def _run_noalloc(plan, n, cap):
+    T = plan.batch.num_tiles
+    keys = torch.full((cap,), -1, dtype=torch.int64, device="cuda")
+    vals = torch.full((cap,), -1, dtype=torch.int32, device="cuda")
+    ranges = torch.full((2 * T,), 7, dtype=torch.int32, device="cuda")
+    out = torch.full((2,), 5, dtype=torch.int64, device="cuda")
+    capi.gs_bin_sort_noalloc(plan.batch, plan.copts, plan.ws_view(capi.WS_RECT, torch.int32, 2 * n),
+                             plan.ws_view(capi.WS_DEPTH, torch.float32, n), keys, vals, ranges, out)
+    torch.cuda.synchronize()
+    return keys, vals, ranges, out.cpu().numpy().view(np.uint64)
+
+
+def _check_against_workspace(plan, n, cap):
+    plan.bin_sort()
+    P = int(plan.stats().num_pairs)
+    keys, vals, ranges, out = _run_noalloc(plan, n, cap)
+    assert out.tolist() == [P, P]
+    assert torch.equal(vals[:P], plan.ws_view(capi.WS_VALS, torch.int32, P))
+    assert torch.equal(ranges, plan.ws_view(capi.WS_RANGES, torch.int32, 2 * plan.batch.num_tiles))
+
+
+def test_bin_sort_noalloc_overflow_writes_nothing_then_recovers():
+    """More pairs requested than batch->pair_capacity (itself within the
+    fixed scratch): nothing is written, out_pairs = [0, requested] and every
+    range is empty; a call within capacity right after it is exact again."""
+    ensure_built()
+    frames_wh, counts = [(640, 480)], [3000]
+    small = _plan(frames_wh, counts, 1000)
+    n = _records(small, 21, frames_wh, counts)
+    r = small.ws_view(capi.WS_RECT, torch.int32, 2 * n).cpu().numpy().view(np.uint32).reshape(n, 2)
+    w = (r[:, 1] & 0xFFFF).astype(np.int64) - (r[:, 0] & 0xFFFF) + 1
+    h = (r[:, 1] >> 16).astype(np.int64) - (r[:, 0] >> 16) + 1
+    requested = int((np.where((w > 0) & (h > 0), w * h, 0)).sum())
+    assert requested > 1000
+    keys, vals, ranges, out = _run_noalloc(small, n, 1000)
+    assert out.tolist() == [0, requested]
+    assert int(ranges.abs().sum()) == 0
+    assert bool((vals == -1).all()) and bool((keys == -1).all())
+    big = _plan(frames_wh, counts, requested + 10)
+    n = _records(big, 21, frames_wh, counts)
+    _check_against_workspace(big, n, requested + 10)
+
+
+def test_bin_sort_noalloc_rejects_rectangles_outside_their_frame():
+    """A rectangle reaching past its frame's last tile column (or row) would
+    name tiles of the next row or frame: the call writes nothing, reports
+    out_pairs = [0, UINT64_MAX] with every range empty, and the next call
+    with valid rectangles is exact again."""
+    ensure_built()
+    frames_wh, counts = [(300, 200), (160, 96)], [500, 300]
+    cap = 1 << 16
+    for bad_field in ("x1", "y1"):
+        plan = _plan(frames_wh, counts, cap)
+        n = _records(plan, 31, frames_wh, counts)
+        rect_t = plan.ws_view(capi.WS_RECT, torch.int32, 2 * n)
+        r = rect_t.cpu().numpy().view(np.uint32).reshape(n, 2).copy()
+        good = r.copy()
+        i = int(np.nonzero(((r[:, 0] & 0xFFFF) <= (r[:, 1] & 0xFFFF)) &
+                           ((r[:, 0] >> 16) <= (r[:, 1] >> 16)))[0][0])  # a non-empty record of frame 0
+        tiles_x, tiles_y = plan.frame(0).tiles_x, plan.frame(0).tiles_y
+        if bad_field == "x1":
+            r[i, 1] = (r[i, 1] & 0xFFFF0000) | np.uint32(tiles_x)
+        else:
+            r[i, 1] = (r[i, 1] & 0xFFFF) | (np.uint32(tiles_y) << 16)
+        rect_t.copy_(torch.from_numpy(r.view(np.int32).ravel()))
+        keys, vals, ranges, out = _run_noalloc(plan, n, cap)
+        assert out.tolist() == [0, 2 ** 64 - 1], bad_field
+        assert int(ranges.abs().sum()) == 0
+        assert bool((vals == -1).all())
+        rect_t.copy_(torch.from_numpy(good.view(np.int32).ravel()))
+        _check_against_workspace(plan, n, cap)
