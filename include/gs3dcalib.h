@@ -167,8 +167,9 @@ gs_status gs_batch_init(gs_frame *frames_host, int32_t num_frames, int32_t num_g
 size_t gs_workspace_size(const gs_batch *batch);
 
 /* Byte offsets of the workspace regions (host), for tests and tools that
- * read intermediate buffers:  [0] stats, [1] pose32 (float[F][16]: R_cw
- * row-major 9, camera centre hi 3, camera centre lo 3, pad), [2] pose64
+ * read intermediate buffers:  [0] stats, [1] pose32 (float[F][32]: R_cw
+ * row-major 9 (high parts), camera centre hi 3, camera centre lo 3, pad,
+ * R_cw row-major 9 (low parts: R_cw - high part, rounded), pad 7), [2] pose64
  * (double[F][32]), [3] rect (uint32[R][2]: x0 | y0 << 16, x1 | y1 << 16,
  * inclusive tile coordinates, empty as x0 > x1), [4] depth (float[R]),
  * [5] splat (float4[R][2]: (mean_x, mean_y, A, B), (C, F, rx, ry), the
@@ -233,8 +234,11 @@ gs_status gs_pose_compose(const gs_batch *batch, const double *traj_t, const dou
  * Gaussian) record, the camera-frame centre X^n = (T^n)^-1 X, the
  * camera-frame covariance R^n^-1 Sigma R^n^-T, the 2D mean, the conic
  * (inverse of J Sigma_c J^T + lowpass I), the opacity, and the rectangle of
- * tiles where alpha can reach alpha_min.  Gaussians with depth <= near_z
- * or opacity < alpha_min are culled (empty rectangle).
+ * tiles where alpha can reach alpha_min.  The camera-frame centre is formed
+ * in float-float arithmetic, and the depth and the 2D mean are rounded once:
+ * the depth is the float nearest to the exact depth, the depth order's key.
+ * Gaussians with that depth <= near_z or opacity < alpha_min are culled
+ * (empty rectangle).
  *   X[N][3]        centres, world frame (float; fixed LiDAR points, Sec. III-B)
  *   quat[N][4]     rotation r, any non-zero norm (normalised inside)
  *   log_scale[N][3] s = exp(log_scale), clamped to scale_max
@@ -244,14 +248,19 @@ gs_status gs_project(const gs_batch *batch, const float *X, const float *quat,
                      const float *log_scale, const float *logit_opacity, const gs_opts *opts,
                      void *ws_dev, void *stream);
 
-/* Tile binning and depth ordering for Phi (Eq. 5): every record emits one
- * pair per tile of its rectangle, value = Gaussian index within its scene;
- * the pairs end up in the order of the key (global tile << 32) | float bits
+/* Tile binning and depth ordering for Phi (Eq. 5).  Each record emits one
+ * pair per tile it can reach, value = Gaussian index within its scene:
+ *   opts->exact_tiles != 0 (the default): only the tiles of its rectangle
+ *     that its alpha >= alpha_min ellipse can meet (in each tile row, a run
+ *     between the ellipse's x-extremes, tested with a margin above float32
+ *     rounding, so the rendered image is the same as with whole rectangles);
+ *   opts->exact_tiles == 0: every tile of its rectangle.
+ * The pairs end up in the order of the key (global tile << 32) | float bits
  * of the depth, equal keys in record order (a stable sort), and each tile's
- * [start, end) range is found.  The workspace keys region holds each sorted
- * pair's global tile (the high half of that key).  If the pairs exceed
- * pair_capacity, GS_DEV_PAIR_OVERFLOW is set and the batch is treated as
- * having no pairs. */
+ * [start, end) range is found, plus a heavy-first order of the tiles for
+ * the render.  The workspace keys region holds each sorted pair's global
+ * tile (the high half of that key).  If the pairs exceed pair_capacity,
+ * GS_DEV_PAIR_OVERFLOW is set and the batch is treated as having no pairs. */
 gs_status gs_bin_sort(const gs_batch *batch, const gs_opts *opts, void *ws_dev, void *stream);
 
 /* Phi (Eq. 5): front-to-back alpha compositing per pixel over its tile's
@@ -326,7 +335,7 @@ gs_status gs_render_bwd(const gs_batch *batch, const float *X, const float *quat
 gs_status gs_pose_grad(const gs_batch *batch, const double *ext, void *ws_dev, double *d_ext,
                        double *d_delta, double *d_xi, int32_t accumulate, void *stream);
 
-/* ------------------------------------------------- no allocation at all -- */
+/* ------------------------------------------- hash-grid attribute model -- */
 
 /* The attribute model F(X | Theta) of Sec. III-C: the Instant-NGP
  * multiresolution hash encoding of a Gaussian's centre, then an MLP
@@ -393,6 +402,8 @@ size_t gs_voxel_scratch_size(int64_t n);
 gs_status gs_voxel_downsample(const float *X, int64_t n, float voxel, int32_t *out_index, uint64_t *out_count,
                               void *scratch_dev, void *stream);
 
+/* ------------------------------------------------- no allocation at all -- */
+
 /* The tile binning and depth sort of gs_bin_sort for callers that cannot
  * allocate device memory: for instance a host framework that owns every
  * device buffer and hands a plugin only its inputs and outputs, or a
@@ -407,17 +418,24 @@ gs_status gs_voxel_downsample(const float *X, int64_t n, float voxel, int32_t *o
  * high halves are gs_bin_sort's workspace keys; the inputs and outputs are
  * the caller's buffers instead of workspace regions:
  *   rect[R][2]   uint32 rectangles (x0 | y0 << 16, x1 | y1 << 16, inclusive
- *                tiles; empty when x0 > x1), R = batch->num_records
- *   depth[R]     float camera depths (the key's low 32 bits)
- *   keys[pair_capacity], vals[pair_capacity]  sorted pairs (output)
- *   ranges[num_tiles][2]  [start, end) of each tile (output)
- *   out_pairs[2] (device, uint64): pairs written and pairs requested; if
- *                the request exceeds batch->pair_capacity nothing is written
- *                and out_pairs[0] = 0.
- * Scratch: one fixed array of about 12.6 MB compiled into the library (every
- * GPU that loads the library holds it until the process exits), sized for at
- * most 2^20 pairs (batch->pair_capacity) and 2^22 records; larger batches
- * return GS_ERR_CAPACITY without enqueuing anything.  No cudaMalloc,
+ *                tiles; empty when x0 > x1), R = batch->num_records,
+ *                8-byte aligned.  A non-empty rectangle must lie within its
+ *                frame: x1 < tiles_x and y1 < tiles_y (tile rows counted
+ *                from the frame's row0).  If any does not, nothing is
+ *                written: out_pairs = {0, UINT64_MAX} and ranges are zero.
+ *   depth[R]     float camera depths (the key's low 32 bits), 4-byte aligned
+ *   keys[pair_capacity] (8-byte aligned), vals[pair_capacity] (4-byte
+ *                aligned)  sorted pairs (output)
+ *   ranges[num_tiles][2]  [start, end) of each tile (output), 8-byte aligned
+ *   out_pairs[2] (device, uint64, 8-byte aligned): pairs written and pairs
+ *                requested; if the request exceeds batch->pair_capacity
+ *                nothing is written, out_pairs[0] = 0 and ranges are zero.
+ * A misaligned pointer returns GS_ERR_INVALID_ARG without enqueuing anything.
+ * Scratch: one fixed array of 12,878,912 bytes (12.9 MB, 12.3 MiB) compiled
+ * into the library (every GPU that loads the library holds it until the
+ * process exits), sized for at most 2^20 pairs (batch->pair_capacity) and
+ * 2^22 records; larger batches return GS_ERR_CAPACITY without enqueuing
+ * anything.  No cudaMalloc,
  * cudaFree or allocating library routine is called.
  * The first call on each device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call

@@ -32,7 +32,19 @@ class OrCam(C.Structure):
                 ("cx", C.c_double), ("cy", C.c_double)]
 
 
-FLAG_ALPHA_EDGE, FLAG_STOP_EDGE, FLAG_DEPTH_TIE, FLAG_POWER_EDGE, FLAG_NEAR_EDGE = 1, 2, 4, 8, 16
+# Per-pixel flags (see gs_oracle.c): the renderer decides in float32, the
+# oracle in FP64 with a bound on the float32 evaluation's error.
+#   FLAG_BRANCH: an ambiguous skip or stop decision; every outcome is given
+#     as an alternative result (render(..., alternatives=True)), and the
+#     pixel's gradient depends on the outcome.
+#   FLAG_CLAMP_EDGE: an alpha within the bound of alpha_max (colour
+#     continuous, gradient not).
+#   FLAG_DEPTH_TIE / FLAG_NEAR_EDGE / FLAG_BRANCH_LIMIT: the depth order or
+#     the near-plane culling is not decided in float32, or more outcomes than
+#     MAX_BRANCHES: no outcome set is given (FLAGS_UNDECIDED).
+FLAG_BRANCH, FLAG_CLAMP_EDGE, FLAG_DEPTH_TIE, FLAG_NEAR_EDGE, FLAG_BRANCH_LIMIT = 1, 2, 4, 16, 32
+FLAGS_UNDECIDED = FLAG_DEPTH_TIE | FLAG_NEAR_EDGE | FLAG_BRANCH_LIMIT
+MAX_BRANCHES = 16
 
 
 @dataclass
@@ -115,10 +127,19 @@ def project(scene, cam, R_cw, t_cw, opts: Opts = Opts(), tile: int = 16):
     out = dict(valid=np.zeros(n, np.int32), depth=np.zeros(n), mean=np.zeros((n, 2)),
                conic=np.zeros((n, 3)), opacity=np.zeros(n), extent=np.zeros((n, 2)),
                cov=np.zeros((n, 3)), rect=np.zeros((n, 4), np.int32))
+    b = np.zeros((n, 7))
     lib().or_project(C.c_int(n), _p(X), _p(q), _p(ls), _p(lo), C.byref(_cam(cam)),
                      _p(_f64(R_cw)), _p(_f64(t_cw)), C.byref(opts.c()), C.c_int(tile),
                      _p(out["valid"]), _p(out["depth"]), _p(out["mean"]), _p(out["conic"]),
-                     _p(out["opacity"]), _p(out["extent"]), _p(out["cov"]), _p(out["rect"]))
+                     _p(out["opacity"]), _p(out["extent"]), _p(out["cov"]), _p(out["rect"]), _p(b))
+    # depth key (float32) and whether its rounding / the near-plane culling
+    # is undecided; bounds of the float32 mean, conic and log2 opacity
+    out["zkey"] = b[:, 0].astype(np.float32)
+    out["zamb"] = b[:, 1] != 0
+    out["near_undecided"] = b[:, 2] != 0
+    out["mean_err"] = b[:, 3:5]
+    out["conic_err"] = b[:, 5]
+    out["logop_err"] = b[:, 6]
     return out
 
 
@@ -129,20 +150,28 @@ def _pix(pixels):
     return pix, len(pix)
 
 
-def render_pose(scene, cam, R_cw, t_cw, opts: Opts = Opts(), pixels=None):
+def render_pose(scene, cam, R_cw, t_cw, opts: Opts = Opts(), pixels=None, alternatives=False):
     """Render one frame for a given world-to-camera pose.
 
-    Returns rgb [P,3], T_final [P], last [P] (Gaussian id or -1), flags [P];
-    P = all pixels in row-major order, or the given (u, v) pixels."""
+    Returns rgb [P,3], T_final [P], last [P] (Gaussian id or -1), flags [P]
+    for the FP64 outcome of every decision; P = all pixels in row-major
+    order, or the given (u, v) pixels.  With alternatives=True a fifth item
+    (nalt [P], alt [P, MAX_BRANCHES-1, 5]) gives, per pixel, the other
+    outcomes of its ambiguous decisions as (r, g, b, T_final, last)."""
     X, q, ls, lo, rgb = _gauss(scene)
     pix, npix = _pix(pixels)
     P = npix if pix is not None else cam.width * cam.height
     out_rgb, out_T = np.zeros((P, 3)), np.zeros(P)
     out_last, out_flags = np.zeros(P, np.int32), np.zeros(P, np.int32)
+    nalt = np.zeros(P, np.int32) if alternatives else None
+    alt = np.zeros((P, MAX_BRANCHES - 1, 5)) if alternatives else None
     lib().or_render(C.c_int(scene.n), _p(X), _p(q), _p(ls), _p(lo), _p(rgb), C.byref(_cam(cam)),
                     _p(_f64(R_cw)), _p(_f64(t_cw)), C.byref(opts.c()), C.c_int(npix),
                     _p(pix) if pix is not None else None,
-                    _p(out_rgb), _p(out_T), _p(out_last), _p(out_flags))
+                    _p(out_rgb), _p(out_T), _p(out_last), _p(out_flags),
+                    _p(nalt) if alternatives else None, _p(alt) if alternatives else None)
+    if alternatives:
+        return out_rgb, out_T, out_last, out_flags, (nalt, alt)
     return out_rgb, out_T, out_last, out_flags
 
 
@@ -157,11 +186,11 @@ def _frame_pixels(frame, pixels):
     return np.stack([u.ravel(), v.ravel()], 1)
 
 
-def render(scene, frame, ext, delta, opts: Opts = Opts(), pixels=None):
+def render(scene, frame, ext, delta, opts: Opts = Opts(), pixels=None, alternatives=False):
     """Render a frame at the pose of Eq. 1 for extrinsic ext (omega, t) and
     time offset delta (a cropped frame: its rows row0 .. H-1)."""
     R, t = frame_pose(scene, ext, delta, frame.timestamp)
-    return render_pose(scene, frame.camera, R, t, opts, _frame_pixels(frame, pixels))
+    return render_pose(scene, frame.camera, R, t, opts, _frame_pixels(frame, pixels), alternatives)
 
 
 def backward(scene, frame, ext, delta, dL_dC, opts: Opts = Opts(), pixels=None):

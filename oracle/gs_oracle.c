@@ -56,14 +56,36 @@ typedef struct {
     double fx, fy, cx, cy;
 } or_cam;
 
-/* per-pixel ambiguity flags: where FP32 and FP64 may legitimately disagree */
+/* Per-pixel flags.  The renderer takes its discrete decisions (skip,
+ * stop, clamp, order) on float32 values; the oracle decides in FP64 and
+ * bounds how far the float32 evaluation can lie from the exact value (see
+ * "float32 decision bounds" below).  A decision whose exact value lies
+ * within that bound of its threshold is ambiguous: both outcomes are
+ * correct results of the method in float32.
+ *   OR_FLAG_BRANCH       an ambiguous skip (alpha_min, exponent > 0) or stop
+ *                        (t_min) decision: every outcome is rendered as an
+ *                        alternative result (or_render's out_alt); the
+ *                        pixel's gradient depends on the outcome.
+ *   OR_FLAG_CLAMP_EDGE   a composited Gaussian's alpha lies within the bound
+ *                        of alpha_max: the colour is continuous there, its
+ *                        gradient is not.
+ *   OR_FLAG_DEPTH_TIE    two consecutive contributors whose float32 depth
+ *                        keys are at most one ulp apart, one of them with an
+ *                        exact depth within the bound of a float32 rounding
+ *                        boundary: their order is not decided.
+ *   OR_FLAG_NEAR_EDGE    a Gaussian whose float32 depth key is not decided
+ *                        at the near plane would contribute.
+ *   OR_FLAG_BRANCH_LIMIT more than OR_MAX_BRANCHES outcomes. */
 enum {
-    OR_FLAG_ALPHA_EDGE = 1,   /* some alpha within 1e-4 (rel.) of alpha_min or alpha_max */
-    OR_FLAG_STOP_EDGE = 2,    /* T*(1-alpha) within 1e-3 (rel.) of t_min */
-    OR_FLAG_DEPTH_TIE = 4,    /* two consecutive contributors within 8 float32 ulps in depth */
-    OR_FLAG_POWER_EDGE = 8,   /* a contributing exponent within 1e-6 (rel. to its terms) of zero */
-    OR_FLAG_NEAR_EDGE = 16,   /* a Gaussian within 1e-5 m of the near plane would contribute */
+    OR_FLAG_BRANCH = 1,
+    OR_FLAG_CLAMP_EDGE = 2,
+    OR_FLAG_DEPTH_TIE = 4,
+    OR_FLAG_NEAR_EDGE = 16,
+    OR_FLAG_BRANCH_LIMIT = 32,
 };
+
+#define OR_MAX_BRANCHES 16  /* outcomes per pixel: the FP64 one and up to 15 alternatives */
+#define OR_MAX_DECISIONS 48 /* ambiguous decisions per pass that can be enumerated */
 
 /* ------------------------------------------------------ 3x3 linear algebra */
 
@@ -257,7 +279,12 @@ void or_frame_pose(const double *traj_t, const double *traj_p, const double *tra
 
 typedef struct {
     int valid;          /* in front of the near plane and opacity >= alpha_min */
-    int near_edge;      /* centre within 1e-5 m of the near plane */
+    int near_edge;      /* the near-plane culling is not decided in float32 */
+    float zkey;         /* depth rounded to float32: the depth order's key */
+    int zamb;           /* the exact depth lies within the bound of a float32 rounding boundary */
+    double dm[2];       /* bound on the float32 2D mean's error, px */
+    double kq;          /* bound on the conic's share of the float32 exponent error, per unit of |e2| */
+    double dF;          /* bound on the float32 log2 opacity's error */
     double X[3], pc[3];
     double q[4], qn, Rg[9], s[3];
     int s_clamped[3];
@@ -272,6 +299,59 @@ typedef struct {
     double extent[2];   /* half-widths of the alpha >= alpha_min ellipse's box */
 } or_proj;
 
+/* ------------------------------------------- float32 decision bounds --
+ *
+ * The renderer evaluates, per pixel and Gaussian, the base-2 exponent
+ *   e2 = A dx^2 + B dx dy + C dy^2,  e = e2 + F   (A = -a/2 log2 e,
+ *   B = -b log2 e, C = -c/2 log2 e, (a, b, c) the conic, F = log2 opacity,
+ *   dx = u - mean_x, dy = v - mean_y)
+ * in float32 from float32 projections, and decides: skip if e2 > 0, skip if
+ * e < log2 alpha_min, clamp alpha = 2^e at alpha_max, stop if T (1 - alpha)
+ * < t_min.  These bounds follow the rounding of that evaluation (u = 2^-24
+ * per operation, first order):
+ *   mean: rounded once from fx x/z + cx (float-float before the rounding),
+ *     so off by half a float32 spacing at the mean, plus the rounding of the
+ *     intrinsics to float32 and a far smaller float-float term;
+ *   conic: about twenty roundings, each relative to the terms of the 2D
+ *     covariance J Sigma_c J^T, whose size is |J|^2 lambda_max(Sigma); a
+ *     covariance error d(cov) moves the exponent by (Q d)^T d(cov) (Q d)
+ *     <= |d(cov)| |e2| / lambda_min(cov) (Q the conic), so that share is
+ *     16 u (1 + |J|^2 lambda_max(Sigma) / lambda_min(cov)) |e2|, plus 4 u
+ *     times the size of e2's terms for the rounding of A, B, C themselves;
+ *   F: log2 of a float32 sigmoid, within 2^-20 (1 + |F|);
+ *   the exponent itself: six roundings relative to its terms, plus the
+ *     offset dx when u - mean_x is not exact;
+ *   2^e: the hardware approximation, relative error below 2^-20;
+ *   thresholds: log2 of float32 alpha_min within 2^-19; alpha_max and t_min
+ *     rounded to float32. */
+#define OR_U32 0x1p-24
+
+static double f32_spacing(double x) { /* spacing of float32 values just above |x| */
+    float f = (float)fabs(x);
+    return (double)nextafterf(f, INFINITY) - (double)f;
+}
+
+static void decision_bounds(or_proj *P, const or_cam *cam, const or_opts *o) {
+    (void)o;
+    double z = P->pc[2];
+    double dn = sqrt(P->pc[0] * P->pc[0] + P->pc[1] * P->pc[1] + z * z) / z;
+    double f[2] = {cam->fx, cam->fy}, c[2] = {cam->cx, cam->cy};
+    for (int i = 0; i < 2; i++) {
+        double r = P->pc[i] / z;
+        P->dm[i] = 0.5 * f32_spacing(P->mean[i]) + fabs(f[i] - (double)(float)f[i]) * fabs(r)
+                 + fabs(c[i] - (double)(float)c[i])
+                 + 0x1p-36 * (fabs(P->mean[i]) + fabs(f[i]) * (1.0 + fabs(r)) * dn + 1.0);
+    }
+    double smax = P->s[0] > P->s[1] ? P->s[0] : P->s[1];
+    if (P->s[2] > smax) smax = P->s[2];
+    double J2 = P->J[0] * P->J[0] + P->J[2] * P->J[2] + P->J[4] * P->J[4] + P->J[5] * P->J[5];
+    double h = 0.5 * (P->cov[0] + P->cov[2]);
+    double r = sqrt(0.25 * (P->cov[0] - P->cov[2]) * (P->cov[0] - P->cov[2]) + P->cov[1] * P->cov[1]);
+    double lmin = h - r;
+    P->kq = 16.0 * OR_U32 * (1.0 + J2 * smax * smax / lmin);
+    P->dF = 0x1p-20 * (1.0 + fabs(log2(P->opacity)));
+}
+
 static void project_one(const double *X, const double *q, const double *log_s, double logit_o,
                         const or_cam *cam, const double *R_cw, const double *t_cw,
                         const or_opts *o, or_proj *P) {
@@ -280,7 +360,24 @@ static void project_one(const double *X, const double *q, const double *log_s, d
     m3_vec(R_cw, P->X, P->pc);
     for (int i = 0; i < 3; i++) P->pc[i] += t_cw[i];
     double z = P->pc[2];
-    P->near_edge = fabs(z - o->near_z) < 1e-5;
+    /* The depth order and the near-plane culling are decided on the depth
+     * rounded to float32 (the renderer's precision for its sort key).  The
+     * kernel forms the depth in float-float arithmetic and rounds it once;
+     * its value and this one differ by far less than 2^-40 (|X| + 2|t| + |z|),
+     * so the two roundings can differ only within that distance of a
+     * rounding boundary. */
+    P->zkey = (float)z;
+    {
+        double eps = 0x1p-40 * (fabs(X[0]) + fabs(X[1]) + fabs(X[2]) + 2.0 * (fabs(t_cw[0]) + fabs(t_cw[1]) + fabs(t_cw[2])) + fabs(z));
+        float k = P->zkey;
+        double below = 0.5 * ((double)k + (double)nextafterf(k, -INFINITY));
+        double above = 0.5 * ((double)k + (double)nextafterf(k, INFINITY));
+        P->zamb = (z - below < eps) || (above - z < eps);
+        float near = (float)o->near_z;
+        float other = z - below < eps ? nextafterf(k, -INFINITY) : nextafterf(k, INFINITY);
+        P->near_edge = P->zamb && ((k > near) != (other > near));
+    }
+    int in_front = P->zkey > (float)o->near_z;
     /* Gaussian covariance Sigma = R S S^T R^T in the world frame */
     double n2 = 0;
     for (int i = 0; i < 4; i++) { P->q[i] = q[i]; n2 += P->q[i] * P->q[i]; }
@@ -305,7 +402,7 @@ static void project_one(const double *X, const double *q, const double *log_s, d
     m3_transpose(R_cw, Rt);
     m3_mul(T1, Rt, P->Sigc);
     P->opacity = 1.0 / (1.0 + exp(-logit_o));
-    if (z <= o->near_z && !P->near_edge) return;
+    if (!in_front && !P->near_edge) return;
     if (z <= 1e-9) return;
     /* EWA: Jacobian of (x,y,z) -> (fx x/z + cx, fy y/z + cy), evaluated at
      * x/z and y/z limited to the widened field of view (3DGS's EWA), which
@@ -348,23 +445,29 @@ static void project_one(const double *X, const double *q, const double *log_s, d
     P->conic[2] = P->cov[0] / det;
     P->mean[0] = cam->fx * x / z + cam->cx;
     P->mean[1] = cam->fy * y / z + cam->cy;
+    decision_bounds(P, cam, o);
     if (P->opacity < o->alpha_min) return;
     /* alpha >= alpha_min  <=>  d^T conic d <= 2 ln(opacity / alpha_min); the
      * box of that ellipse has half-widths sqrt(k cov_xx), sqrt(k cov_yy). */
     double kk = o->alpha_min > 0 ? 2.0 * log(P->opacity / o->alpha_min) : INFINITY;
     P->extent[0] = sqrt(kk * P->cov[0]);
     P->extent[1] = sqrt(kk * P->cov[2]);
-    P->valid = z > o->near_z;
+    P->valid = in_front;
 }
 
 /* Exported: projection of all Gaussians of a scene for one camera pose.
  * out_* arrays have N rows; rect is [N][4] = (x0,y0,x1,y1) in tiles of
- * size `tile`, inclusive, clamped to the image, empty as x0 > x1. */
+ * size `tile`, inclusive, clamped to the image, empty as x0 > x1.
+ * out_bounds (optional) is [N][7]: the float32 depth key, whether its
+ * rounding is undecided (1/0), whether the near-plane culling is undecided
+ * (1/0), the float32 mean's error bounds (x, y, px), the conic's share of
+ * the exponent error per unit of |e2|, the log2 opacity's error bound
+ * (see "float32 decision bounds"). */
 void or_project(int N, const double *X, const double *q, const double *log_s, const double *logit_o,
                 const or_cam *cam, const double *R_cw, const double *t_cw, const or_opts *o,
                 int tile, int32_t *out_valid, double *out_depth, double *out_mean,
                 double *out_conic, double *out_opacity, double *out_extent, double *out_cov,
-                int32_t *out_rect) {
+                int32_t *out_rect, double *out_bounds) {
     int tx = (cam->width + tile - 1) / tile, ty = (cam->height + tile - 1) / tile;
     for (int g = 0; g < N; g++) {
         or_proj P;
@@ -375,6 +478,11 @@ void or_project(int N, const double *X, const double *q, const double *log_s, co
         for (int i = 0; i < 3; i++) { out_conic[3 * g + i] = P.conic[i]; out_cov[3 * g + i] = P.cov[i]; }
         out_opacity[g] = P.opacity;
         out_extent[2 * g] = P.extent[0]; out_extent[2 * g + 1] = P.extent[1];
+        if (out_bounds) {
+            double *b = out_bounds + 7 * (size_t)g;
+            b[0] = P.zkey; b[1] = P.zamb; b[2] = P.near_edge;
+            b[3] = P.dm[0]; b[4] = P.dm[1]; b[5] = P.kq; b[6] = P.dF;
+        }
         int x0 = 1, y0 = 1, x1 = 0, y1 = 0;
         if (P.valid && !(isfinite(P.extent[0]) && isfinite(P.extent[1]))) {
             x0 = 0; y0 = 0; x1 = tx - 1; y1 = ty - 1;
@@ -396,7 +504,9 @@ void or_project(int N, const double *X, const double *q, const double *log_s, co
 
 /* ---------------------------------------------------------- compositing */
 
-typedef struct { double z; int g; } zkey;
+/* Depth order (Eq. 5 composites in depth order): by the float32 depth key,
+ * equal keys by Gaussian index. */
+typedef struct { float z; int g; } zkey;
 
 static int cmp_zkey(const void *a, const void *b) {
     const zkey *x = a, *y = b;
@@ -424,7 +534,7 @@ static void frame_state(or_frame_state *S, int N, const double *X, const double 
     S->n_edge = 0;
     for (int g = 0; g < N; g++) {
         project_one(X + 3 * g, q + 4 * g, log_s + 3 * g, logit_o[g], cam, R_cw, t_cw, o, &S->P[g]);
-        if (S->P[g].valid) { keys[S->M].z = S->P[g].pc[2]; keys[S->M].g = g; S->M++; }
+        if (S->P[g].valid) { keys[S->M].z = S->P[g].zkey; keys[S->M].g = g; S->M++; }
         if (S->P[g].near_edge) S->edge_ids[S->n_edge++] = g;
     }
     qsort(keys, S->M, sizeof(zkey), cmp_zkey);
@@ -450,11 +560,6 @@ static void eval_alpha(const or_proj *P, double u, double v, const or_opts *o,
     *alpha = *clamped ? o->alpha_max : a;
 }
 
-static double f32_ulp(double z) {
-    float f = (float)z;
-    return (double)(nextafterf(f, INFINITY) - f);
-}
-
 /* Blend list of one pixel: the Gaussians that are composited, in order, with
  * their alpha and the transmittance in front of each. */
 typedef struct {
@@ -464,33 +569,83 @@ typedef struct {
     int *clamped;
     double T_final;
     int flags;
+    int ndec;                         /* ambiguous decisions met by this pass */
 } or_blend;
 
-static void blend_pixel(const or_frame_state *S, double u, double v, const or_opts *o, or_blend *B) {
+/* The outcome of each ambiguous decision of a pass, in the order met: the
+ * first n are given (1 = the outcome opposite to FP64's), the rest take the
+ * FP64 outcome. */
+typedef struct {
+    int n;
+    unsigned char flip[OR_MAX_DECISIONS];
+} or_path;
+
+/* Take an ambiguous decision: the FP64 outcome, or its opposite where the
+ * path says so. */
+static int decide(or_blend *B, const or_path *path, int fp64_outcome) {
+    int j = B->ndec;
+    if (j >= OR_MAX_DECISIONS) { B->flags |= OR_FLAG_BRANCH_LIMIT; return fp64_outcome; }
+    B->ndec++;
+    B->flags |= OR_FLAG_BRANCH;
+    return (j < path->n && path->flip[j]) ? !fp64_outcome : fp64_outcome;
+}
+
+/* One front-to-back pass over the pixel's depth-ordered Gaussians (Eq. 5,
+ * with the skip/stop rules of the readings in or_opts), taking every
+ * ambiguous decision as `path` says. */
+static void blend_pixel_path(const or_frame_state *S, double u, double v, const or_opts *o, const or_path *path,
+                             or_blend *B) {
     B->n = 0;
     B->flags = 0;
+    B->ndec = 0;
     double T = 1.0;
-    double zprev = -1.0;
+    double eT = 0.0;                  /* bound on the float32 transmittance's relative error */
+    float kprev = 0.f;
+    int aprev = 0, have_prev = 0;
+    const double log2e = 1.0 / log(2.0);
+    const double lmin = o->alpha_min > 0 ? log2(o->alpha_min) : -INFINITY;
+    const double lmax = log2(o->alpha_max);
+    const double amax32 = (double)(float)o->alpha_max, tmin32 = (double)(float)o->t_min;
     for (int i = 0; i < S->M; i++) {
         const or_proj *P = &S->P[S->order[i]];
         double dx, dy, power, G, alpha;
         int clamped;
         eval_alpha(P, u, v, o, &dx, &dy, &power, &G, &alpha, &clamped);
-        if (power > 0) continue;
-        double araw = P->opacity * G;
-        if (o->alpha_min > 0 && fabs(araw - o->alpha_min) < 1e-4 * o->alpha_min) B->flags |= OR_FLAG_ALPHA_EDGE;
-        if (fabs(araw - o->alpha_max) < 1e-4 * o->alpha_max) B->flags |= OR_FLAG_ALPHA_EDGE;
-        if (alpha < o->alpha_min) continue;
-        {   /* a float32 rounding of the exponent can only turn it positive
-             * when it is within a few ulps of zero relative to its terms */
-            double mag = 0.5 * (P->conic[0] * dx * dx + P->conic[2] * dy * dy) + fabs(P->conic[1] * dx * dy);
-            if (power > -1e-6 * mag) B->flags |= OR_FLAG_POWER_EDGE;
-        }
+        /* the exponent in base 2 and the bound on its float32 evaluation */
+        double A = -0.5 * log2e * P->conic[0], Bc = -log2e * P->conic[1], C = -0.5 * log2e * P->conic[2];
+        double e2 = power * log2e, F = log2(P->opacity), e = e2 + F;
+        double mag = fabs(A) * dx * dx + fabs(Bc * dx * dy) + fabs(C) * dy * dy;
+        double gx = fabs(2.0 * A * dx + Bc * dy), gy = fabs(Bc * dx + 2.0 * C * dy);
+        double eps2 = gx * (P->dm[0] + OR_U32 * fabs(dx)) + gy * (P->dm[1] + OR_U32 * fabs(dy))
+                    + P->kq * fabs(e2) + 10.0 * OR_U32 * mag;
+        double eps = eps2 + OR_U32 * (fabs(e2) + fabs(F)) + P->dF;
+        /* skip where the exponent is positive (only by rounding: the form is
+         * negative definite) */
+        int skip = power > 0;
+        if (e2 + eps2 > 0) skip = decide(B, path, skip);
+        if (skip) continue;
+        /* skip alpha < alpha_min */
+        skip = alpha < o->alpha_min;
+        if (o->alpha_min > 0 && fabs(e - lmin) <= eps + 0x1p-19) skip = decide(B, path, skip);
+        if (skip) continue;
+        /* the clamp at alpha_max is continuous in colour, not in gradient */
+        int near_clamp = o->alpha_max < 1.0 && fabs(e - lmax) <= eps + 0x1p-22;
+        /* float32 alpha's relative error, then (1 - alpha)'s */
+        double ea = clamped && !near_clamp ? fabs(amax32 - o->alpha_max) / o->alpha_max
+                                           : log(2.0) * eps + 0x1p-20;
+        double e1 = alpha * ea / (1.0 - alpha) + OR_U32;
         double testT = T * (1.0 - alpha);
-        if (o->t_min > 0 && fabs(testT - o->t_min) < 1e-3 * o->t_min) B->flags |= OR_FLAG_STOP_EDGE;
-        if (zprev >= 0 && P->pc[2] - zprev < 8.0 * f32_ulp(P->pc[2])) B->flags |= OR_FLAG_DEPTH_TIE;
-        zprev = P->pc[2];
-        if (testT < o->t_min) break;
+        int stop = testT < o->t_min;
+        if (o->t_min > 0 && fabs(testT - o->t_min) <= testT * (eT + e1 + 2.0 * OR_U32) + fabs(tmin32 - o->t_min))
+            stop = decide(B, path, stop);
+        if (stop) break;
+        if (near_clamp) B->flags |= OR_FLAG_CLAMP_EDGE;
+        /* consecutive contributors whose float32 order is not decided */
+        if (have_prev && (aprev || P->zamb) && (double)P->zkey - (double)kprev <= f32_spacing(P->zkey))
+            B->flags |= OR_FLAG_DEPTH_TIE;
+        kprev = P->zkey;
+        aprev = P->zamb;
+        have_prev = 1;
         int k = B->n++;
         B->g[k] = S->order[i];
         B->alpha[k] = alpha;
@@ -500,6 +655,7 @@ static void blend_pixel(const or_frame_state *S, double u, double v, const or_op
         B->dy[k] = dy;
         B->clamped[k] = clamped;
         T = testT;
+        eT += e1 + 2.0 * OR_U32;
     }
     B->T_final = T;
     for (int e = 0; e < S->n_edge; e++) {
@@ -510,6 +666,13 @@ static void blend_pixel(const or_frame_state *S, double u, double v, const or_op
         eval_alpha(P, u, v, o, &dx, &dy, &power, &G, &alpha, &clamped);
         if (power <= 0 && alpha >= o->alpha_min) B->flags |= OR_FLAG_NEAR_EDGE;
     }
+}
+
+/* The FP64 pass (every ambiguous decision takes its FP64 outcome). */
+static void blend_pixel(const or_frame_state *S, double u, double v, const or_opts *o, or_blend *B) {
+    or_path none;
+    none.n = 0;
+    blend_pixel_path(S, u, v, o, &none, B);
 }
 
 static void blend_alloc(or_blend *B, int M) {
@@ -527,33 +690,94 @@ static void blend_free(or_blend *B) {
     free(B->g); free(B->clamped); free(B->alpha); free(B->T); free(B->G); free(B->dx); free(B->dy);
 }
 
+/* The outcome of a pass: rgb = sum_i c_i alpha_i T_i + T_final bg, T_final,
+ * last composited Gaussian (-1 if none). */
+static void blend_result(const or_blend *B, const double *rgb, const or_opts *o, double *out5) {
+    double C[3] = {0, 0, 0};
+    for (int k = 0; k < B->n; k++)
+        for (int ch = 0; ch < 3; ch++) C[ch] += rgb[3 * B->g[k] + ch] * B->alpha[k] * B->T[k];
+    for (int ch = 0; ch < 3; ch++) out5[ch] = C[ch] + B->T_final * o->bg[ch];
+    out5[3] = B->T_final;
+    out5[4] = B->n > 0 ? B->g[B->n - 1] : -1;
+}
+
+typedef struct {
+    const or_frame_state *S;
+    const double *rgb;
+    const or_opts *o;
+    double u, v;
+    or_blend *B;
+    int count;                 /* outcomes found */
+    double out[OR_MAX_BRANCHES][5];
+    int flags;
+} or_branches;
+
+/* Every outcome of the pixel's ambiguous decisions, depth first: run the
+ * pass for `path` (its later decisions at their FP64 outcome), keep its
+ * result, then for each later decision it met, the path that flips it. */
+static void explore(or_branches *X, const or_path *path) {
+    if (X->count >= OR_MAX_BRANCHES) { X->flags |= OR_FLAG_BRANCH_LIMIT; return; }
+    blend_pixel_path(X->S, X->u, X->v, X->o, path, X->B);
+    blend_result(X->B, X->rgb, X->o, X->out[X->count++]);
+    X->flags |= X->B->flags;
+    int ndec = X->B->ndec;
+    for (int j = path->n; j < ndec && j < OR_MAX_DECISIONS; j++) {
+        or_path child = *path;
+        for (int k = path->n; k < j; k++) child.flip[k] = 0;
+        child.flip[j] = 1;
+        child.n = j + 1;
+        explore(X, &child);
+    }
+}
+
 /* Exported: render the requested pixels of one frame.
  * pix: [npix][2] integer pixel coordinates (u, v), or NULL for all pixels in
  * row-major order.  Pixel (u, v) is the image point (u, v) in the same
  * coordinates as fx x/z + cx (pinhole, OpenCV convention).
  * Outputs per requested pixel: rgb[3] = sum_i c_i alpha_i T_i + T_final bg,
- * T_final, last = id of the last composited Gaussian (-1 if none), flags. */
+ * T_final, last = id of the last composited Gaussian (-1 if none), flags
+ * (OR_FLAG_*), all for the FP64 outcome of every decision.  If out_alt is
+ * given, out_nalt[p] is the number of other outcomes of the pixel's
+ * ambiguous decisions (0..OR_MAX_BRANCHES-1) and out_alt[p][k] = (rgb[3],
+ * T_final, last) of outcome k. */
 void or_render(int N, const double *X, const double *q, const double *log_s, const double *logit_o,
                const double *rgb, const or_cam *cam, const double *R_cw, const double *t_cw,
                const or_opts *o, int npix, const int32_t *pix,
-               double *out_rgb, double *out_T, int32_t *out_last, int32_t *out_flags) {
+               double *out_rgb, double *out_T, int32_t *out_last, int32_t *out_flags,
+               int32_t *out_nalt, double *out_alt) {
     or_frame_state S;
     frame_state(&S, N, X, q, log_s, logit_o, cam, R_cw, t_cw, o);
     or_blend B;
     blend_alloc(&B, S.M);
+    or_branches *Xb = (or_branches *)malloc(sizeof(or_branches));
     int total = pix ? npix : cam->width * cam->height;
     for (int p = 0; p < total; p++) {
         double u = pix ? pix[2 * p] : (double)(p % cam->width);
         double v = pix ? pix[2 * p + 1] : (double)(p / cam->width);
-        blend_pixel(&S, u, v, o, &B);
-        double C[3] = {0, 0, 0};
-        for (int k = 0; k < B.n; k++)
-            for (int ch = 0; ch < 3; ch++) C[ch] += rgb[3 * B.g[k] + ch] * B.alpha[k] * B.T[k];
-        for (int ch = 0; ch < 3; ch++) out_rgb[3 * p + ch] = C[ch] + B.T_final * o->bg[ch];
-        out_T[p] = B.T_final;
-        out_last[p] = B.n > 0 ? B.g[B.n - 1] : -1;
-        out_flags[p] = B.flags;
+        Xb->S = &S; Xb->rgb = rgb; Xb->o = o; Xb->u = u; Xb->v = v; Xb->B = &B;
+        Xb->count = 0;
+        Xb->flags = 0;
+        or_path none;
+        none.n = 0;
+        if (out_alt) {
+            explore(Xb, &none);
+        } else {
+            blend_pixel_path(&S, u, v, o, &none, &B);
+            blend_result(&B, rgb, o, Xb->out[0]);
+            Xb->count = 1;
+            Xb->flags = B.flags;
+        }
+        for (int ch = 0; ch < 3; ch++) out_rgb[3 * p + ch] = Xb->out[0][ch];
+        out_T[p] = Xb->out[0][3];
+        out_last[p] = (int32_t)Xb->out[0][4];
+        out_flags[p] = Xb->flags;
+        if (out_alt) {
+            out_nalt[p] = Xb->count - 1;
+            for (int k = 1; k < Xb->count; k++)
+                for (int j = 0; j < 5; j++) out_alt[((size_t)p * (OR_MAX_BRANCHES - 1) + k - 1) * 5 + j] = Xb->out[k][j];
+        }
     }
+    free(Xb);
     blend_free(&B);
     frame_state_free(&S);
 }

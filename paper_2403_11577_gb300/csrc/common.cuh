@@ -9,7 +9,8 @@
 
 namespace gs {
 
-constexpr int kPose32Stride = 16;   // floats per frame: R_cw[9], c_hi[3], c_lo[3], pad
+constexpr int kPose32Stride = 32;   // floats per frame: R_cw hi[9], c_hi[3], c_lo[3], pad, R_cw lo[9], pad[7]
+constexpr int kPoseRlo = 16;        // offset of R_cw's low parts within a frame's pose32
 constexpr int kPose64Stride = 32;   // doubles per frame, see pose.cu
 constexpr int kEmitItems = 1024;    // records per pair-emission block
 constexpr int kEmitThreads = 256;
@@ -72,6 +73,19 @@ __device__ __forceinline__ int frame_of_record(const gs_frame *fr, int F, long l
         if (fr[mid].record_offset <= r) lo = mid; else hi = mid - 1;
     }
     return lo;
+}
+
+// Error-free transformations in float (never contracted into FMAs): a + b =
+// s + e exactly (two_sum), and a * b = p + e exactly (two_prod).
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+__device__ __forceinline__ void two_prod(float a, float b, float &p, float &e) {
+    p = __fmul_rn(a, b);
+    e = __fmaf_rn(a, b, -p);
 }
 
 __device__ __forceinline__ float ex2_approx(float x) {

@@ -5,9 +5,10 @@
 //   p(tau) = p_k + s (p_{k+1} - p_k);  R(tau) = R_k Exp(s w_k) where
 //   w_k = Log(R_k^T R_{k+1}) (the rotation-matrix form of SLERP).
 //   Camera-to-world T^n = T_L(tau) [R_e | t_e];  world-to-camera R_cw =
-//   (R_L R_e)^T, camera centre c = R_L t_e + p.  Stored in float as R_cw and
-//   c split into hi + lo floats, so the projection can form X - c with an
-//   error relative to |X - c| rather than to |X|.
+//   (R_L R_e)^T, camera centre c = R_L t_e + p.  Stored in float with R_cw
+//   and c each split into hi + lo floats, so that the projection can form
+//   R_cw (X - c) in float-float arithmetic and round the depth and the 2D
+//   mean once.
 //   The time-offset gradient needs the camera-frame velocity twist
 //   nu = Ad(T_e^-1) eta, eta = (R_L^T p_dot, w_k / dt) the LiDAR body twist:
 //   nu = (R_e^T (v + w x t_e), R_e^T w).
@@ -149,7 +150,9 @@ __global__ void k_pose_compose(const gs_frame *__restrict__ frames, int F, const
     for (int i = 0; i < 3; i++)
         for (int j = 0; j < 3; j++) {
             double r = R_wc[3 * j + i];  // R_cw = R_wc^T
-            o32[3 * i + j] = (float)r;
+            const float hi = (float)r;
+            o32[3 * i + j] = hi;
+            o32[kPoseRlo + 3 * i + j] = (float)(r - (double)hi);
             o64[3 * i + j] = r;
         }
     for (int i = 0; i < 3; i++) {
@@ -161,6 +164,7 @@ __global__ void k_pose_compose(const gs_frame *__restrict__ frames, int F, const
         o64[15 + i] = R_e[i] * w_body[0] + R_e[3 + i] * w_body[1] + R_e[6 + i] * w_body[2];   // nu_phi
     }
     o32[15] = 0.f;
+    for (int i = kPoseRlo + 9; i < kPose32Stride; i++) o32[i] = 0.f;
     for (int i = 0; i < 9; i++) o64[18 + i] = R_e[i];
     for (int i = 27; i < kPose64Stride; i++) o64[i] = 0.0;
 }

@@ -4,8 +4,12 @@
 // Layout: one thread per Gaussian of the whole batch; the thread reads the
 // Gaussian's parameters once (44 bytes) and loops over the frames of its
 // scene, writing one record per frame.  Frame-dependent work uses
-//   d = (X - c_hi) - c_lo   (camera centre c = c_hi + c_lo in two floats),
-//   p = R_cw d              (Eq. 2: X^n = (T^n)^-1 X = R_cw (X - c)),
+//   p = R_cw (X - c)        (Eq. 2: X^n = (T^n)^-1 X), formed in float-float
+//                           arithmetic from R_cw and c given as hi + lo
+//                           floats; the depth p.z and the 2D mean are each
+//                           rounded once, so they are the floats nearest to
+//                           their exact values (the depth key and the culling
+//                           at the near plane are decided on that float),
 //   T = J R_cw              (J: Jacobian of the pinhole map at p, with x/z
 //                            and y/z limited to the widened field of view),
 //   cov = T Sigma T^T + lowpass I   (= J Sigma_c J^T, Sigma_c of Eq. 3),
@@ -17,7 +21,7 @@
 //             the box of the ellipse d^T conic d <= 2 ln(opacity/alpha_min),
 //             half-widths sqrt(k cov_xx), sqrt(k cov_yy), widened by a
 //             relative 1e-4 and 0.01 px against float32 rounding;
-//   depth[r]  camera depth p.z;
+//   depth[r]  camera depth p.z, the float nearest to its exact value;
 //   splat[r]  (mean_x, mean_y, A, B), (C, F, rx, ry) with the exponent in
 //             base 2: log2 alpha = A dx^2 + B dx dy + C dy^2 + F,
 //             A = -a/2 log2 e, B = -b log2 e, C = -c/2 log2 e, F = log2 opacity,
@@ -89,17 +93,70 @@ struct Proj {
     float mean[2];
 };
 
+// Camera-frame centre p = R_cw (X - c) (Eq. 2) in float-float arithmetic.
+// R_cw and c come as hi + lo floats; X - c_hi is split exactly (two_sum),
+// each product R_ij d_j is kept exactly to first order (two_prod plus the
+// cross terms) and the sums are carried with their rounding errors, so that
+// p_i = ph_i + pl_i is within a few 2^-48 sum_j |R_ij| |d_j| of the exact
+// value for the float inputs X and the double pose.  ph_i is that sum
+// rounded once, so the depth ph_2 is the float nearest to the exact depth
+// (unless the exact depth lies within that error of a rounding boundary).
+__device__ __forceinline__ void camera_point(const float (&X)[3], const float *__restrict__ P, float (&ph)[3],
+                                             float (&pl)[3]) {
+    float dh[3], dl[3];
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        float e;
+        two_sum(X[k], -P[9 + k], dh[k], e);
+        dl[k] = __fsub_rn(e, P[12 + k]);
+    }
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+        float sh = 0.f, sl = 0.f;
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            const float rh = P[3 * i + k], rl = P[kPoseRlo + 3 * i + k];
+            float pr, pe, te;
+            two_prod(rh, dh[k], pr, pe);
+            pe = __fadd_rn(pe, __fmaf_rn(rh, dl[k], __fmul_rn(rl, dh[k])));
+            two_sum(sh, pr, sh, te);
+            sl = __fadd_rn(sl, __fadd_rn(te, pe));
+        }
+        two_sum(sh, sl, ph[i], pl[i]);
+    }
+}
+
+// (hi + lo) / z for z = zh + zl, to about 2^-46 relative: the quotient of
+// the high parts rounded, its remainder (exact by the fma) plus the low
+// parts, divided again.
+__device__ __forceinline__ void ff_div(float xh, float xl, float zh, float zl, float &q, float &ql) {
+    q = __fdiv_rn(xh, zh);
+    float r = __fmaf_rn(-q, zh, xh);
+    r = __fadd_rn(r, __fsub_rn(xl, __fmul_rn(q, zl)));
+    ql = __fdiv_rn(r, zh);
+}
+
+// f (q + ql) + c rounded once (two_prod and two_sum keep the parts exact).
+__device__ __forceinline__ float ff_affine(float f, float q, float ql, float c) {
+    float a, ae, sh, se;
+    two_prod(f, q, a, ae);
+    ae = __fmaf_rn(f, ql, ae);
+    two_sum(a, c, sh, se);
+    return __fadd_rn(sh, __fadd_rn(se, ae));
+}
+
 __device__ __forceinline__ bool project_frame(const GaussParams &G, const float *__restrict__ P,
                                               const gs_frame &fr, const gs_opts &o, Proj &Q) {
-    float d0 = (G.X[0] - P[9]) - P[12];
-    float d1 = (G.X[1] - P[10]) - P[13];
-    float d2 = (G.X[2] - P[11]) - P[14];
-    for (int i = 0; i < 3; i++) Q.p[i] = P[3 * i] * d0 + P[3 * i + 1] * d1 + P[3 * i + 2] * d2;
-    float z = Q.p[2];
+    float pl[3];
+    camera_point(G.X, P, Q.p, pl);
+    // the depth key is the float nearest to the exact depth: the culling
+    // at the near plane and the depth order are decided on it
+    const float z = Q.p[2];
     if (!(z > o.near_z)) return false;
+    float xl, yl;
+    ff_div(Q.p[0], pl[0], z, pl[2], Q.xz, xl);
+    ff_div(Q.p[1], pl[1], z, pl[2], Q.yz, yl);
     Q.iz = 1.f / z;
-    Q.xz = Q.p[0] * Q.iz;
-    Q.yz = Q.p[1] * Q.iz;
     // J at x/z, y/z limited to the field of view widened by frustum_margin
     // of the image size per side (bounds the footprint of far off-image centres)
     Q.jx = Q.xz;
@@ -135,8 +192,9 @@ __device__ __forceinline__ bool project_frame(const GaussParams &G, const float 
     Q.conic[0] = Q.cov[2] * idet;
     Q.conic[1] = -Q.cov[1] * idet;
     Q.conic[2] = Q.cov[0] * idet;
-    Q.mean[0] = fr.fx * Q.xz + fr.cx;
-    Q.mean[1] = fr.fy * Q.yz + fr.cy;
+    // the 2D mean, rounded once from fx x/z + cx, fy y/z + cy
+    Q.mean[0] = ff_affine(fr.fx, Q.xz, xl, fr.cx);
+    Q.mean[1] = ff_affine(fr.fy, Q.yz, yl, fr.cy);
     return isfinite(Q.mean[0]) && isfinite(Q.mean[1]);
 }
 

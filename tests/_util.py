@@ -61,3 +61,30 @@ def rel_l2(a, b):
     a, b = np.asarray(a, np.float64).ravel(), np.asarray(b, np.float64).ravel()
     den = np.linalg.norm(b)
     return np.linalg.norm(a - b) / den if den > 0 else np.linalg.norm(a - b)
+
+
+def oracle_outcomes(scene, frame, ext, delta, opts, pixels=None):
+    """The oracle's render of a frame's pixels together with every outcome of
+    their ambiguous float32 decisions (oracle.render(..., alternatives=True))."""
+    return oracle.render(scene, frame, ext, delta, oracle_opts(opts), pixels, alternatives=True)
+
+
+def match_outcomes(rgb_g, T_g, last_g, ref, tol):
+    """Compare the GPU's colour, transmittance and last Gaussian per pixel
+    with the oracle's outcomes: the FP64 one and, where a skip or stop
+    decision is ambiguous in float32, each alternative (every one is a
+    correct float32 result).  Returns (decided, matched): decided = the
+    oracle gives the pixel an outcome set (no undecided depth order, near
+    plane culling or branch overflow); matched = the GPU equals one outcome
+    within tol, with the same last Gaussian."""
+    rgb_o, T_o, last_o, flags, (nalt, alt) = ref
+    rgb_g = np.asarray(rgb_g, np.float64).reshape(-1, 3)
+    T_g = np.asarray(T_g, np.float64).reshape(-1)
+    last_g = np.asarray(last_g).reshape(-1)
+    matched = (np.abs(rgb_g - rgb_o).max(1) <= tol) & (np.abs(T_g - T_o) <= tol) & (last_g == last_o)
+    for k in range(alt.shape[1]):
+        a = alt[:, k]
+        matched |= (nalt > k) & (np.abs(rgb_g - a[:, :3]).max(1) <= tol) & (np.abs(T_g - a[:, 3]) <= tol) & \
+                   (last_g == a[:, 4].astype(np.int64))
+    decided = (flags & oracle.FLAGS_UNDECIDED) == 0
+    return decided, matched

@@ -1,11 +1,18 @@
 """Parity of the CUDA path (through the C-ABI) with the FP64 CPU oracle.
 
 Tolerances (from the stated targets): rendered colour and transmittance
-within 1e-4 max-abs on pixels the oracle does not flag as lying on a
-float32/float64 discontinuity; the last composited Gaussian identical there;
-tile binning and sort order bit-exact; gradients within 1e-3 relative L2 per
-parameter group.
+within 1e-4 max-abs and the last composited Gaussian identical, against the
+oracle's outcome for every pixel whose decisions the oracle can enumerate
+(where a skip or stop decision is ambiguous in float32, the GPU must equal
+one of its outcomes); tile binning and sort order bit-exact; gradients
+within 1e-3 relative L2 per parameter group, with dL/dC zero on pixels with
+an ambiguous decision (their gradient depends on the outcome).
 """
+
+# share of sampled pixels allowed without a decidable outcome set (an
+# undecided depth order or near-plane culling in float32): none on the tiny
+# scenes, at most 1e-3 on the LiDAR-shaped frames
+UNDECIDED_MAX = 1e-3
 import copy
 import math
 
@@ -16,7 +23,8 @@ import torch
 import oracle
 from paper_2403_11577_gb300 import capi, render, scenes
 
-from _util import ensure_built, ext_delta, last_gaussian_ids, oracle_opts, rel_l2, sample_pixels, setup
+from _util import (ensure_built, ext_delta, last_gaussian_ids, match_outcomes, oracle_opts, oracle_outcomes, rel_l2,
+                   sample_pixels, setup)
 
 pytestmark = pytest.mark.gpu
 
@@ -48,7 +56,7 @@ def test_pose_compose_matches_oracle(delta):
     scene, plan, ext, dl = setup(p)
     plan.pose(scene, ext, dl)
     pose64 = plan.ws_view(capi.WS_POSE64, torch.float64, 32 * 8).cpu().numpy().reshape(8, 32)
-    pose32 = plan.ws_view(capi.WS_POSE32, torch.float32, 16 * 8).cpu().numpy().reshape(8, 16)
+    pose32 = plan.ws_view(capi.WS_POSE32, torch.float32, 32 * 8).cpu().numpy().reshape(8, 32)
     for i, f in enumerate(p.frames):
         R, t = oracle.frame_pose(sc, p.ext[0], delta, f.timestamp)
         c = -R.T @ t
@@ -56,6 +64,9 @@ def test_pose_compose_matches_oracle(delta):
         np.testing.assert_allclose(pose64[i, 9:12], c, atol=1e-9)
         hi, lo = pose32[i, 9:12].astype(np.float64), pose32[i, 12:15].astype(np.float64)
         np.testing.assert_allclose(hi + lo, c, rtol=1e-9, atol=1e-9)
+        # R_cw as high and low floats: their sum is the double rotation to ~2^-48
+        Rhl = pose32[i, :9].astype(np.float64) + pose32[i, 16:25].astype(np.float64)
+        np.testing.assert_allclose(Rhl.reshape(3, 3), R, rtol=0, atol=1e-13)
 
 
 # -------------------------------------------------------------- projection
@@ -95,7 +106,11 @@ def test_project_matches_oracle():
     np.testing.assert_allclose(splat[k, 6], o["extent"][k, 0] * 1.0001 + 0.01, rtol=1e-4)
     np.testing.assert_allclose(splat[k, 7], o["extent"][k, 1] * 1.0001 + 0.01, rtol=1e-4)
     depth = plan.ws_view(capi.WS_DEPTH, torch.float32, n).cpu().numpy()
-    np.testing.assert_allclose(depth[k], o["depth"][k], rtol=1e-5)
+    # the depth key is the float nearest to the exact depth (the oracle's
+    # key), bit for bit, wherever the oracle finds the rounding decided
+    dec = k & ~o["zamb"]
+    np.testing.assert_array_equal(depth[dec].view(np.uint32), o["zkey"][dec].view(np.uint32))
+    assert (k & o["zamb"]).sum() <= 1e-4 * k.sum()
     # rect: GPU contains the oracle's; equal unless an extent edge is near a tile boundary
     ext_ = o["extent"][k]
     m = o["mean"][k]
@@ -108,6 +123,59 @@ def test_project_matches_oracle():
     assert np.all(g_r[:, :2] <= o_r[:, :2]) and np.all(g_r[:, 2:] >= o_r[:, 2:])
     same = np.all(g_r == o_r, axis=1)
     assert np.all(same | near)
+
+
+@pytest.mark.parametrize("which", ["lidar_frame", "drive_1M"])
+def test_projection_errors_within_the_oracles_decision_bounds(which):
+    """The oracle decides each skip and stop in FP64 and treats a decision as
+    ambiguous when its exact value lies within a bound of the float32
+    evaluation's error.  The GPU's own records must stay inside that bound:
+    the 2D mean within the oracle's mean bound, and the exponent of every
+    record, evaluated in FP64 from the GPU's (A, B, C, F) at points of its
+    alpha = alpha_min ellipse (16 directions), within the oracle's conic and
+    log-opacity share of it.  (The per-pixel evaluation's own rounding is
+    the rest of the bound.)  Checked on every record of the LiDAR frame and
+    of two frames of the 1M-Gaussian drive."""
+    if which == "lidar_frame":
+        p, frame_ids = scenes.lidar_frame_problem(), [0]
+    else:
+        p, frame_ids = scenes.batched_problem(n=1_000_000), [0, 7]
+    opts = render.RenderOptions()
+    scene, plan, ext, dl = setup(p, opts)
+    plan.pose(scene, ext, dl)
+    plan.project(scene)
+    n = p.scenes[0].n
+    F = plan.num_frames
+    rect = plan.ws_view(capi.WS_RECT, torch.int32, 2 * n * F).cpu().numpy().view(np.uint32).reshape(F, n, 2)
+    splat = plan.ws_view(capi.WS_SPLAT, torch.float32, 8 * n * F).cpu().numpy().reshape(F, n, 8).astype(np.float64)
+    log2e = 1.0 / math.log(2.0)
+    lmin = math.log2(opts.alpha_min)
+    worst_mean = worst_e = 0.0
+    for fi in frame_ids:
+        f = p.frames[fi]
+        R, t = oracle.frame_pose(p.scenes[0], p.ext[0], float(p.delta[0]), f.timestamp)
+        o = oracle.project(p.scenes[0], f.camera, R, t, oracle_opts(opts), tile=16)
+        gvis = (rect[fi, :, 0] & 0xFFFF) <= (rect[fi, :, 1] & 0xFFFF)
+        k = gvis & o["valid"].astype(bool)
+        s = splat[fi, k]
+        dm = np.abs(s[:, :2] - o["mean"][k])
+        worst_mean = max(worst_mean, float((dm / o["mean_err"][k]).max()))
+        conic = o["conic"][k]
+        A, B, C = -0.5 * log2e * conic[:, 0], -log2e * conic[:, 1], -0.5 * log2e * conic[:, 2]
+        Fx = np.log2(o["opacity"][k])
+        reach = Fx - lmin
+        for th in np.linspace(0, 2 * np.pi, 16, endpoint=False):
+            ux, uy = math.cos(th), math.sin(th)
+            r = np.sqrt(reach / -(A * ux * ux + B * ux * uy + C * uy * uy))
+            dx, dy = r * ux, r * uy
+            e2 = A * dx * dx + B * dx * dy + C * dy * dy
+            e2g = s[:, 2] * dx * dx + s[:, 3] * dx * dy + s[:, 4] * dy * dy
+            mag = np.abs(A) * dx * dx + np.abs(B * dx * dy) + np.abs(C) * dy * dy
+            bound = o["conic_err"][k] * np.abs(e2) + 4 * 2.0 ** -24 * mag + o["logop_err"][k]
+            err = np.abs((e2g + s[:, 5]) - (e2 + Fx))
+            worst_e = max(worst_e, float((err / bound).max()))
+    assert worst_mean <= 1.0, worst_mean
+    assert worst_e <= 1.0, worst_e
 
 
 # ---------------------------------------------------------- bin and sort
@@ -192,21 +260,18 @@ def _compare_frame(plan, p, fi, opts, ext=None, delta=None, pixels=None):
     e = (p.ext if ext is None else ext)[f.camera_id]
     d = float((p.delta if delta is None else delta)[f.camera_id])
     cam = f.camera
-    rgb_o, T_o, last_o, flags = oracle.render(sc, f, e, d, oracle_opts(opts), pixels)
+    ref = oracle_outcomes(sc, f, e, d, opts, pixels)
     rgb_g = plan.image(plan.rgb, fi).cpu().numpy().reshape(-1, 3)
     T_g = plan.image(plan.T, fi).cpu().numpy().reshape(-1)
     gid = last_gaussian_ids(plan, fi)
     if pixels is not None:
         idx = pixels[:, 1] * cam.width + pixels[:, 0]
         rgb_g, T_g, gid = rgb_g[idx], T_g[idx], gid[idx]
-    ok = flags == 0
-    # discontinuity flags are rare; a sample of a few hundred pixels may hold a few
-    assert ok.mean() > (0.95 if pixels is not None else 0.99), "too many flagged pixels: %d" % (~ok).sum()
-    err = np.abs(rgb_g[ok] - rgb_o[ok]).max()
-    assert err <= COLOUR_TOL, err
-    assert np.abs(T_g[ok] - T_o[ok]).max() <= COLOUR_TOL
-    np.testing.assert_array_equal(gid[ok], last_o[ok])
-    return ok
+    decided, matched = match_outcomes(rgb_g, T_g, gid, ref, COLOUR_TOL)
+    assert (~decided).mean() <= UNDECIDED_MAX, "undecided pixels: %d of %d" % ((~decided).sum(), len(decided))
+    bad = np.nonzero(decided & ~matched)[0]
+    assert len(bad) == 0, "pixels matching no oracle outcome: %s" % bad[:10]
+    return decided
 
 
 @pytest.mark.parametrize("size", [(64, 48), (70, 45), (16, 16), (1, 1), (33, 130)])
@@ -303,13 +368,13 @@ def test_crop_is_the_bottom_of_the_full_render(row0):
         assert rel_l2(g[k].cpu().numpy(), gfull[k].cpu().numpy()) <= GRAD_TOL, k
     rng = np.random.default_rng(row0)
     pix = np.stack([rng.integers(0, cam.width, 150), rng.integers(row0, cam.height, 150)], 1)
-    rgb_o, T_o, _, flags = oracle.render(pc.scenes[0], pc.frames[0], pc.ext[0], 0.0, oracle_opts(opts), pix)
+    ref = oracle_outcomes(pc.scenes[0], pc.frames[0], pc.ext[0], 0.0, opts, pix)
     got = crop.image(crop.rgb, 0).cpu().numpy()[pix[:, 1] - row0, pix[:, 0]]
-    ok = flags == 0
-    # the last image row sees the ground just ahead of the camera, where more
-    # pixels carry near-plane and depth-tie flags
-    assert ok.mean() > (0.95 if cam.height - row0 >= 16 else 0.8)
-    assert np.abs(got[ok] - rgb_o[ok]).max() <= COLOUR_TOL
+    got_T = crop.image(crop.T, 0).cpu().numpy()[pix[:, 1] - row0, pix[:, 0]]
+    got_last = last_gaussian_ids(crop, 0).reshape(cam.height - row0, cam.width)[pix[:, 1] - row0, pix[:, 0]]
+    decided, matched = match_outcomes(got, got_T, got_last, ref, COLOUR_TOL)
+    assert decided.all()
+    assert matched.all(), np.nonzero(~matched)[0]
 
 
 def _tile_lists(plan):
@@ -460,7 +525,8 @@ def _grads_vs_oracle(p, opts, W_frames, pixels=None, groups=None):
 
 
 def _weights(p, opts, seed, density=1.0):
-    """Random dL/dC per frame, zero on pixels the oracle flags."""
+    """Random dL/dC per frame, zero on pixels with an ambiguous decision
+    (flagged by the oracle)."""
     rng = np.random.default_rng(seed)
     out = []
     for f in p.frames:
@@ -503,8 +569,8 @@ def test_render_bwd_lidar_frame_sparse_pixels():
     cam = p.frames[0].camera
     rng = np.random.default_rng(7)
     pix = np.unique(sample_pixels(rng, cam, 300), axis=0)
-    rgb_o, _, _, flags = oracle.render(p.scenes[0], p.frames[0], p.ext[0], 0.0, oracle_opts(opts), pix)
-    pix = pix[flags == 0]
+    flags = oracle.render(p.scenes[0], p.frames[0], p.ext[0], 0.0, oracle_opts(opts), pix)[3]
+    pix = pix[flags == 0]  # no ambiguous decision: the gradient is unique
     Wp = rng.normal(size=(len(pix), 3))
     W = np.zeros((cam.height * cam.width, 3))
     W[pix[:, 1] * cam.width + pix[:, 0]] = Wp
@@ -538,23 +604,25 @@ def test_bench_workload_sampled_forward_and_backward():
     rng = np.random.default_rng(11)
     dL = torch.zeros_like(plan.rgb)
     ref = {k: 0.0 for k in ("quat", "log_scale", "logit_opacity", "rgb", "ext", "delta")}
+    n_dec = n_all = n_grad = 0
     for fi, f in enumerate(p.frames):
         cam = f.camera
         pix = np.unique(sample_pixels(rng, cam, 80), axis=0)
         sc, e, d = p.scenes[f.scene_id], p.ext[f.camera_id], float(p.delta[f.camera_id])
-        rgb_o, T_o, last_o, flags = oracle.render(sc, f, e, d, oracle_opts(opts), pix)
-        # with hundreds of contributors per pixel, a fifth of the pixels have
-        # one whose alpha lies within the flag margin of a threshold
-        ok = flags == 0
-        assert ok.mean() >= 0.5, (~ok).sum()
+        outc = oracle_outcomes(sc, f, e, d, opts, pix)
+        flags = outc[3]
         idx = pix[:, 1] * cam.width + pix[:, 0]
         rgb_g = plan.image(plan.rgb, fi).cpu().numpy().reshape(-1, 3)[idx]
         T_g = plan.image(plan.T, fi).cpu().numpy().reshape(-1)[idx]
         gid = last_gaussian_ids(plan, fi)[idx]
-        assert np.abs(rgb_g[ok] - rgb_o[ok]).max() <= COLOUR_TOL
-        assert np.abs(T_g[ok] - T_o[ok]).max() <= COLOUR_TOL
-        np.testing.assert_array_equal(gid[ok], last_o[ok])
-        pix = pix[ok]
+        decided, matched = match_outcomes(rgb_g, T_g, gid, outc, COLOUR_TOL)
+        n_dec += int(decided.sum())
+        n_all += len(decided)
+        bad = np.nonzero(decided & ~matched)[0]
+        assert len(bad) == 0, (fi, bad)
+        # gradients on the pixels whose every decision is unambiguous
+        pix = pix[flags == 0]
+        n_grad += len(pix)
         Wp = rng.normal(size=(len(pix), 3))
         W = np.zeros((cam.height * cam.width, 3))
         W[pix[:, 1] * cam.width + pix[:, 0]] = Wp
@@ -563,6 +631,10 @@ def test_bench_workload_sampled_forward_and_backward():
                              oracle_opts(opts), pixels=pix)
         for k in ref:
             ref[k] = ref[k] + np.asarray(og[k], np.float64)
+    # every sampled pixel has an outcome set, and all but a few percent carry
+    # no ambiguous decision at all
+    assert n_dec >= (1 - UNDECIDED_MAX) * n_all, (n_dec, n_all)
+    assert n_grad >= 0.9 * n_all, (n_grad, n_all)
     g = render.empty_grads(scene, p.num_cameras)
     plan.backward(scene, dL, g, ext)
     for k in ("quat", "log_scale", "logit_opacity", "rgb"):
@@ -711,7 +783,7 @@ def test_calibration_step_with_photo_loss_matches_oracle():
     tgt = target.cpu().numpy().reshape(24, 70, 3).astype(np.float64)
     lo, (go,) = oracle.photo_loss([img_o], [tgt], 0.2)
     assert loss == pytest.approx(lo, rel=1e-4)
-    assert flags.max() == 0  # no ambiguous pixel in this scene
+    assert flags.max() == 0  # no ambiguous decision in this scene
     og = oracle.backward(p.scenes[0], f, p.ext[0], 0.013, go.reshape(-1, 3), oracle_opts(opts))
     for k in ("quat", "log_scale", "logit_opacity", "rgb"):
         assert rel_l2(step.grads[k].cpu().numpy(), og[k]) <= GRAD_TOL, k

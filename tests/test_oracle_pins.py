@@ -406,16 +406,180 @@ def test_l1_matches_numpy():
     np.testing.assert_array_equal(grad, np.sign(a - b) / a.size)
 
 
-def test_ambiguity_flag_alpha_threshold():
-    """A pixel where some alpha sits on the 1/255 skip threshold is flagged."""
-    # o = 0.5; choose the pixel offset dx so that 0.5 exp(-dx^2 conic / 2) = 1/255
-    sc = _single_scene([[0, 0, 2]], [[0.1] * 3], [0.0], [[1, 1, 1]])
-    conic = 1 / 9.3
-    dx = math.sqrt(2 * math.log(0.5 * 255) / conic)
-    cam = scenes.Camera(64, 48, 60.0, 60.0, 32.0 - (dx - round(dx)), 24.0)
-    fr = scenes.Frame(cam, 0.0)
-    _, _, _, flags = oracle.render(sc, fr, np.zeros(6), 0.0, oracle.Opts(), pixels=[[32 + round(dx), 24], [32, 24]])
-    assert flags[0] & oracle.FLAG_ALPHA_EDGE and flags[1] == 0
+def _outcomes(sc, cam, pixels, opts=oracle.Opts(bg=BG)):
+    """Every outcome (rgb, T, last) per pixel, the FP64 one first, and the flags."""
+    rgb, T, last, flags, (nalt, alt) = oracle.render(sc, scenes.Frame(cam, 0.0), np.zeros(6), 0.0, opts,
+                                                       pixels=pixels, alternatives=True)
+    out = []
+    for p in range(len(flags)):
+        o = [(rgb[p], T[p], int(last[p]))]
+        o += [(alt[p, k, :3], alt[p, k, 3], int(alt[p, k, 4])) for k in range(nalt[p])]
+        out.append(o)
+    return out, flags
+
+
+def _same_outcomes(got, want):
+    """The outcome sets agree (any order), colours and T to 1e-12."""
+    assert len(got) == len(want), (got, want)
+    for w in want:
+        assert any(abs(g[1] - w[1]) < 1e-12 and g[2] == w[2] and np.abs(np.asarray(g[0]) - w[0]).max() < 1e-12
+                   for g in got), (w, got)
+
+
+# The renderer decides skip, stop, clamp and order on float32 values; where
+# the exact value lies within the float32 evaluation's error bound of a
+# threshold, either outcome is a correct result.  Each pin below places a
+# pixel on such an edge (both outcomes, in closed form) and one just off it
+# (the one FP64 outcome, no flag).  For these well-conditioned Gaussians the
+# bound is a few 1e-5 in log2 units, so 1e-3 is clearly off the edge.
+
+def test_alpha_min_edge_has_both_outcomes():
+    """alpha = opacity exp(power) = alpha_min exactly: the Gaussian is
+    composited (C = alpha c + (1 - alpha) bg) or skipped (C = bg)."""
+    sc = _single_scene([[0, 0, 2]], [[0.1] * 3], [0.0], [[1.0, 0.5, 0.25]])
+    cov = (60.0 * 0.1 / 2) ** 2 + 0.3  # EWA covariance of the on-axis Gaussian, px^2
+    amin = 1.0 / 255.0
+    for shift, on_edge in ((0.0, True), (1e-3, False), (-1e-3, False)):
+        # log2 alpha = log2 alpha_min + shift at a distance dx from the mean
+        power = math.log(amin / 0.5) + shift * math.log(2.0)
+        dx = math.sqrt(-2.0 * power * cov)
+        cam = scenes.Camera(64, 48, 60.0, 60.0, 42.0 - dx, 24.0)
+        (got,), flags = _outcomes(sc, cam, [[42, 24]])
+        a = 0.5 * math.exp(power)
+        composited = (a * np.array([1.0, 0.5, 0.25]) + (1 - a) * np.array(BG), 1 - a, 0)
+        skipped = (np.array(BG), 1.0, -1)
+        if on_edge:
+            assert flags[0] == oracle.FLAG_BRANCH
+            _same_outcomes(got, [composited, skipped])
+        else:
+            assert flags[0] == 0
+            _same_outcomes(got, [composited if shift > 0 else skipped])
+
+
+def test_stop_edge_has_both_outcomes():
+    """T (1 - alpha) = t_min exactly at the second of two stacked Gaussians
+    (alpha 0.98 then 0.9, t_min = 0.002): compositing stops before it, or
+    composites it; just off the edge it stops."""
+    c1, c2 = np.array([1.0, 0.0, 0.0]), np.array([0.0, 0.0, 1.0])
+    for a2, on_edge in ((0.9, True), (0.9 * (1 + 1e-3), False)):
+        sc = _single_scene([[0, 0, 2], [0, 0, 3]], [[0.1] * 3] * 2, [math.log(49.0), math.log(a2 / (1 - a2))],
+                           [c1, c2])
+        opts = oracle.Opts(bg=BG, t_min=0.02 * 0.1)
+        (got,), flags = _outcomes(sc, CAM, [[32, 24]], opts)
+        stopped = (0.98 * c1 + 0.02 * np.array(BG), 0.02, 0)
+        T2 = 0.02 * (1 - a2)
+        through = (0.98 * c1 + 0.02 * a2 * c2 + T2 * np.array(BG), T2, 1)
+        if on_edge:
+            assert flags[0] == oracle.FLAG_BRANCH
+            _same_outcomes(got, [stopped, through])
+        else:
+            assert flags[0] == 0
+            _same_outcomes(got, [stopped])
+
+
+def test_exponent_sign_edge_of_a_needle():
+    """Along the long axis of a needle (scales 50 m x 1 mm x 1 mm, at 45
+    degrees in the image, 2 m away) the exponent is -d^2 / (2 sigma_long^2),
+    a few 1e-6, while its terms are of order 10: its float32 sign is not
+    decided, so the Gaussian is composited or skipped (C = bg).  Across a
+    moderate Gaussian the same offset is decided."""
+    c = np.array([0.2, 0.9, 0.4])
+    q45 = [math.cos(math.pi / 8), 0, 0, math.sin(math.pi / 8)]
+    needle = _single_scene([[0, 0, 2]], [[50.0, 1e-3, 1e-3]], [0.0], [c], quats=[q45])
+    (got,), flags = _outcomes(needle, CAM, [[36, 28]])
+    assert flags[0] == oracle.FLAG_BRANCH
+    rgb, T, last = got[0]
+    a = 1 - T
+    assert 0.49 < a <= 0.5 and last == 0  # alpha ~ opacity along the axis
+    _same_outcomes(got, [(a * c + (1 - a) * np.array(BG), T, 0), (np.array(BG), 1.0, -1)])
+    plain = _single_scene([[0, 0, 2]], [[0.3, 0.1, 0.1]], [0.0], [c], quats=[q45])
+    (got,), flags = _outcomes(plain, CAM, [[36, 28]])
+    assert flags[0] == 0 and len(got) == 1
+
+
+def test_alpha_max_clamp_edge_flag():
+    """opacity 0.995 with alpha_raw = alpha_max = 0.99 exactly at the pixel:
+    the colour is continuous (one outcome) but the gradient is not, so the
+    pixel is flagged CLAMP_EDGE; at the peak (0.995, clearly clamped) and
+    1.5 px away (0.88) it is not."""
+    sc = _single_scene([[0, 0, 2]], [[0.1] * 3], [math.log(199.0)], [[1.0, 1.0, 1.0]])
+    cov = (60.0 * 0.1 / 2) ** 2 + 0.3
+    dx = math.sqrt(-2.0 * math.log(0.99 / 0.995) * cov)
+    cam = scenes.Camera(64, 48, 60.0, 60.0, 33.0 - dx, 24.0)
+    (got,), flags = _outcomes(sc, cam, [[33, 24]])
+    assert flags[0] == oracle.FLAG_CLAMP_EDGE and len(got) == 1
+    assert got[0][1] == pytest.approx(0.01, abs=1e-12)
+    cam2 = scenes.Camera(64, 48, 60.0, 60.0, 33.0, 24.0)
+    outs, flags = _outcomes(sc, cam2, [[33, 24], [34, 24], [35, 24]])
+    assert flags[0] == 0 and flags[2] == 0  # peak (clamped) and 2 px away (0.80)
+    assert outs[0][0][1] == pytest.approx(0.01, abs=1e-12)
+
+
+def _f32_neighbours(z):
+    f = np.float32(z)
+    return float(f), float(np.nextafter(f, np.float32(np.inf)))
+
+
+def test_depth_order_by_float32_key_and_index():
+    """The depth order is the float32 depth key, equal keys by Gaussian index
+    (Eq. 5's depth order decided in float32): a Gaussian slightly farther in
+    FP64 but with the same key, and a lower index, is composited first."""
+    lo, hi = _f32_neighbours(4.0)
+    c0, c1 = np.array([1.0, 0.0, 0.0]), np.array([0.0, 1.0, 0.0])
+    z_far = lo + 0.25 * (hi - lo)  # rounds to lo, as does z = lo
+    sc = _single_scene([[0, 0, z_far], [0, 0, lo]], [[0.1] * 3] * 2, [0.0, 0.0], [c0, c1])
+    rgb, T, last, flags = oracle.render(sc, FRAME, np.zeros(6), 0.0, oracle.Opts(bg=BG), pixels=[[32, 24]])
+    assert flags[0] == 0 and last[0] == 1
+    pr = oracle.project(sc, CAM, np.eye(3), np.zeros(3), oracle.Opts())
+    assert pr["zkey"][0] == pr["zkey"][1] == np.float32(lo)
+    a0 = 1 - math.sqrt(T[0])  # both alphas are equal at the shared centre
+    np.testing.assert_allclose(rgb[0], a0 * c0 + (1 - a0) * a0 * c1 + (1 - a0) ** 2 * np.array(BG), atol=1e-12)
+
+
+def test_depth_tie_flag_on_an_undecided_rounding():
+    """Two contributors whose keys are one float32 step apart, one of them at
+    an exact rounding midpoint (its key is not decided): DEPTH_TIE.  Moved
+    1e-9 m off the midpoint, the keys are decided and nothing is flagged."""
+    lo, hi = _f32_neighbours(4.0)
+    mid = 0.5 * (lo + hi)
+    for z, flagged in ((mid, True), (mid + 1e-9, False)):
+        sc = _single_scene([[0, 0, lo], [0, 0, z]], [[0.1] * 3] * 2, [0.0, 0.0], [[1, 0, 0], [0, 1, 0]])
+        pr = oracle.project(sc, CAM, np.eye(3), np.zeros(3), oracle.Opts())
+        assert bool(pr["zamb"][1]) == flagged and not pr["zamb"][0]
+        flags = oracle.render(sc, FRAME, np.zeros(6), 0.0, oracle.Opts(bg=BG), pixels=[[32, 24]])[3]
+        assert flags[0] == (oracle.FLAG_DEPTH_TIE if flagged else 0)
+
+
+def test_near_plane_culling_decided_in_float32():
+    """Culling at the near plane compares the float32 depth key with float32
+    near_z: a centre at the midpoint above float32(0.2) may be kept or
+    culled (NEAR_EDGE where it would contribute); at 0.3 m it is decided."""
+    lo, hi = _f32_neighbours(0.2)
+    for z, flagged in ((0.5 * (lo + hi), True), (0.3, False)):
+        sc = _single_scene([[0, 0, z]], [[0.01] * 3], [0.0], [[1, 1, 1]])
+        pr = oracle.project(sc, CAM, np.eye(3), np.zeros(3), oracle.Opts())
+        assert bool(pr["near_undecided"][0]) == flagged
+        flags = oracle.render(sc, FRAME, np.zeros(6), 0.0, oracle.Opts(bg=BG), pixels=[[32, 24]])[3]
+        assert flags[0] == (oracle.FLAG_NEAR_EDGE if flagged else 0)
+    # exactly on float32(near_z) the key is not in front: culled, decided
+    sc = _single_scene([[0, 0, lo]], [[0.01] * 3], [0.0], [[1, 1, 1]])
+    pr = oracle.project(sc, CAM, np.eye(3), np.zeros(3), oracle.Opts())
+    assert pr["valid"][0] == 0 and not pr["near_undecided"][0]
+
+
+def test_branch_limit_flag():
+    """More ambiguous decisions than OR_MAX_BRANCHES outcomes: twenty
+    stacked Gaussians, each with alpha exactly alpha_min at the pixel, give
+    2^20 outcomes: the pixel is flagged BRANCH_LIMIT (undecided)."""
+    n = 20
+    cov = (60.0 * 0.1 / 2) ** 2 + 0.3
+    dx = math.sqrt(-2.0 * math.log((1 / 255.0) / 0.5) * cov)
+    cam = scenes.Camera(64, 48, 60.0, 60.0, 42.0 - dx, 24.0)
+    zs = [2.0 * (1 + 0.01 * k) for k in range(n)]
+    # the same pixel offset at each depth: scale the Gaussians with depth
+    sc = _single_scene([[0, 0, z] for z in zs], [[0.1 * z / 2.0] * 3 for z in zs], [0.0] * n, [[1, 1, 1]] * n)
+    _, flags = _outcomes(sc, cam, [[42, 24]])
+    assert flags[0] & oracle.FLAG_BRANCH_LIMIT and flags[0] & oracle.FLAG_BRANCH
 
 
 def test_scale_clamp():
