@@ -5,17 +5,18 @@
 // value = Gaussian index within its scene, stable in record order.
 // gs_bin_sort gets there in two cheap stages instead of one wide sort, with
 // 32-bit keys throughout:
-// 1. k_rec_keys + 4 LSD passes over the per-(frame, Gaussian) records keyed
-//    by the float bits of their depth (culled records last): a stable depth
-//    order of the records (ties keep record order).
+// 1. 4 LSD passes over the per-(frame, Gaussian) records keyed by the float
+//    bits of their depth (culled records last; the first pass reads the
+//    depths and rectangles directly): a stable depth order of the records
+//    (ties keep record order).
 // 2. k_pair_count / k_pair_scan / k_pair_emit over the records in that
 //    order: every record emits one pair per tile of its rectangle (emission
 //    is cooperative: threads stride over the block's output range and find
 //    their record by binary search).  With exact tiles (gs_opts.exact_tiles)
 //    k_pair_count_exact / k_pair_emit_exact emit only the tiles of each
-//    rectangle row that the record's ellipse can meet (see "exact tile
-//    binning" below).  The pairs are thus already in (depth, record) order;
-//    their key is the global tile alone.
+//    rectangle row that the record's ellipse can meet (spans.cuh).  The
+//    pairs are thus already in (depth, record) order; their key is the
+//    global tile alone.
 // 3. LSD passes over the tile id (2 for up to 65,536 tiles): a stable sort
 //    by tile keeps the depth order inside each tile, so the result is the
 //    full-key order bit for bit, with a fraction of the traffic.
@@ -29,22 +30,17 @@
 // per-warp ranking with match_any in index order, per-tile prefix over
 // warps, staging in shared memory by digit, coalesced writes; the next
 // tile's keys and values are loaded into registers while the current tile is
-// staged and written); each block owns one contiguous chunk of the input.  No kernel waits on another
-// block; there are no spin loops.
+// staged and written); each block owns one contiguous chunk of the input.
+// No kernel waits on another block; there are no spin loops.
 #include <algorithm>
 #include <atomic>
 
 #include "common.cuh"
+#include "spans.cuh"
 
 namespace gs {
 
 namespace {
-
-__device__ __forceinline__ uint32_t rect_count(uint2 rc) {
-    uint32_t x0 = rc.x & 0xffffu, y0 = rc.x >> 16, x1 = rc.y & 0xffffu, y1 = rc.y >> 16;
-    if (x0 > x1 || y0 > y1) return 0u;
-    return (x1 - x0 + 1u) * (y1 - y0 + 1u);
-}
 
 template <int NT>
 __device__ __forceinline__ unsigned long long block_sum_u64(unsigned long long v, unsigned long long *sh) {
@@ -55,18 +51,6 @@ __device__ __forceinline__ unsigned long long block_sum_u64(unsigned long long v
     if (threadIdx.x == 0)
         for (int w = 0; w < NT / 32; w++) t += sh[w];
     return t;  // valid in thread 0
-}
-
-// Depth keys of the records for the first stage: float bits of the depth
-// (ordered like the depths, which are positive), culled records last; the
-// value is the record index.  Also stores the record count for the sort.
-__global__ void k_rec_keys(const uint2 *__restrict__ rect, const float *__restrict__ depth, long long R,
-                           uint32_t *__restrict__ keys, uint32_t *__restrict__ vals, Stats *__restrict__ stats) {
-    const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r == 0) stats->num_records = (unsigned long long)R;
-    if (r >= R) return;
-    keys[r] = rect_count(rect[r]) ? __float_as_uint(depth[r]) : 0xffffffffu;
-    vals[r] = (uint32_t)r;
 }
 
 // perm (optional): the order in which records are visited; NULL = record order.
@@ -125,90 +109,6 @@ k_pair_scan(unsigned long long *__restrict__ sums, int nb, long long capacity, S
     }
 }
 
-// ---------------------------------------------------- exact tile binning
-//
-// With exact tiles a record is listed only for the tiles of its rectangle
-// that its ellipse P(d) <= F - lmin (P = -(A dx^2 + B dx dy + C dy^2), the
-// splat's base-2 exponent) can meet: in every tile row the pixel centres
-// where a Gaussian reaches alpha_min lie between the x-extremes of the
-// ellipse within the row's y-range, a contiguous run of tiles.  The test
-// uses the ellipse enlarged by 2^-8 |F - lmin| + 2^-14 M (M bounds P's
-// terms over the whole rectangle), four times the margins of the render's
-// band culling, and widens each run by 0.02 px + 2^-10 of its offsets, so
-// every band the render would keep lies in a listed tile: the image is the
-// same, bit for bit, as with whole rectangles.  A degenerate or non-finite
-// ellipse keeps whole rows.
-struct RowSpanner {
-    float mx, my, qb, lim4a, D, ymax, yR, inv2a, full;  // full != 0: whole rows
-};
-
-// The span arithmetic is written with explicitly rounded operations (no
-// contraction into fused multiply-adds), so that the pair count and the
-// emission, separate kernels, compute every span bit for bit alike.
-__device__ __forceinline__ float mul_(float a, float b) { return __fmul_rn(a, b); }
-__device__ __forceinline__ float add_(float a, float b) { return __fadd_rn(a, b); }
-__device__ __forceinline__ float sub_(float a, float b) { return __fsub_rn(a, b); }
-
-__device__ __forceinline__ RowSpanner make_spanner(float4 s0, float4 s1, float lmin, uint2 rc, const gs_frame &fr,
-                                                   int T) {
-    RowSpanner s;
-    s.mx = s0.x;
-    s.my = s0.y;
-    const float qa = -s0.z, qb = -s0.w, qc = -s1.x;
-    s.qb = qb;
-    const float lim0 = sub_(s1.y, lmin);
-    const float x0 = (float)((rc.x & 0xffffu) * (uint32_t)T), x1 = (float)((rc.y & 0xffffu) * (uint32_t)T + T - 1);
-    const float y0 = (float)(fr.row0 + (int)(rc.x >> 16) * T), y1 = (float)(fr.row0 + (int)(rc.y >> 16) * T + T - 1);
-    const float Rx = fmaxf(fabsf(sub_(x0, s.mx)), fabsf(sub_(x1, s.mx)));
-    const float Ry = fmaxf(fabsf(sub_(y0, s.my)), fabsf(sub_(y1, s.my)));
-    const float M = add_(add_(mul_(mul_(qa, Rx), Rx), mul_(mul_(fabsf(qb), Rx), Ry)), mul_(mul_(qc, Ry), Ry));
-    const float lim = add_(add_(lim0, mul_(fabsf(lim0), 0x1p-8f)), mul_(M, 0x1p-14f));
-    s.D = sub_(mul_(mul_(4.f, qa), qc), mul_(qb, qb));
-    const bool ok = qa > 0.f && qc > 0.f && s.D > 0.f && lim > 0.f && isfinite(lim) && isfinite(s.D) &&
-                    isfinite(s.mx) && isfinite(s.my) && isfinite(qb);
-    s.full = ok ? 0.f : 1.f;
-    s.lim4a = mul_(mul_(4.f, qa), lim);
-    s.inv2a = __fdiv_rn(1.f, mul_(2.f, qa));
-    // largest |y| on the ellipse (widened), and the y of its rightmost point
-    // (the leftmost is at -yR)
-    s.ymax = ok ? add_(mul_(__fsqrt_rn(__fdiv_rn(s.lim4a, s.D)), 1.f + 0x1p-12f), 1e-3f) : 0.f;
-    const float xm = ok ? __fsqrt_rn(__fdiv_rn(mul_(mul_(4.f, qc), lim), s.D)) : 0.f;
-    s.yR = ok ? __fdiv_rn(mul_(-qb, xm), mul_(2.f, qc)) : 0.f;
-    return s;
-}
-
-// Tile columns [lo, hi] of tile row ty within the rectangle's columns
-// [rx0, rx1] (lo > hi: none).
-__device__ __forceinline__ void row_span(const RowSpanner &s, int ty, int rx0, int rx1, const gs_frame &fr, int T,
-                                         int &lo, int &hi) {
-    lo = rx0;
-    hi = rx1;
-    if (s.full != 0.f) return;
-    const float ylo = (float)(fr.row0 + ty * T), yhi = (float)min(fr.row0 + ty * T + T - 1, fr.height - 1);
-    const float a = fmaxf(sub_(ylo, s.my), -s.ymax), b = fminf(sub_(yhi, s.my), s.ymax);
-    if (a > b) {
-        lo = 1;
-        hi = 0;
-        return;
-    }
-    // the x-extremes over y in [a, b]: x+(y) is concave, largest at the
-    // clamped y of the rightmost point; x-(y) is its mirror
-    const float yr = fminf(fmaxf(s.yR, a), b), yl = fminf(fmaxf(-s.yR, a), b);
-    const float rr = __fsqrt_rn(fmaxf(0.f, sub_(s.lim4a, mul_(mul_(s.D, yr), yr))));
-    const float rl = __fsqrt_rn(fmaxf(0.f, sub_(s.lim4a, mul_(mul_(s.D, yl), yl))));
-    const float Xb = mul_(add_(mul_(-s.qb, yr), rr), s.inv2a);
-    const float Xa = mul_(sub_(mul_(-s.qb, yl), rl), s.inv2a);
-    const float w = add_(add_(0.02f, mul_(0x1p-10f, add_(fabsf(Xa), fabsf(Xb)))), mul_(0x1p-12f, fabsf(s.mx)));
-    const float xa = fminf(fmaxf(sub_(add_(s.mx, Xa), w), -1e9f), 1e9f);
-    const float xb = fminf(fmaxf(add_(add_(s.mx, Xb), w), -1e9f), 1e9f);
-    // T is 8, 16 or 32: x / T and x * (1 / T) are the same real number
-    // (a power-of-two scaling), so the rounded product equals the rounded
-    // quotient bit for bit
-    const float invT = T == 8 ? 0.125f : (T == 16 ? 0.0625f : 0.03125f);
-    lo = max(rx0, (int)floorf(mul_(xa, invT)));
-    hi = min(rx1, (int)floorf(mul_(xb, invT)));
-}
-
 // Pairs of each emission block with exact tiles (as k_pair_count); also
 // each record's pairs and non-empty rows, by sorted position, for the
 // emission.
@@ -218,18 +118,39 @@ k_pair_count_exact(const gs_frame *__restrict__ frames, int F, int T, float lmin
                    unsigned long long *__restrict__ sums, uint2 *__restrict__ rec_pairs) {
     __shared__ unsigned long long sh[kEmitThreads / 32];
     const long long base = (long long)blockIdx.x * kEmitItems;
+    constexpr int PER = kEmitItems / kEmitThreads;
+    // the gathers of the thread's records are issued together (records i =
+    // threadIdx.x + j * kEmitThreads, coalesced across the block)
+    uint32_t r[PER];
+    uint2 rc[PER];
+    float4 s0[PER], s1[PER];
+#pragma unroll
+    for (int j = 0; j < PER; j++) {
+        const long long p = base + threadIdx.x + j * kEmitThreads;
+        r[j] = p < R ? perm[p] : 0u;
+    }
+#pragma unroll
+    for (int j = 0; j < PER; j++) {
+        const long long p = base + threadIdx.x + j * kEmitThreads;
+        rc[j] = p < R ? rect[r[j]] : make_uint2(1u, 0u);
+    }
+#pragma unroll
+    for (int j = 0; j < PER; j++) {
+        const bool any = rect_count(rc[j]) != 0u;
+        s0[j] = any ? splat[2 * (long long)r[j]] : make_float4(0.f, 0.f, 0.f, 0.f);
+        s1[j] = any ? splat[2 * (long long)r[j] + 1] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
     unsigned long long c = 0;
-    for (int i = threadIdx.x; i < kEmitItems; i += kEmitThreads) {
-        const long long p = base + i;
+#pragma unroll
+    for (int j = 0; j < PER; j++) {
+        const long long p = base + threadIdx.x + j * kEmitThreads;
         if (p >= R) continue;
-        const long long r = (long long)perm[p];
-        const uint2 rc = rect[r];
         uint32_t np = 0, ns = 0;  // pairs and non-empty rows of the record
-        if (rect_count(rc) != 0u) {
-            const gs_frame &fr = frames[frame_of_record(frames, F, r)];
-            const RowSpanner sp = make_spanner(splat[2 * r], splat[2 * r + 1], lmin, rc, fr, T);
-            const int rx0 = (int)(rc.x & 0xffffu), rx1 = (int)(rc.y & 0xffffu);
-            for (int ty = (int)(rc.x >> 16); ty <= (int)(rc.y >> 16); ty++) {
+        if (rect_count(rc[j]) != 0u) {
+            const gs_frame &fr = frames[frame_of_record(frames, F, r[j])];
+            const RowSpanner sp = make_spanner(s0[j], s1[j], lmin, rc[j], fr, T);
+            const int rx0 = (int)(rc[j].x & 0xffffu), rx1 = (int)(rc[j].y & 0xffffu);
+            for (int ty = (int)(rc[j].x >> 16); ty <= (int)(rc[j].y >> 16); ty++) {
                 int lo, hi;
                 row_span(sp, ty, rx0, rx1, fr, T, lo, hi);
                 if (hi >= lo) {
@@ -487,17 +408,38 @@ __device__ __forceinline__ Chunk sort_chunk(unsigned long long P, int nb, int b)
     return {lo, hi};
 }
 
+// The input of a pass: key/value buffers, or (the first pass over the
+// records) the records themselves, keyed by the float bits of their depth
+// (positive, so ordered like the depths), culled records last, valued by
+// their index.
+template <typename K>
+struct PassInput {
+    const K *keys;
+    const uint32_t *vals;
+    const uint2 *rect;    // non-null: read the records instead
+    const float *depth;
+    const unsigned long long *count;  // items (device), or null: count_host
+    long long count_host;
+    __device__ __forceinline__ unsigned long long n() const {
+        return count ? *count : (unsigned long long)count_host;
+    }
+    __device__ __forceinline__ K key(long long i) const {
+        if (rect) return (K)(rect_count(rect[i]) ? __float_as_uint(depth[i]) : 0xffffffffu);
+        return keys[i];
+    }
+    __device__ __forceinline__ uint32_t val(long long i) const { return rect ? (uint32_t)i : vals[i]; }
+};
+
 template <typename K>
 __global__ void __launch_bounds__(kSortThreads)
-k_radix_hist(const K *__restrict__ keys, const unsigned long long *__restrict__ count, int shift, int nb,
-             uint32_t *__restrict__ hist) {
+k_radix_hist(const PassInput<K> in, int shift, int nb, uint32_t *__restrict__ hist) {
     __shared__ uint32_t h[kSortThreads / 32][kRadix];
     const int warp = threadIdx.x >> 5;
     for (int i = threadIdx.x; i < (kSortThreads / 32) * kRadix; i += kSortThreads) (&h[0][0])[i] = 0;
     __syncthreads();
-    const Chunk c = sort_chunk(*count, nb, blockIdx.x);
+    const Chunk c = sort_chunk(in.n(), nb, blockIdx.x);
     for (long long i = c.lo + threadIdx.x; i < c.hi; i += kSortThreads)
-        atomicAdd(&h[warp][(uint32_t)(keys[i] >> shift) & (kRadix - 1)], 1u);
+        atomicAdd(&h[warp][(uint32_t)(in.key(i) >> shift) & (kRadix - 1)], 1u);
     __syncthreads();
     for (int d = threadIdx.x; d < kRadix; d += kSortThreads) {
         uint32_t s = 0;
@@ -544,15 +486,17 @@ struct ScatterSmem {
     uint32_t wtot[kRadix / 32];
 };
 
+// ranges (optional, the last pass over tile keys): every tile's [start, end)
+// in the output, found from the staged, sorted items (min/max atomics over
+// the run boundaries; the ranges start at {UINT32_MAX, 0}).
 template <typename K>
 __global__ void __launch_bounds__(kSortThreads, 2)
-k_radix_scatter(const K *__restrict__ kin, const uint32_t *__restrict__ vin, K *__restrict__ kout,
-                uint32_t *__restrict__ vout, const unsigned long long *__restrict__ count, int shift, int nb,
-                const uint32_t *__restrict__ hist, const uint32_t *__restrict__ totals) {
+k_radix_scatter(const PassInput<K> in, K *__restrict__ kout, uint32_t *__restrict__ vout, int shift, int nb,
+                const uint32_t *__restrict__ hist, const uint32_t *__restrict__ totals, uint2 *__restrict__ ranges) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     ScatterSmem<K> &S = *reinterpret_cast<ScatterSmem<K> *>(smem_raw);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const Chunk c = sort_chunk(*count, nb, blockIdx.x);
+    const Chunk c = sort_chunk(in.n(), nb, blockIdx.x);
     // run[d] = (items of digits < d) + (items of digit d in earlier blocks)
     if (threadIdx.x < kRadix) {
         const uint32_t x = totals[threadIdx.x];
@@ -581,8 +525,8 @@ k_radix_scatter(const K *__restrict__ kin, const uint32_t *__restrict__ vin, K *
     for (int r = 0; r < kSortItems; r++) {
         const long long idx = c.lo + (long long)warp * 32 * kSortItems + r * 32 + lane;
         const bool valid = idx < c.hi;
-        kn[r] = valid ? kin[idx] : K(0);
-        vn[r] = valid ? vin[idx] : 0u;
+        kn[r] = valid ? in.key(idx) : K(0);
+        vn[r] = valid ? in.val(idx) : 0u;
     }
     for (long long t0 = c.lo; t0 < c.hi; t0 += kSortTile) {
         for (int i = lane; i < kRadix; i += 32) S.wcnt[warp][i] = 0;
@@ -614,8 +558,8 @@ k_radix_scatter(const K *__restrict__ kin, const uint32_t *__restrict__ vin, K *
             for (int r = 0; r < kSortItems; r++) {
                 const long long idx = t0 + kSortTile + (long long)warp * 32 * kSortItems + r * 32 + lane;
                 const bool valid = idx < c.hi;
-                kn[r] = valid ? kin[idx] : K(0);
-                vn[r] = valid ? vin[idx] : 0u;
+                kn[r] = valid ? in.key(idx) : K(0);
+                vn[r] = valid ? in.val(idx) : 0u;
             }
         }
         __syncthreads();
@@ -665,6 +609,15 @@ k_radix_scatter(const K *__restrict__ kin, const uint32_t *__restrict__ vin, K *
             const uint32_t pos = S.run[d] + (uint32_t)i - S.tstart[d];
             kout[pos] = key;
             vout[pos] = S.sval[i];
+            if (ranges) {
+                // within a digit's run the staged keys are in output order, so a
+                // tile's items here are contiguous; its neighbours across run
+                // edges were staged by other tiles or blocks (min/max settle it)
+                const uint32_t t = (uint32_t)key;
+                const int r0 = (int)S.tstart[d], r1 = r0 + (int)S.tcnt[d];
+                if (i == r0 || S.skey[i - 1] != key) atomicMin(&ranges[t].x, pos);
+                if (i + 1 == r1 || S.skey[i + 1] != key) atomicMax(&ranges[t].y, pos + 1u);
+            }
         }
         __syncthreads();
         for (int d = threadIdx.x; d < kRadix; d += kSortThreads) S.run[d] += S.tcnt[d];
@@ -692,16 +645,22 @@ __global__ void k_tile_ranges(const K *__restrict__ keys, const unsigned long lo
 constexpr int kOrderBuckets = 33;
 
 __global__ void __launch_bounds__(1024)
-k_tile_order(const uint2 *__restrict__ ranges, int T, uint32_t *__restrict__ order) {
+k_tile_order(uint2 *__restrict__ ranges, int T, uint32_t *__restrict__ order) {
     __shared__ uint32_t cnt[kOrderBuckets], base[kOrderBuckets];
     if (threadIdx.x < kOrderBuckets) cnt[threadIdx.x] = 0;
     __syncthreads();
     auto bucket = [](uint32_t len) { return len == 0 ? 0u : (uint32_t)(32 - __clz(len)); };  // 0..32
     const int lane = threadIdx.x & 31;
+    // empty tiles come as {UINT32_MAX, 0} from the sort and leave as {0, 0};
     // warp-aggregated counting: one shared atomic per distinct bucket per warp
     for (int t0 = 0; t0 < T; t0 += blockDim.x) {
         const int t = t0 + threadIdx.x;
-        const uint32_t k = t < T ? bucket(ranges[t].y - ranges[t].x) : (uint32_t)(kOrderBuckets + lane);
+        uint2 rg = t < T ? ranges[t] : make_uint2(0u, 0u);
+        if (t < T && rg.x > rg.y) {
+            rg = make_uint2(0u, 0u);
+            ranges[t] = rg;
+        }
+        const uint32_t k = t < T ? bucket(rg.y - rg.x) : (uint32_t)(kOrderBuckets + lane);
         const uint32_t peers = __match_any_sync(0xffffffffu, k);
         if (t < T && (__ffs(peers) - 1) == lane) atomicAdd(&cnt[k], (uint32_t)__popc(peers));
     }
@@ -741,16 +700,32 @@ int full_key_passes(int num_tiles) { return radix_passes(num_tiles) + 32 / kRadi
 
 namespace {
 
-// One LSD pass (histogram, column scan, scatter) over *count items.
+// One LSD pass (histogram, column scan, scatter) over the input's items;
+// with `ranges`, the last pass over tile keys also finds the tile ranges.
+template <typename K>
+cudaError_t radix_pass(const PassInput<K> &in, K *kout, uint32_t *vout, int shift, int nb, uint32_t *hist,
+                       cudaStream_t s, uint2 *ranges = nullptr) {
+    uint32_t *totals = hist + (size_t)kRadix * nb;
+    k_radix_hist<K><<<nb, kSortThreads, 0, s>>>(in, shift, nb, hist);
+    k_radix_colscan<<<kRadix, kColThreads, 0, s>>>(hist, nb, totals);
+    k_radix_scatter<K><<<nb, kSortThreads, sizeof(ScatterSmem<K>), s>>>(in, kout, vout, shift, nb, hist, totals,
+                                                                        ranges);
+    return cudaGetLastError();
+}
+
+// One pass over key/value buffers of *count items (count_host items if
+// count is null).
 template <typename K>
 cudaError_t radix_pass(const K *kin, const uint32_t *vin, K *kout, uint32_t *vout, const unsigned long long *count,
-                       int shift, int nb, uint32_t *hist, cudaStream_t s) {
-    uint32_t *totals = hist + (size_t)kRadix * nb;
-    k_radix_hist<K><<<nb, kSortThreads, 0, s>>>(kin, count, shift, nb, hist);
-    k_radix_colscan<<<kRadix, kColThreads, 0, s>>>(hist, nb, totals);
-    k_radix_scatter<K><<<nb, kSortThreads, sizeof(ScatterSmem<K>), s>>>(kin, vin, kout, vout, count, shift, nb, hist,
-                                                                        totals);
-    return cudaGetLastError();
+                       int shift, int nb, uint32_t *hist, cudaStream_t s, long long count_host = 0,
+                       uint2 *ranges = nullptr) {
+    return radix_pass(PassInput<K>{kin, vin, nullptr, nullptr, count, count_host}, kout, vout, shift, nb, hist, s,
+                      ranges);
+}
+
+__global__ void k_ranges_init(uint2 *__restrict__ ranges, int T) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < T) ranges[t] = make_uint2(0xffffffffu, 0u);
 }
 
 template <typename K>
@@ -786,11 +761,13 @@ cudaError_t launch_bin_sort(const gs_batch *b, const gs_opts *o, const Layout &L
                                  (int)sizeof(EmitExactSmem));
     if (e != cudaSuccess) return e;
     if (L.emit_blocks > 0) {
-        // stage 1: stable depth order of the records (4 passes, ends in buffer 0)
-        k_rec_keys<<<(int)((R + 255) / 256), 256, 0, s>>>(rect, depth, R, rkeys[0], rvals[0], stats);
-        for (int p = 0; p < 4 && e == cudaSuccess; p++)
-            e = radix_pass(rkeys[p & 1], rvals[p & 1], rkeys[(p + 1) & 1], rvals[(p + 1) & 1], &stats->num_records,
-                           8 * p, L.rec_sort_blocks, hist, s);
+        // stage 1: stable depth order of the records (4 passes, ends in buffer 0;
+        // the first reads the records' depths and rectangles)
+        e = radix_pass(PassInput<uint32_t>{nullptr, nullptr, rect, depth, nullptr, R}, rkeys[1], rvals[1], 0,
+                       L.rec_sort_blocks, hist, s);
+        for (int p = 1; p < 4 && e == cudaSuccess; p++)
+            e = radix_pass(rkeys[p & 1], rvals[p & 1], rkeys[(p + 1) & 1], rvals[(p + 1) & 1],
+                           (const unsigned long long *)nullptr, 8 * p, L.rec_sort_blocks, hist, s, R);
         if (e != cudaSuccess) return e;
         // stage 2: pairs emitted in that order (exact tiles or whole rectangles)
         if (exact) {
@@ -812,16 +789,24 @@ cudaError_t launch_bin_sort(const gs_batch *b, const gs_opts *o, const Layout &L
         e = cudaMemsetAsync(&stats->num_pairs, 0, sizeof(unsigned long long), s);
     }
     if (e == cudaSuccess) e = cudaGetLastError();
-    // stage 3: stable passes over the tile bits only (end in buffer 0)
+    // stage 3: stable passes over the tile bits only (end in buffer 0); the
+    // last one also finds the tile ranges (empty tiles stay {UINT32_MAX, 0}
+    // until k_tile_order writes them as {0, 0})
+    if (e == cudaSuccess) {
+        k_ranges_init<<<(b->num_tiles + 255) / 256, 256, 0, s>>>(ranges, b->num_tiles);
+        e = cudaGetLastError();
+    }
     int cur = L.first_buffer;
     for (int p = 0; p < L.passes && e == cudaSuccess; p++) {
         e = radix_pass(keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], &stats->num_pairs, 8 * p, L.sort_blocks,
-                       hist, s);
+                       hist, s, 0, p == L.passes - 1 ? ranges : nullptr);
         cur ^= 1;
     }
+    if (e == cudaSuccess && L.passes == 0) {  // a single tile: no pass, its range is every pair
+        k_tile_ranges<uint32_t><<<1216, 256, 0, s>>>(keys[0], &stats->num_pairs, ranges);
+        e = cudaGetLastError();
+    }
     if (e != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(ranges, 0, sizeof(uint2) * (size_t)b->num_tiles, s)) != cudaSuccess) return e;
-    k_tile_ranges<uint32_t><<<1216, 256, 0, s>>>(keys[0], &stats->num_pairs, ranges);
     k_tile_order<<<1, 1024, 0, s>>>(ranges, b->num_tiles, reinterpret_cast<uint32_t *>(ws + L.order));
     return cudaGetLastError();
 }

@@ -100,6 +100,19 @@ __device__ __forceinline__ float rcp_approx(float x) {
     return y;
 }
 
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Tiles of a packed rectangle (x0 | y0 << 16, x1 | y1 << 16), 0 if empty.
+__device__ __forceinline__ uint32_t rect_count(uint2 rc) {
+    uint32_t x0 = rc.x & 0xffffu, y0 = rc.x >> 16, x1 = rc.y & 0xffffu, y1 = rc.y >> 16;
+    if (x0 > x1 || y0 > y1) return 0u;
+    return (x1 - x0 + 1u) * (y1 - y0 + 1u);
+}
+
 constexpr float kLog2e = 1.4426950408889634f;
 constexpr float kLn2 = 0.6931471805599453f;
 

@@ -126,14 +126,15 @@ __device__ __forceinline__ void camera_point(const float (&X)[3], const float *_
     }
 }
 
-// (hi + lo) / z for z = zh + zl, to about 2^-46 relative: the quotient of
-// the high parts rounded, its remainder (exact by the fma) plus the low
-// parts, divided again.
-__device__ __forceinline__ void ff_div(float xh, float xl, float zh, float zl, float &q, float &ql) {
-    q = __fdiv_rn(xh, zh);
+// (xh + xl) / (zh + zl) as q + ql, to a few 2^-48 relative, from an
+// approximate reciprocal iz of zh: q = xh iz is off by a few 2^-24; its
+// residual xh - q zh (one fma), plus the low parts, times iz is the
+// correction, whose own error is of second order.
+__device__ __forceinline__ void ff_div(float xh, float xl, float zh, float zl, float iz, float &q, float &ql) {
+    q = __fmul_rn(xh, iz);
     float r = __fmaf_rn(-q, zh, xh);
-    r = __fadd_rn(r, __fsub_rn(xl, __fmul_rn(q, zl)));
-    ql = __fdiv_rn(r, zh);
+    r = __fadd_rn(r, __fmaf_rn(-q, zl, xl));
+    ql = __fmul_rn(r, iz);
 }
 
 // f (q + ql) + c rounded once (two_prod and two_sum keep the parts exact).
@@ -153,10 +154,10 @@ __device__ __forceinline__ bool project_frame(const GaussParams &G, const float 
     // at the near plane and the depth order are decided on it
     const float z = Q.p[2];
     if (!(z > o.near_z)) return false;
+    Q.iz = rcp_approx(z);
     float xl, yl;
-    ff_div(Q.p[0], pl[0], z, pl[2], Q.xz, xl);
-    ff_div(Q.p[1], pl[1], z, pl[2], Q.yz, yl);
-    Q.iz = 1.f / z;
+    ff_div(Q.p[0], pl[0], z, pl[2], Q.iz, Q.xz, xl);
+    ff_div(Q.p[1], pl[1], z, pl[2], Q.iz, Q.yz, yl);
     // J at x/z, y/z limited to the field of view widened by frustum_margin
     // of the image size per side (bounds the footprint of far off-image centres)
     Q.jx = Q.xz;
