@@ -383,6 +383,17 @@ gs_status gs_ngp_backward(const gs_ngp *cfg, const float *theta, const float *X,
  * d_theta[0].  Errors: GS_ERR_INVALID_ARG (NULL out), GS_ERR_CUDA. */
 gs_status gs_ngp_fault(uint32_t *out);
 
+/* Sets the bound on the hash-grid kernels' waits for their tensor-core MMAs,
+ * in ns, for every later call on the current device (host; default one
+ * second, the value to restore).  0 makes a wait give up as soon as one
+ * non-blocking test finds the MMAs unfinished, which lets a test drive the
+ * timeout path (gs_ngp_fault then reports bit 0).  After a timeout the
+ * kernels still wait, for at most one second whatever this bound, for the
+ * MMAs in flight before they release tensor memory.  The paper has no
+ * counterpart: it bounds the waits of this implementation.
+ * Errors: GS_ERR_CUDA. */
+gs_status gs_ngp_set_wait_limit(uint64_t ns);
+
 /* Accumulated-LiDAR downsampling (Sec. III-D): keep one point per occupied
  * voxel of edge `voxel`, the point of smallest index.  A point's voxel is
  * (floor(x / voxel), floor(y / voxel), floor(z / voxel)) with the quotients

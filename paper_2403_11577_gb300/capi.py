@@ -293,6 +293,12 @@ def gs_ngp_backward(cfg, theta, X, d_rgb, d_logit_opacity, d_log_scale, d_quat, 
                                  _ptr(d_theta, F32, "d_theta"), _stream(stream)), "gs_ngp_backward")
 
 
+def gs_ngp_set_wait_limit(ns):
+    """Bound (ns) on the hash-grid kernels' waits for their MMAs; 0 makes the
+    first unfinished wait give up (a test hook); default 10**9."""
+    _check(lib().gs_ngp_set_wait_limit(C.c_uint64(int(ns))), "gs_ngp_set_wait_limit")
+
+
 def gs_ngp_fault():
     """Read and clear the hash-grid kernels' fault word (bit 0: a tensor-core
     wait ran out; that call's outputs are incomplete)."""

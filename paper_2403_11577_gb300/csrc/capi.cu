@@ -34,6 +34,7 @@ long long ngp_param_count(const gs_ngp *c);
 cudaError_t launch_ngp_fwd(const gs_ngp *c, const float *theta, const float *X, long long n, float *rgb,
                            float *logit_o, float *log_s, float *quat, cudaStream_t s);
 cudaError_t ngp_fault(unsigned int *out);
+cudaError_t ngp_set_wait_limit(unsigned long long ns);
 cudaError_t launch_ngp_bwd(const gs_ngp *c, const float *theta, const float *X, long long n, const float *d_rgb,
                            const float *d_logit_o, const float *d_log_s, const float *d_quat, float *d_theta,
                            cudaStream_t s);
@@ -310,6 +311,8 @@ gs_status gs_loss_photo(const gs_batch *b, const float *rgb, const float *target
 }
 
 int64_t gs_ngp_param_count(const gs_ngp *cfg) { return ngp_param_count(cfg); }
+
+gs_status gs_ngp_set_wait_limit(uint64_t ns) { return cuda_status(ngp_set_wait_limit(ns)); }
 
 gs_status gs_ngp_fault(uint32_t *out) {
     if (!out) return GS_ERR_INVALID_ARG;

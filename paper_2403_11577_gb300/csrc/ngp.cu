@@ -54,7 +54,7 @@ constexpr int kH = 64, kO = 11, kMaxLevels = 16;
 constexpr int kTile = 128;     // points per tile: the MMA's M
 constexpr int kThreads = 256;  // 8 warps
 constexpr int kK1 = 32;        // encoding columns (2L, zero padded)
-constexpr unsigned long long kWaitNs = 1000000000ull;  // bound on every mbarrier wait
+constexpr unsigned long long kWaitNs = 1000000000ull;  // default bound of the waits; the drain wait's bound
 
 // Byte offsets of an MN-major operand: true when the descriptor's leading
 // byte offset is the stride along M/N and its stride byte offset the stride
@@ -62,6 +62,9 @@ constexpr unsigned long long kWaitNs = 1000000000ull;  // bound on every mbarrie
 constexpr bool kMnLboIsMn = false;
 
 __device__ unsigned int g_ngp_fault;  // bit 0: an mbarrier wait ran out
+// Bound, in ns, on the waits for the tensor cores' MMAs (gs_ngp_set_wait_limit);
+// 0: a wait gives up as soon as one non-blocking test finds its phase open.
+__device__ unsigned long long g_ngp_wait_ns = kWaitNs;
 
 struct NgpArgs {
     float lo[3], inv_ext[3];
@@ -149,8 +152,19 @@ __device__ __forceinline__ unsigned long long global_ns() {
     return t;
 }
 
-// Wait for phase `parity` of the mbarrier for at most kWaitNs; false on timeout.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+// Wait for phase `parity` of the mbarrier for at most limit_ns; false on
+// timeout.  With limit 0 one non-blocking test decides.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, unsigned long long limit_ns) {
+    if (limit_ns == 0) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.b32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        return ok != 0;
+    }
     const unsigned long long t0 = global_ns();
     while (true) {
         uint32_t ok;
@@ -161,9 +175,18 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
             : "r"(bar), "r"(parity)
             : "memory");
         if (ok) return true;
-        if (global_ns() - t0 > kWaitNs) return false;
+        if (global_ns() - t0 > limit_ns) return false;
     }
 }
+
+// A wait for the MMAs (the settable bound).
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+    return mbar_wait(bar, parity, *(volatile unsigned long long *)&g_ngp_wait_ns);
+}
+
+// After a timeout: the wait for the MMAs still in flight before the tensor
+// memory is released (always the fixed one-second bound).
+__device__ __forceinline__ bool mbar_drain(uint32_t bar, uint32_t parity) { return mbar_wait(bar, parity, kWaitNs); }
 
 // 32 lanes x 16 consecutive FP32 columns of tensor memory (waits for the load).
 // Every lane of the warp executes it.
@@ -435,7 +458,7 @@ __device__ __forceinline__ void init_bar(uint32_t bar) {
 __device__ __forceinline__ void on_timeout(const Sync &s) {
     if (threadIdx.x == 0) {
         atomicOr(&g_ngp_fault, 1u);
-        mbar_wait(s.bar, s.phase);
+        mbar_drain(s.bar, s.phase);
     }
 }
 
@@ -815,7 +838,7 @@ k_ngp_bwd(NgpArgs a, const float *__restrict__ theta, const float *__restrict__ 
     if (*abort) {
         if (threadIdx.x == 0) {
             atomicOr(&g_ngp_fault, 1u);
-            mbar_wait(s.bar, s.phase);  // the MMAs still in flight, bounded
+            mbar_drain(s.bar, s.phase);  // the MMAs still in flight, bounded
             atomicAdd(d_theta, __int_as_float(0x7fc00000));  // poison: the gradient is incomplete
         }
     } else if (K > 0) {
@@ -932,6 +955,8 @@ cudaError_t launch_ngp_bwd(const gs_ngp *c, const float *theta, const float *X, 
     k_ngp_bwd<<<grid, kBwdThreads, bwd_smem(), s>>>(a, theta, X, n, d_rgb, d_logit_o, d_log_s, d_quat, d_theta);
     return cudaGetLastError();
 }
+
+cudaError_t ngp_set_wait_limit(unsigned long long ns) { return cudaMemcpyToSymbol(g_ngp_wait_ns, &ns, sizeof(ns)); }
 
 cudaError_t ngp_fault(unsigned int *out) {
     unsigned int v = 0, z = 0;

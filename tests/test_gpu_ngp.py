@@ -176,3 +176,38 @@ def test_ngp_backward_on_coherent_points():
     for name, numel in cfg.blocks():
         assert rel_l2(got[off:off + numel], ref[off:off + numel]) <= 1e-4, name
         off += numel
+
+
+def test_ngp_wait_limit_runs_out_and_the_context_stays_usable():
+    """The waits for the tensor cores' MMAs are bounded.  With the bound set
+    to 0, the first wait that finds its MMAs unfinished gives up: the
+    backward reports bit 0 of gs_ngp_fault and poisons d_theta[0] with NaN
+    (its gradient is incomplete), after a bounded drain of the MMAs in flight.
+    With the default bound restored, the next call is clean and gives the
+    gradient of a call made before (to the rounding of the table atomics)."""
+    cfg = ngp.HashGridConfig(LO, HI, log2_table=12, levels=16)
+    o, theta = _random_theta(cfg, 5)
+    mlp = ngp.HashGridMLP(cfg)
+    mlp.theta.copy_(torch.from_numpy(theta))
+    rng = np.random.default_rng(6)
+    X = torch.from_numpy(_points(rng, 1000)).cuda()
+    d = {k: torch.from_numpy(rng.normal(size=s).astype(np.float32)).cuda()
+         for k, s in (("rgb", (1000, 3)), ("logit_opacity", (1000,)), ("log_scale", (1000, 3)),
+                      ("quat", (1000, 4)))}
+    assert capi.gs_ngp_fault() == 0
+    mlp.backward(X, d)
+    torch.cuda.synchronize()
+    before = mlp.grad.clone()
+    assert capi.gs_ngp_fault() == 0 and bool(torch.isfinite(before).all())
+    capi.gs_ngp_set_wait_limit(0)
+    try:
+        mlp.backward(X, d)
+        torch.cuda.synchronize()
+        assert capi.gs_ngp_fault() & 1
+        assert bool(torch.isnan(mlp.grad[0]))
+    finally:
+        capi.gs_ngp_set_wait_limit(10 ** 9)
+    mlp.backward(X, d)
+    torch.cuda.synchronize()
+    assert capi.gs_ngp_fault() == 0
+    assert rel_l2(mlp.grad.cpu().numpy(), before.cpu().numpy()) < 1e-5
