@@ -69,10 +69,11 @@ typedef struct {
  *   OR_FLAG_CLAMP_EDGE   a composited Gaussian's alpha lies within the bound
  *                        of alpha_max: the colour is continuous there, its
  *                        gradient is not.
- *   OR_FLAG_DEPTH_TIE    two consecutive contributors whose float32 depth
- *                        keys are at most one ulp apart, one of them with an
- *                        exact depth within the bound of a float32 rounding
- *                        boundary: their order is not decided.
+ *   OR_FLAG_DEPTH_TIE    two consecutive contributors whose order is not
+ *                        decided: one of them has an exact depth within the
+ *                        bound of a float32 rounding boundary, and its other
+ *                        candidate key would put the pair out of (key,
+ *                        index) order.
  *   OR_FLAG_NEAR_EDGE    a Gaussian whose float32 depth key is not decided
  *                        at the near plane would contribute.
  *   OR_FLAG_BRANCH_LIMIT more than OR_MAX_BRANCHES outcomes. */
@@ -282,6 +283,7 @@ typedef struct {
     int near_edge;      /* the near-plane culling is not decided in float32 */
     float zkey;         /* depth rounded to float32: the depth order's key */
     int zamb;           /* the exact depth lies within the bound of a float32 rounding boundary */
+    float zalt;         /* the other candidate key where zamb (the float across that boundary), else zkey */
     double dm[2];       /* bound on the float32 2D mean's error, px */
     double kq;          /* bound on the conic's share of the float32 exponent error, per unit of |e2| */
     double dF;          /* bound on the float32 log2 opacity's error */
@@ -375,6 +377,7 @@ static void project_one(const double *X, const double *q, const double *log_s, d
         P->zamb = (z - below < eps) || (above - z < eps);
         float near = (float)o->near_z;
         float other = z - below < eps ? nextafterf(k, -INFINITY) : nextafterf(k, INFINITY);
+        P->zalt = P->zamb ? other : k;
         P->near_edge = P->zamb && ((k > near) != (other > near));
     }
     int in_front = P->zkey > (float)o->near_z;
@@ -600,8 +603,8 @@ static void blend_pixel_path(const or_frame_state *S, double u, double v, const 
     B->ndec = 0;
     double T = 1.0;
     double eT = 0.0;                  /* bound on the float32 transmittance's relative error */
-    float kprev = 0.f;
-    int aprev = 0, have_prev = 0;
+    float kprev_max = 0.f;  /* the previous contributor's largest candidate key, and its index */
+    int gprev = -1;
     const double log2e = 1.0 / log(2.0);
     const double lmin = o->alpha_min > 0 ? log2(o->alpha_min) : -INFINITY;
     const double lmax = log2(o->alpha_max);
@@ -640,12 +643,16 @@ static void blend_pixel_path(const or_frame_state *S, double u, double v, const 
             stop = decide(B, path, stop);
         if (stop) break;
         if (near_clamp) B->flags |= OR_FLAG_CLAMP_EDGE;
-        /* consecutive contributors whose float32 order is not decided */
-        if (have_prev && (aprev || P->zamb) && (double)P->zkey - (double)kprev <= f32_spacing(P->zkey))
-            B->flags |= OR_FLAG_DEPTH_TIE;
-        kprev = P->zkey;
-        aprev = P->zamb;
-        have_prev = 1;
+        /* consecutive contributors whose float32 order is not decided: some
+         * choice of their candidate keys puts them out of (key, index) order */
+        {
+            const int gcur = S->order[i];
+            const float kmin = P->zalt < P->zkey ? P->zalt : P->zkey;
+            if (gprev >= 0 && (kmin < kprev_max || (kmin == kprev_max && gcur < gprev)))
+                B->flags |= OR_FLAG_DEPTH_TIE;
+            kprev_max = P->zalt > P->zkey ? P->zalt : P->zkey;
+            gprev = gcur;
+        }
         int k = B->n++;
         B->g[k] = S->order[i];
         B->alpha[k] = alpha;

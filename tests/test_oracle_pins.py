@@ -537,17 +537,23 @@ def test_depth_order_by_float32_key_and_index():
 
 
 def test_depth_tie_flag_on_an_undecided_rounding():
-    """Two contributors whose keys are one float32 step apart, one of them at
-    an exact rounding midpoint (its key is not decided): DEPTH_TIE.  Moved
-    1e-9 m off the midpoint, the keys are decided and nothing is flagged."""
+    """Two contributors, one at depth lo (a float) and one at the exact
+    midpoint between lo and the next float (its key is not decided: either
+    rounding is within the float32 evaluation's error).  With the midpoint
+    Gaussian first in index order, one rounding puts it before the other and
+    one after: DEPTH_TIE.  With it second in index order, both roundings give
+    the same order (equal keys go by index): no flag.  Moved 1e-9 m off the
+    midpoint, the key is decided: no flag."""
     lo, hi = _f32_neighbours(4.0)
     mid = 0.5 * (lo + hi)
-    for z, flagged in ((mid, True), (mid + 1e-9, False)):
-        sc = _single_scene([[0, 0, lo], [0, 0, z]], [[0.1] * 3] * 2, [0.0, 0.0], [[1, 0, 0], [0, 1, 0]])
+    for z, mid_first, flagged in ((mid, True, True), (mid, False, False), (mid + 1e-9, True, False)):
+        Xs = [[0, 0, z], [0, 0, lo]] if mid_first else [[0, 0, lo], [0, 0, z]]
+        sc = _single_scene(Xs, [[0.1] * 3] * 2, [0.0, 0.0], [[1, 0, 0], [0, 1, 0]])
         pr = oracle.project(sc, CAM, np.eye(3), np.zeros(3), oracle.Opts())
-        assert bool(pr["zamb"][1]) == flagged and not pr["zamb"][0]
+        k = 0 if mid_first else 1
+        assert bool(pr["zamb"][k]) == (z == mid) and not pr["zamb"][1 - k]
         flags = oracle.render(sc, FRAME, np.zeros(6), 0.0, oracle.Opts(bg=BG), pixels=[[32, 24]])[3]
-        assert flags[0] == (oracle.FLAG_DEPTH_TIE if flagged else 0)
+        assert flags[0] == (oracle.FLAG_DEPTH_TIE if flagged else 0), (z, mid_first)
 
 
 def test_near_plane_culling_decided_in_float32():
