@@ -146,18 +146,34 @@ __device__ __forceinline__ float ff_affine(float f, float q, float ql, float c) 
     return __fadd_rn(sh, __fadd_rn(se, ae));
 }
 
+// kExact (the forward): p in float-float, the depth key and the 2D mean
+// rounded once, culling at the near plane on the key.  Otherwise (the
+// backward, whose records were kept by the forward's rectangles): p in plain
+// float arithmetic, no near-plane test and no mean; every quantity the
+// gradient needs (J, the covariance, the conic) to float accuracy.
+template <bool kExact>
 __device__ __forceinline__ bool project_frame(const GaussParams &G, const float *__restrict__ P,
                                               const gs_frame &fr, const gs_opts &o, Proj &Q) {
-    float pl[3];
-    camera_point(G.X, P, Q.p, pl);
+    float pl[3] = {0.f, 0.f, 0.f};
+    if (kExact) {
+        camera_point(G.X, P, Q.p, pl);
+    } else {
+        const float d0 = (G.X[0] - P[9]) - P[12], d1 = (G.X[1] - P[10]) - P[13], d2 = (G.X[2] - P[11]) - P[14];
+        for (int i = 0; i < 3; i++) Q.p[i] = P[3 * i] * d0 + P[3 * i + 1] * d1 + P[3 * i + 2] * d2;
+    }
     // the depth key is the float nearest to the exact depth: the culling
     // at the near plane and the depth order are decided on it
     const float z = Q.p[2];
-    if (!(z > o.near_z)) return false;
+    if (kExact ? !(z > o.near_z) : !(z > 0.f)) return false;
     Q.iz = rcp_approx(z);
-    float xl, yl;
-    ff_div(Q.p[0], pl[0], z, pl[2], Q.iz, Q.xz, xl);
-    ff_div(Q.p[1], pl[1], z, pl[2], Q.iz, Q.yz, yl);
+    float xl = 0.f, yl = 0.f;
+    if (kExact) {
+        ff_div(Q.p[0], pl[0], z, pl[2], Q.iz, Q.xz, xl);
+        ff_div(Q.p[1], pl[1], z, pl[2], Q.iz, Q.yz, yl);
+    } else {
+        Q.xz = Q.p[0] * Q.iz;
+        Q.yz = Q.p[1] * Q.iz;
+    }
     // J at x/z, y/z limited to the field of view widened by frustum_margin
     // of the image size per side (bounds the footprint of far off-image centres)
     Q.jx = Q.xz;
@@ -193,6 +209,7 @@ __device__ __forceinline__ bool project_frame(const GaussParams &G, const float 
     Q.conic[0] = Q.cov[2] * idet;
     Q.conic[1] = -Q.cov[1] * idet;
     Q.conic[2] = Q.cov[0] * idet;
+    if (!kExact) return true;
     // the 2D mean, rounded once from fx x/z + cx, fy y/z + cy
     Q.mean[0] = ff_affine(fr.fx, Q.xz, xl, fr.cx);
     Q.mean[1] = ff_affine(fr.fy, Q.yz, yl, fr.cy);
@@ -227,7 +244,7 @@ k_project(const gs_frame *__restrict__ frames, int F, int N, const float *__rest
         if (g < fr.gauss_offset || g >= fr.gauss_offset + fr.gauss_count) continue;
         const long long r = fr.record_offset + (g - fr.gauss_offset);
         Proj Q;
-        bool vis = opaque_enough && project_frame(G, pose32 + kPose32Stride * f, fr, o, Q);
+        bool vis = opaque_enough && project_frame<true>(G, pose32 + kPose32Stride * f, fr, o, Q);
         uint2 rc = make_uint2(kEmptyLo, kEmptyHi);
         if (vis) {
             float rx = sqrtf(G.kext * Q.cov[0]) * 1.0001f + 0.01f;
@@ -309,7 +326,7 @@ k_project_bwd(const gs_frame *__restrict__ frames, int F, int N, const float *__
             bool vis = (rc.x & 0xffffu) <= (rc.y & 0xffffu);
             Proj Q;
             const float *P = pose32 + kPose32Stride * f;
-            if (vis && project_frame(G, P, fr, o, Q)) {
+            if (vis && project_frame<false>(G, P, fr, o, Q)) {
                 float4 g0 = grad2d[3 * r], g1 = grad2d[3 * r + 1], g2 = grad2d[3 * r + 2];
                 dc0 += g1.z; dc1 += g1.w; dc2 += g2.x;
                 dF += g1.y;

@@ -104,6 +104,18 @@ __device__ __forceinline__ float exponent2(float dx, float dy, float A, float B,
     return __fmaf_rn(dx, t, q);
 }
 
+// exponent2 for a thread's two vertically adjacent pixels (offsets dx and
+// dy.x, dy.y) in packed f32x2 arithmetic: each element is rounded exactly as
+// the scalar operations of exponent2 round it, so both give the same bits.
+__device__ __forceinline__ float2 exponent2x2(float dx, float2 dy, float A, float B, float C) {
+    const float2 dx2 = make_float2(dx, dx);
+    const float2 bdy = __fmul2_rn(make_float2(B, B), dy);
+    const float2 t = __ffma2_rn(make_float2(A, A), dx2, bdy);
+    const float2 cdy = __fmul2_rn(make_float2(C, C), dy);
+    const float2 q = __fmul2_rn(cdy, dy);
+    return __ffma2_rn(dx2, t, q);
+}
+
 // Whether a Gaussian with centre m, exponent coefficients (A, B, C), F =
 // log2 opacity and alpha box half-widths (rx, ry) can reach alpha >=
 // alpha_min at some point of the band [xlo, xhi] x [ylo, yhi].
@@ -282,6 +294,16 @@ __device__ __forceinline__ void fwd_item(int t, int rbase, Staged *st_all, unsig
             float e[PPT];
             bool ct[PPT];
             bool anyc = false;
+            if constexpr (PPT == 2) {
+                const float2 e2 = exponent2x2(dx, __fadd2_rn(make_float2(py[0], py[1]), make_float2(-a.y, -a.y)),
+                                              a.z, a.w, b.x);
+                const float2 ev = __fadd2_rn(e2, make_float2(b.y, b.y));
+                e[0] = ev.x;
+                e[1] = ev.y;
+                ct[0] = !done[0] && !(e2.x > 0.f) && !(ev.x < rp.lmin);
+                ct[1] = !done[1] && !(e2.y > 0.f) && !(ev.y < rp.lmin);
+                anyc = ct[0] || ct[1];
+            } else {
 #pragma unroll
             for (int k = 0; k < PPT; k++) {
                 const float e2 = exponent2(dx, py[k] - a.y, a.z, a.w, b.x);
@@ -289,10 +311,38 @@ __device__ __forceinline__ void fwd_item(int t, int rbase, Staged *st_all, unsig
                 ct[k] = !done[k] && !(e2 > 0.f) && !(e[k] < rp.lmin);
                 anyc |= ct[k];
             }
+            }
             if (!__any_sync(0xffffffffu, anyc)) continue;
             const uint4 z = st[j].z;
             const float cb = __uint_as_float(z.x);
             const int pos1 = (int)z.y + 1;
+            if constexpr (PPT == 2) {
+                // the two pixels side by side in packed f32x2 arithmetic
+                // (each element rounded as the scalar loop below rounds it)
+                const float2 al = make_float2(fminf(rp.amax, ex2_approx(e[0])), fminf(rp.amax, ex2_approx(e[1])));
+                const float2 T2 = make_float2(T[0], T[1]);
+                const float2 nT = __fmul2_rn(T2, __ffma2_rn(al, make_float2(-1.f, -1.f), make_float2(1.f, 1.f)));
+                const float2 wa = __fmul2_rn(al, T2);
+                const bool s0 = ct[0] && nT.x < rp.tmin, s1 = ct[1] && nT.y < rp.tmin;
+                const bool b0 = ct[0] && !s0, b1 = ct[1] && !s1;
+                done[0] = done[0] || s0;
+                done[1] = done[1] || s1;
+                evals += (unsigned)b0 + (unsigned)b1;
+                const float2 w = make_float2(b0 ? wa.x : 0.f, b1 ? wa.y : 0.f);
+                const float2 r = __ffma2_rn(make_float2(b.z, b.z), w, make_float2(c0[0], c0[1]));
+                const float2 g = __ffma2_rn(make_float2(b.w, b.w), w, make_float2(c1[0], c1[1]));
+                const float2 bl = __ffma2_rn(make_float2(cb, cb), w, make_float2(c2[0], c2[1]));
+                c0[0] = r.x;
+                c0[1] = r.y;
+                c1[0] = g.x;
+                c1[1] = g.y;
+                c2[0] = bl.x;
+                c2[1] = bl.y;
+                T[0] = b0 ? nT.x : T[0];
+                T[1] = b1 ? nT.y : T[1];
+                last[0] = b0 ? pos1 : last[0];
+                last[1] = b1 ? pos1 : last[1];
+            } else {
 #pragma unroll
             for (int k = 0; k < PPT; k++) {
                 const float alpha = fminf(rp.amax, ex2_approx(e[k]));
@@ -307,6 +357,7 @@ __device__ __forceinline__ void fwd_item(int t, int rbase, Staged *st_all, unsig
                 c2[k] = fmaf(cb, w, c2[k]);
                 T[k] = blend ? nT : T[k];
                 last[k] = blend ? pos1 : last[k];
+            }
             }
         }
         __syncwarp();
@@ -476,6 +527,18 @@ __device__ __forceinline__ void bwd_item(int t, int rbase, Staged *st_all, unsig
             float e[PPT], dy[PPT];
             bool ct[PPT];
             bool anyc = false;
+            if constexpr (PPT == 2) {
+                const float2 d2 = __fadd2_rn(make_float2(py[0], py[1]), make_float2(-a.y, -a.y));
+                dy[0] = d2.x;
+                dy[1] = d2.y;
+                const float2 e2 = exponent2x2(dx, d2, a.z, a.w, b.x);
+                const float2 ev = __fadd2_rn(e2, make_float2(b.y, b.y));
+                e[0] = ev.x;
+                e[1] = ev.y;
+                ct[0] = pos < last[0] && !(e2.x > 0.f) && !(ev.x < rp.lmin);
+                ct[1] = pos < last[1] && !(e2.y > 0.f) && !(ev.y < rp.lmin);
+                anyc = ct[0] || ct[1];
+            } else {
 #pragma unroll
             for (int k = 0; k < PPT; k++) {
                 dy[k] = py[k] - a.y;
@@ -484,10 +547,49 @@ __device__ __forceinline__ void bwd_item(int t, int rbase, Staged *st_all, unsig
                 ct[k] = pos < last[k] && !(e2 > 0.f) && !(e[k] < rp.lmin);
                 anyc |= ct[k];
             }
+            }
             if (!__any_sync(0xffffffffu, anyc)) continue;
             const float cb = __uint_as_float(z.x);
             // per-thread sums: sum de dx, sum de dy, dA, dB, dC, dF, dr, dg, db
             float sx = 0.f, sy = 0.f, dA = 0.f, dB = 0.f, dC = 0.f, dF = 0.f, dr = 0.f, dg = 0.f, db = 0.f;
+            if constexpr (PPT == 2) {
+                // the thread's two pixels side by side in packed f32x2
+                // arithmetic (the same terms as the scalar loop below)
+                const float G0 = ex2_approx(ct[0] ? e[0] : -INFINITY), G1 = ex2_approx(ct[1] ? e[1] : -INFINITY);
+                const float2 al = make_float2(fminf(rp.amax, G0), fminf(rp.amax, G1));
+                const float2 om = __ffma2_rn(al, make_float2(-1.f, -1.f), make_float2(1.f, 1.f));  // 1 - alpha
+                const float2 inv = make_float2(ct[0] ? rcp_approx(om.x) : 1.f, ct[1] ? rcp_approx(om.y) : 1.f);
+                const float2 T2 = __fmul2_rn(make_float2(T[0], T[1]), inv);  // T before this Gaussian
+                T[0] = T2.x;
+                T[1] = T2.y;
+                const float2 w = __fmul2_rn(al, T2);
+                const float2 gr = make_float2(g0[0], g0[1]), gg = make_float2(g1[0], g1[1]),
+                             gb = make_float2(g2[0], g2[1]);
+                const float2 wr = __fmul2_rn(w, gr), wg = __fmul2_rn(w, gg), wb = __fmul2_rn(w, gb);
+                const float2 cd = __ffma2_rn(make_float2(b.z, b.z), gr,
+                                             __ffma2_rn(make_float2(b.w, b.w), gg, __fmul2_rn(make_float2(cb, cb), gb)));
+                const float2 S2 = make_float2(S[0], S[1]);
+                const float2 dal = __ffma2_rn(T2, cd, __fmul2_rn(make_float2(-S2.x, -S2.y), inv));
+                const float2 Sn = __ffma2_rn(w, cd, S2);
+                S[0] = Sn.x;
+                S[1] = Sn.y;
+                float2 de = __fmul2_rn(dal, al);  // dL/de / ln 2
+                de.x = G0 > rp.amax ? 0.f : de.x;
+                de.y = G1 > rp.amax ? 0.f : de.y;
+                const float2 dx2 = make_float2(dx, dx), dy2 = make_float2(dy[0], dy[1]);
+                const float2 tx2 = __fmul2_rn(de, dx2), ty2 = __fmul2_rn(de, dy2);
+                const float2 a2 = __fmul2_rn(tx2, dx2), b2 = __fmul2_rn(tx2, dy2), c2 = __fmul2_rn(ty2, dy2);
+                sx = tx2.x + tx2.y;
+                sy = ty2.x + ty2.y;
+                dA = a2.x + a2.y;
+                dB = b2.x + b2.y;
+                dC = c2.x + c2.y;
+                dF = de.x + de.y;
+                dr = wr.x + wr.y;
+                dg = wg.x + wg.y;
+                db = wb.x + wb.y;
+                evals += (unsigned)ct[0] + (unsigned)ct[1];
+            } else {
 #pragma unroll
             for (int k = 0; k < PPT; k++) {
                 // a pixel that does not composite this Gaussian gets alpha = 0
@@ -512,6 +614,7 @@ __device__ __forceinline__ void bwd_item(int t, int rbase, Staged *st_all, unsig
                 sy += ty_;
                 dF += de;
                 evals += ct[k];
+            }
             }
             // record layout: (dmx, dmy, dA, dB), (dC, dF, dr, dg), (db, -, -, -)
             const float v8[8] = {sx, sy, dA, dB, dC, dF, dr, dg};
