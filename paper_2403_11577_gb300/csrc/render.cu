@@ -63,6 +63,17 @@ namespace {
 // halves of heavy tiles.
 __host__ __device__ constexpr int pix_per_thread(int tile) { return tile == 32 ? 4 : 2; }
 
+// The backward's pixels per thread: four at tiles 16 and 32 (16x8 bands, 8x8
+// in the halves of heavy tiles), which spreads each kept Gaussian's 9-value
+// warp reduction over twice the pixels of the forward's 8x8 bands; two at
+// tile 8.  GS_BWD_PPT16 overrides tile 16's value (2 or 4) at build time.
+#ifndef GS_BWD_PPT16
+#define GS_BWD_PPT16 4
+#endif
+__host__ __device__ constexpr int bwd_pix_per_thread(int tile) {
+    return tile == 8 ? 2 : (tile == 16 ? GS_BWD_PPT16 : 4);
+}
+
 // A work item of TILE-wide rows for NT threads at PPT pixels per thread.
 // A warp's band holds 32 * PPT pixels in the squarest shape the tile allows:
 // 8x4 (32 pixels), 8x8 (64) or 16x8 (128).  Of two bands of equal area the
@@ -87,6 +98,11 @@ struct Threads {
     static constexpr int NT = TILE * TILE / pix_per_thread(TILE);
 };
 
+template <int TILE>
+struct BwdThreads {
+    static constexpr int NT = TILE * TILE / bwd_pix_per_thread(TILE);
+};
+
 struct RenderParams {
     float lmin;       // log2(alpha_min)
     float amax, tmin;
@@ -104,7 +120,7 @@ __device__ __forceinline__ float exponent2(float dx, float dy, float A, float B,
     return __fmaf_rn(dx, t, q);
 }
 
-// exponent2 for a thread's two vertically adjacent pixels (offsets dx and
+// exponent2 for two vertically adjacent pixels of a thread (offsets dx and
 // dy.x, dy.y) in packed f32x2 arithmetic: each element is rounded exactly as
 // the scalar operations of exponent2 round it, so both give the same bits.
 __device__ __forceinline__ float2 exponent2x2(float dx, float2 dy, float A, float B, float C) {
@@ -294,15 +310,18 @@ __device__ __forceinline__ void fwd_item(int t, int rbase, Staged *st_all, unsig
             float e[PPT];
             bool ct[PPT];
             bool anyc = false;
-            if constexpr (PPT == 2) {
-                const float2 e2 = exponent2x2(dx, __fadd2_rn(make_float2(py[0], py[1]), make_float2(-a.y, -a.y)),
-                                              a.z, a.w, b.x);
-                const float2 ev = __fadd2_rn(e2, make_float2(b.y, b.y));
-                e[0] = ev.x;
-                e[1] = ev.y;
-                ct[0] = !done[0] && !(e2.x > 0.f) && !(ev.x < rp.lmin);
-                ct[1] = !done[1] && !(e2.y > 0.f) && !(ev.y < rp.lmin);
-                anyc = ct[0] || ct[1];
+            if constexpr (PPT % 2 == 0) {
+#pragma unroll
+                for (int k = 0; k < PPT; k += 2) {
+                    const float2 e2 = exponent2x2(
+                        dx, __fadd2_rn(make_float2(py[k], py[k + 1]), make_float2(-a.y, -a.y)), a.z, a.w, b.x);
+                    const float2 ev = __fadd2_rn(e2, make_float2(b.y, b.y));
+                    e[k] = ev.x;
+                    e[k + 1] = ev.y;
+                    ct[k] = !done[k] && !(e2.x > 0.f) && !(ev.x < rp.lmin);
+                    ct[k + 1] = !done[k + 1] && !(e2.y > 0.f) && !(ev.y < rp.lmin);
+                    anyc = anyc || ct[k] || ct[k + 1];
+                }
             } else {
 #pragma unroll
             for (int k = 0; k < PPT; k++) {
@@ -316,32 +335,35 @@ __device__ __forceinline__ void fwd_item(int t, int rbase, Staged *st_all, unsig
             const uint4 z = st[j].z;
             const float cb = __uint_as_float(z.x);
             const int pos1 = (int)z.y + 1;
-            if constexpr (PPT == 2) {
-                // the two pixels side by side in packed f32x2 arithmetic
-                // (each element rounded as the scalar loop below rounds it)
-                const float2 al = make_float2(fminf(rp.amax, ex2_approx(e[0])), fminf(rp.amax, ex2_approx(e[1])));
-                const float2 T2 = make_float2(T[0], T[1]);
-                const float2 nT = __fmul2_rn(T2, __ffma2_rn(al, make_float2(-1.f, -1.f), make_float2(1.f, 1.f)));
-                const float2 wa = __fmul2_rn(al, T2);
-                const bool s0 = ct[0] && nT.x < rp.tmin, s1 = ct[1] && nT.y < rp.tmin;
-                const bool b0 = ct[0] && !s0, b1 = ct[1] && !s1;
-                done[0] = done[0] || s0;
-                done[1] = done[1] || s1;
-                evals += (unsigned)b0 + (unsigned)b1;
-                const float2 w = make_float2(b0 ? wa.x : 0.f, b1 ? wa.y : 0.f);
-                const float2 r = __ffma2_rn(make_float2(b.z, b.z), w, make_float2(c0[0], c0[1]));
-                const float2 g = __ffma2_rn(make_float2(b.w, b.w), w, make_float2(c1[0], c1[1]));
-                const float2 bl = __ffma2_rn(make_float2(cb, cb), w, make_float2(c2[0], c2[1]));
-                c0[0] = r.x;
-                c0[1] = r.y;
-                c1[0] = g.x;
-                c1[1] = g.y;
-                c2[0] = bl.x;
-                c2[1] = bl.y;
-                T[0] = b0 ? nT.x : T[0];
-                T[1] = b1 ? nT.y : T[1];
-                last[0] = b0 ? pos1 : last[0];
-                last[1] = b1 ? pos1 : last[1];
+            if constexpr (PPT % 2 == 0) {
+                // the pixels two by two in packed f32x2 arithmetic (each
+                // element rounded as the scalar loop below rounds it)
+#pragma unroll
+                for (int k = 0; k < PPT; k += 2) {
+                    const float2 al = make_float2(fminf(rp.amax, ex2_approx(e[k])), fminf(rp.amax, ex2_approx(e[k + 1])));
+                    const float2 T2 = make_float2(T[k], T[k + 1]);
+                    const float2 nT = __fmul2_rn(T2, __ffma2_rn(al, make_float2(-1.f, -1.f), make_float2(1.f, 1.f)));
+                    const float2 wa = __fmul2_rn(al, T2);
+                    const bool s0 = ct[k] && nT.x < rp.tmin, s1 = ct[k + 1] && nT.y < rp.tmin;
+                    const bool b0 = ct[k] && !s0, b1 = ct[k + 1] && !s1;
+                    done[k] = done[k] || s0;
+                    done[k + 1] = done[k + 1] || s1;
+                    evals += (unsigned)b0 + (unsigned)b1;
+                    const float2 w = make_float2(b0 ? wa.x : 0.f, b1 ? wa.y : 0.f);
+                    const float2 r = __ffma2_rn(make_float2(b.z, b.z), w, make_float2(c0[k], c0[k + 1]));
+                    const float2 g = __ffma2_rn(make_float2(b.w, b.w), w, make_float2(c1[k], c1[k + 1]));
+                    const float2 bl = __ffma2_rn(make_float2(cb, cb), w, make_float2(c2[k], c2[k + 1]));
+                    c0[k] = r.x;
+                    c0[k + 1] = r.y;
+                    c1[k] = g.x;
+                    c1[k + 1] = g.y;
+                    c2[k] = bl.x;
+                    c2[k + 1] = bl.y;
+                    T[k] = b0 ? nT.x : T[k];
+                    T[k + 1] = b1 ? nT.y : T[k + 1];
+                    last[k] = b0 ? pos1 : last[k];
+                    last[k + 1] = b1 ? pos1 : last[k + 1];
+                }
             } else {
 #pragma unroll
             for (int k = 0; k < PPT; k++) {
@@ -448,7 +470,7 @@ __device__ __forceinline__ void bwd_item(int t, int rbase, Staged *st_all, unsig
                                          const float *__restrict__ dL_drgb, float4 *__restrict__ grad2d) {
     using C = Cfg<TILE, PPT, NT>;
     constexpr int CH = BATCH / 2, PER = CH / 32;
-    static_assert(C::ROWS * (PPT == pix_per_thread(TILE) ? 1 : 2) == TILE, "a work item is a tile or half of one");
+    static_assert(C::ROWS * (PPT == bwd_pix_per_thread(TILE) ? 1 : 2) == TILE, "a work item is a tile or half of one");
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     Staged *st = st_all + warp * CH;
     const int f = frame_of_tile(frames, F, t);
@@ -527,17 +549,20 @@ __device__ __forceinline__ void bwd_item(int t, int rbase, Staged *st_all, unsig
             float e[PPT], dy[PPT];
             bool ct[PPT];
             bool anyc = false;
-            if constexpr (PPT == 2) {
-                const float2 d2 = __fadd2_rn(make_float2(py[0], py[1]), make_float2(-a.y, -a.y));
-                dy[0] = d2.x;
-                dy[1] = d2.y;
-                const float2 e2 = exponent2x2(dx, d2, a.z, a.w, b.x);
-                const float2 ev = __fadd2_rn(e2, make_float2(b.y, b.y));
-                e[0] = ev.x;
-                e[1] = ev.y;
-                ct[0] = pos < last[0] && !(e2.x > 0.f) && !(ev.x < rp.lmin);
-                ct[1] = pos < last[1] && !(e2.y > 0.f) && !(ev.y < rp.lmin);
-                anyc = ct[0] || ct[1];
+            if constexpr (PPT % 2 == 0) {
+#pragma unroll
+                for (int k = 0; k < PPT; k += 2) {
+                    const float2 d2 = __fadd2_rn(make_float2(py[k], py[k + 1]), make_float2(-a.y, -a.y));
+                    dy[k] = d2.x;
+                    dy[k + 1] = d2.y;
+                    const float2 e2 = exponent2x2(dx, d2, a.z, a.w, b.x);
+                    const float2 ev = __fadd2_rn(e2, make_float2(b.y, b.y));
+                    e[k] = ev.x;
+                    e[k + 1] = ev.y;
+                    ct[k] = pos < last[k] && !(e2.x > 0.f) && !(ev.x < rp.lmin);
+                    ct[k + 1] = pos < last[k + 1] && !(e2.y > 0.f) && !(ev.y < rp.lmin);
+                    anyc = anyc || ct[k] || ct[k + 1];
+                }
             } else {
 #pragma unroll
             for (int k = 0; k < PPT; k++) {
@@ -552,43 +577,68 @@ __device__ __forceinline__ void bwd_item(int t, int rbase, Staged *st_all, unsig
             const float cb = __uint_as_float(z.x);
             // per-thread sums: sum de dx, sum de dy, dA, dB, dC, dF, dr, dg, db
             float sx = 0.f, sy = 0.f, dA = 0.f, dB = 0.f, dC = 0.f, dF = 0.f, dr = 0.f, dg = 0.f, db = 0.f;
-            if constexpr (PPT == 2) {
-                // the thread's two pixels side by side in packed f32x2
-                // arithmetic (the same terms as the scalar loop below)
-                const float G0 = ex2_approx(ct[0] ? e[0] : -INFINITY), G1 = ex2_approx(ct[1] ? e[1] : -INFINITY);
-                const float2 al = make_float2(fminf(rp.amax, G0), fminf(rp.amax, G1));
-                const float2 om = __ffma2_rn(al, make_float2(-1.f, -1.f), make_float2(1.f, 1.f));  // 1 - alpha
-                const float2 inv = make_float2(ct[0] ? rcp_approx(om.x) : 1.f, ct[1] ? rcp_approx(om.y) : 1.f);
-                const float2 T2 = __fmul2_rn(make_float2(T[0], T[1]), inv);  // T before this Gaussian
-                T[0] = T2.x;
-                T[1] = T2.y;
-                const float2 w = __fmul2_rn(al, T2);
-                const float2 gr = make_float2(g0[0], g0[1]), gg = make_float2(g1[0], g1[1]),
-                             gb = make_float2(g2[0], g2[1]);
-                const float2 wr = __fmul2_rn(w, gr), wg = __fmul2_rn(w, gg), wb = __fmul2_rn(w, gb);
-                const float2 cd = __ffma2_rn(make_float2(b.z, b.z), gr,
-                                             __ffma2_rn(make_float2(b.w, b.w), gg, __fmul2_rn(make_float2(cb, cb), gb)));
-                const float2 S2 = make_float2(S[0], S[1]);
-                const float2 dal = __ffma2_rn(T2, cd, __fmul2_rn(make_float2(-S2.x, -S2.y), inv));
-                const float2 Sn = __ffma2_rn(w, cd, S2);
-                S[0] = Sn.x;
-                S[1] = Sn.y;
-                float2 de = __fmul2_rn(dal, al);  // dL/de / ln 2
-                de.x = G0 > rp.amax ? 0.f : de.x;
-                de.y = G1 > rp.amax ? 0.f : de.y;
-                const float2 dx2 = make_float2(dx, dx), dy2 = make_float2(dy[0], dy[1]);
-                const float2 tx2 = __fmul2_rn(de, dx2), ty2 = __fmul2_rn(de, dy2);
-                const float2 a2 = __fmul2_rn(tx2, dx2), b2 = __fmul2_rn(tx2, dy2), c2 = __fmul2_rn(ty2, dy2);
-                sx = tx2.x + tx2.y;
-                sy = ty2.x + ty2.y;
-                dA = a2.x + a2.y;
-                dB = b2.x + b2.y;
-                dC = c2.x + c2.y;
-                dF = de.x + de.y;
-                dr = wr.x + wr.y;
-                dg = wg.x + wg.y;
-                db = wb.x + wb.y;
-                evals += (unsigned)ct[0] + (unsigned)ct[1];
+            if constexpr (PPT % 2 == 0) {
+                // the thread's pixels two by two in packed f32x2 arithmetic
+                // (the same terms as the scalar loop below)
+                float2 sxv, syv, dAv, dBv, dCv, dFv, drv, dgv, dbv;
+#pragma unroll
+                for (int k = 0; k < PPT; k += 2) {
+                    const float G0 = ex2_approx(ct[k] ? e[k] : -INFINITY);
+                    const float G1 = ex2_approx(ct[k + 1] ? e[k + 1] : -INFINITY);
+                    const float2 al = make_float2(fminf(rp.amax, G0), fminf(rp.amax, G1));
+                    const float2 om = __ffma2_rn(al, make_float2(-1.f, -1.f), make_float2(1.f, 1.f));  // 1 - alpha
+                    const float2 inv = make_float2(ct[k] ? rcp_approx(om.x) : 1.f, ct[k + 1] ? rcp_approx(om.y) : 1.f);
+                    const float2 T2 = __fmul2_rn(make_float2(T[k], T[k + 1]), inv);  // T before this Gaussian
+                    T[k] = T2.x;
+                    T[k + 1] = T2.y;
+                    const float2 w = __fmul2_rn(al, T2);
+                    const float2 gr = make_float2(g0[k], g0[k + 1]), gg = make_float2(g1[k], g1[k + 1]),
+                                 gb = make_float2(g2[k], g2[k + 1]);
+                    const float2 cd = __ffma2_rn(make_float2(b.z, b.z), gr,
+                                                 __ffma2_rn(make_float2(b.w, b.w), gg,
+                                                            __fmul2_rn(make_float2(cb, cb), gb)));
+                    const float2 S2 = make_float2(S[k], S[k + 1]);
+                    const float2 dal = __ffma2_rn(T2, cd, __fmul2_rn(make_float2(-S2.x, -S2.y), inv));
+                    const float2 Sn = __ffma2_rn(w, cd, S2);
+                    S[k] = Sn.x;
+                    S[k + 1] = Sn.y;
+                    float2 de = __fmul2_rn(dal, al);  // dL/de / ln 2
+                    de.x = G0 > rp.amax ? 0.f : de.x;
+                    de.y = G1 > rp.amax ? 0.f : de.y;
+                    const float2 dx2 = make_float2(dx, dx), dy2 = make_float2(dy[k], dy[k + 1]);
+                    const float2 tx2 = __fmul2_rn(de, dx2), ty2 = __fmul2_rn(de, dy2);
+                    if (k == 0) {
+                        sxv = tx2;
+                        syv = ty2;
+                        dAv = __fmul2_rn(tx2, dx2);
+                        dBv = __fmul2_rn(tx2, dy2);
+                        dCv = __fmul2_rn(ty2, dy2);
+                        dFv = de;
+                        drv = __fmul2_rn(w, gr);
+                        dgv = __fmul2_rn(w, gg);
+                        dbv = __fmul2_rn(w, gb);
+                    } else {
+                        sxv = __fadd2_rn(sxv, tx2);
+                        syv = __fadd2_rn(syv, ty2);
+                        dAv = __ffma2_rn(tx2, dx2, dAv);
+                        dBv = __ffma2_rn(tx2, dy2, dBv);
+                        dCv = __ffma2_rn(ty2, dy2, dCv);
+                        dFv = __fadd2_rn(dFv, de);
+                        drv = __ffma2_rn(w, gr, drv);
+                        dgv = __ffma2_rn(w, gg, dgv);
+                        dbv = __ffma2_rn(w, gb, dbv);
+                    }
+                    evals += (unsigned)ct[k] + (unsigned)ct[k + 1];
+                }
+                sx = sxv.x + sxv.y;
+                sy = syv.x + syv.y;
+                dA = dAv.x + dAv.y;
+                dB = dBv.x + dBv.y;
+                dC = dCv.x + dCv.y;
+                dF = dFv.x + dFv.y;
+                dr = drv.x + drv.y;
+                dg = dgv.x + dgv.y;
+                db = dbv.x + dbv.y;
             } else {
 #pragma unroll
             for (int k = 0; k < PPT; k++) {
@@ -641,13 +691,13 @@ __device__ __forceinline__ void bwd_item(int t, int rbase, Staged *st_all, unsig
 }
 
 template <int TILE, int BATCH>
-__global__ void __launch_bounds__(Threads<TILE>::NT)
+__global__ void __launch_bounds__(BwdThreads<TILE>::NT)
 k_render_bwd(const gs_frame *__restrict__ frames, int F, const uint32_t *__restrict__ order, int heavy,
              const uint2 *__restrict__ ranges, const uint32_t *__restrict__ vals,
              const float4 *__restrict__ splat, const float *__restrict__ colors, RenderParams rp,
              Stats *__restrict__ stats, const float *__restrict__ in_T, const int32_t *__restrict__ in_last,
              const float *__restrict__ dL_drgb, float4 *__restrict__ grad2d) {
-    constexpr int NT = Threads<TILE>::NT, PL = pix_per_thread(TILE);
+    constexpr int NT = BwdThreads<TILE>::NT, PL = bwd_pix_per_thread(TILE);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ unsigned long long s_eval;
     Staged *st = reinterpret_cast<Staged *>(smem_raw);
@@ -683,16 +733,16 @@ cudaError_t smem_opt_in(K kern, size_t bytes) {
     return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
-template <int TILE, int BATCH>
+template <int NT, int BATCH>
 constexpr size_t stage_bytes() {
-    return (size_t)(Threads<TILE>::NT / 32) * (BATCH / 2) * sizeof(Staged);
+    return (size_t)(NT / 32) * (BATCH / 2) * sizeof(Staged);
 }
 
 template <int TILE, int BATCH>
 cudaError_t run_fwd(const gs_batch *b, const uint32_t *order, const uint2 *ranges, const uint32_t *vals,
                     const float4 *splat, const float *colors, RenderParams rp, Stats *stats, float *out_rgb,
                     float *out_T, int32_t *out_last, cudaStream_t s) {
-    constexpr size_t smem = stage_bytes<TILE, BATCH>();
+    constexpr size_t smem = stage_bytes<Threads<TILE>::NT, BATCH>();
     const int heavy = heavy_tiles(b->num_tiles);
     cudaError_t e = smem_opt_in(k_render_fwd<TILE, BATCH>, smem);
     if (e != cudaSuccess) return e;
@@ -705,11 +755,11 @@ template <int TILE, int BATCH>
 cudaError_t run_bwd(const gs_batch *b, const uint32_t *order, const uint2 *ranges, const uint32_t *vals,
                     const float4 *splat, const float *colors, RenderParams rp, Stats *stats, const float *in_T,
                     const int32_t *in_last, const float *dL, float4 *grad2d, cudaStream_t s) {
-    constexpr size_t smem = stage_bytes<TILE, BATCH>();
+    constexpr size_t smem = stage_bytes<BwdThreads<TILE>::NT, BATCH>();
     const int heavy = heavy_tiles(b->num_tiles);
     cudaError_t e = smem_opt_in(k_render_bwd<TILE, BATCH>, smem);
     if (e != cudaSuccess) return e;
-    k_render_bwd<TILE, BATCH><<<(unsigned)(b->num_tiles + heavy), Threads<TILE>::NT, smem, s>>>(
+    k_render_bwd<TILE, BATCH><<<(unsigned)(b->num_tiles + heavy), BwdThreads<TILE>::NT, smem, s>>>(
         b->frames_dev, b->num_frames, order, heavy, ranges, vals, splat, colors, rp, stats, in_T, in_last, dL,
         grad2d);
     return cudaGetLastError();
