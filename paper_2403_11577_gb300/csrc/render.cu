@@ -61,7 +61,12 @@ namespace {
 
 // Pixels per thread: 2 at tiles 8 and 16, 4 at 32; half of that in the
 // halves of heavy tiles.
-__host__ __device__ constexpr int pix_per_thread(int tile) { return tile == 32 ? 4 : 2; }
+// The forward's pixels per thread: two at tiles 8 and 16 (8x8 bands), four at
+// tile 32.  GS_FWD_PPT16 overrides tile 16's value (2 or 4) at build time.
+#ifndef GS_FWD_PPT16
+#define GS_FWD_PPT16 2
+#endif
+__host__ __device__ constexpr int pix_per_thread(int tile) { return tile == 32 ? 4 : (tile == 16 ? GS_FWD_PPT16 : 2); }
 
 // The backward's pixels per thread: four at tiles 16 and 32 (16x8 bands, 8x8
 // in the halves of heavy tiles), which spreads each kept Gaussian's 9-value
