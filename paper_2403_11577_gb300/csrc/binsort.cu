@@ -6,9 +6,10 @@
 // gs_bin_sort gets there in two cheap stages instead of one wide sort, with
 // 32-bit keys throughout:
 // 1. 4 LSD passes over the per-(frame, Gaussian) records keyed by the float
-//    bits of their depth (culled records last; the first pass reads the
-//    depths and rectangles directly): a stable depth order of the records
-//    (ties keep record order).
+//    bits of their depth: a stable depth order of the records (ties keep
+//    record order).  The first pass reads the depths and rectangles
+//    directly and drops the culled records (empty rectangle); it counts the
+//    rest, and the later passes and stage 2 visit only those.
 // 2. k_pair_count / k_pair_scan / k_pair_emit over the records in that
 //    order: every record emits one pair per tile of its rectangle (emission
 //    is cooperative: threads stride over the block's output range and find
@@ -27,10 +28,11 @@
 // same 64-bit passes to bin LiDAR points into voxels.
 // Each radix pass: k_radix_hist (per-block digit counts) -> k_radix_colscan
 // (per-digit prefix over blocks, digit totals) -> k_radix_scatter (stable:
-// per-warp ranking with match_any in index order, per-tile prefix over
-// warps, staging in shared memory by digit, coalesced writes; the next
-// tile's keys and values are loaded into registers while the current tile is
-// staged and written); each block owns one contiguous chunk of the input.
+// per-warp ranking in index order, the lanes of equal digit found by one
+// ballot per digit bit; per-tile prefix over warps; staging in shared memory
+// by digit; coalesced writes; the next tile's keys and values are loaded
+// into registers while the current tile is staged and written); each block
+// owns one contiguous chunk of the input.
 // No kernel waits on another block; there are no spin loops.
 #include <algorithm>
 #include <atomic>
@@ -54,10 +56,17 @@ __device__ __forceinline__ unsigned long long block_sum_u64(unsigned long long v
 }
 
 // perm (optional): the order in which records are visited; NULL = record order.
+// live (optional): the entries of perm to visit (the records that survived
+// culling in the record sort), else R.
+__device__ __forceinline__ long long visited(long long R, const unsigned long long *live) {
+    return live ? min(R, (long long)*live) : R;
+}
+
 __global__ void __launch_bounds__(kEmitThreads)
-k_pair_count(const uint2 *__restrict__ rect, long long R, const uint32_t *__restrict__ perm,
-             unsigned long long *__restrict__ sums) {
+k_pair_count(const uint2 *__restrict__ rect, long long R, const unsigned long long *__restrict__ live,
+             const uint32_t *__restrict__ perm, unsigned long long *__restrict__ sums) {
     __shared__ unsigned long long sh[kEmitThreads / 32];
+    R = visited(R, live);
     const long long base = (long long)blockIdx.x * kEmitItems;
     unsigned long long c = 0;
     for (int i = threadIdx.x; i < kEmitItems; i += kEmitThreads) {
@@ -114,10 +123,16 @@ k_pair_scan(unsigned long long *__restrict__ sums, int nb, long long capacity, S
 // emission.
 __global__ void __launch_bounds__(kEmitThreads)
 k_pair_count_exact(const gs_frame *__restrict__ frames, int F, int T, float lmin, const uint2 *__restrict__ rect,
-                   const float4 *__restrict__ splat, long long R, const uint32_t *__restrict__ perm,
-                   unsigned long long *__restrict__ sums, uint2 *__restrict__ rec_pairs) {
+                   const float4 *__restrict__ splat, long long R, const unsigned long long *__restrict__ live,
+                   const uint32_t *__restrict__ perm, unsigned long long *__restrict__ sums,
+                   uint2 *__restrict__ rec_pairs) {
     __shared__ unsigned long long sh[kEmitThreads / 32];
+    R = visited(R, live);
     const long long base = (long long)blockIdx.x * kEmitItems;
+    if (base >= R) {  // past the live records: no pairs
+        if (threadIdx.x == 0) sums[blockIdx.x] = 0ull;
+        return;
+    }
     constexpr int PER = kEmitItems / kEmitThreads;
     // the gathers of the thread's records are issued together (records i =
     // threadIdx.x + j * kEmitThreads, coalesced across the block)
@@ -170,7 +185,7 @@ k_pair_count_exact(const gs_frame *__restrict__ frames, int F, int T, float lmin
 // are its rows' runs of tiles, each a segment (first pair, length, first
 // tile, value); the block's segments are staged in shared memory in windows
 // of kSegWindow, and the warps expand them into pairs 32 at a time.
-constexpr int kSegWindow = 4096;
+constexpr int kSegWindow = 1024;  // 16 KB of segments: eight blocks fit on an SM
 
 struct Segment {
     uint32_t off, len, tile0, val;  // off: first pair, relative to the block's first
@@ -185,13 +200,16 @@ struct EmitExactSmem {
 
 __global__ void __launch_bounds__(kEmitThreads)
 k_pair_emit_exact(const gs_frame *__restrict__ frames, int F, int T, float lmin, const uint2 *__restrict__ rect,
-                  const float4 *__restrict__ splat, long long R, const uint32_t *__restrict__ perm,
-                  const unsigned long long *__restrict__ sums, const uint2 *__restrict__ rec_pairs,
-                  const Stats *__restrict__ stats, uint32_t *__restrict__ keys, uint32_t *__restrict__ vals) {
+                  const float4 *__restrict__ splat, long long R, const unsigned long long *__restrict__ live,
+                  const uint32_t *__restrict__ perm, const unsigned long long *__restrict__ sums,
+                  const uint2 *__restrict__ rec_pairs, const Stats *__restrict__ stats, uint32_t *__restrict__ keys,
+                  uint32_t *__restrict__ vals) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     EmitExactSmem &S = *reinterpret_cast<EmitExactSmem *>(smem_raw);
     if (stats->num_pairs == 0) return;  // nothing to emit, or overflow
+    R = visited(R, live);
     const long long base = (long long)blockIdx.x * kEmitItems;
+    if (base >= R) return;
     constexpr int PER = kEmitItems / kEmitThreads;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     // this thread's records: pairs and non-empty rows (from the count)
@@ -324,7 +342,8 @@ __device__ __forceinline__ uint32_t key_tile(unsigned long long k) { return (uin
 template <typename K>
 __global__ void __launch_bounds__(kEmitThreads)
 k_pair_emit(const gs_frame *__restrict__ frames, int F, const uint2 *__restrict__ rect,
-            const float *__restrict__ depth, long long R, const uint32_t *__restrict__ perm,
+            const float *__restrict__ depth, long long R, const unsigned long long *__restrict__ live,
+            const uint32_t *__restrict__ perm,
             const unsigned long long *__restrict__ sums, const Stats *__restrict__ stats, K *__restrict__ keys,
             uint32_t *__restrict__ vals) {
     __shared__ unsigned long long off[kEmitItems + 1];
@@ -335,7 +354,9 @@ k_pair_emit(const gs_frame *__restrict__ frames, int F, const uint2 *__restrict_
     __shared__ uint32_t s_val[kEmitItems];
     __shared__ unsigned long long wsum[kEmitThreads / 32];
     if (stats->num_pairs == 0) return;  // nothing to emit, or overflow
+    R = visited(R, live);
     const long long base = (long long)blockIdx.x * kEmitItems;
+    if (base >= R) return;
     constexpr int PER = kEmitItems / kEmitThreads;
     // counts of this thread's PER consecutive records
     unsigned long long c[PER];
@@ -410,8 +431,11 @@ __device__ __forceinline__ Chunk sort_chunk(unsigned long long P, int nb, int b)
 
 // The input of a pass: key/value buffers, or (the first pass over the
 // records) the records themselves, keyed by the float bits of their depth
-// (positive, so ordered like the depths), culled records last, valued by
-// their index.
+// (positive, so ordered like the depths) and valued by their index; culled
+// records (empty rectangle) are dropped there, so the later passes and the
+// pair emission see only the records that can make pairs.
+constexpr uint32_t kDropped = 0xffffffffu;  // value of a dropped record (indices are < 2^31)
+
 template <typename K>
 struct PassInput {
     const K *keys;
@@ -423,11 +447,26 @@ struct PassInput {
     __device__ __forceinline__ unsigned long long n() const {
         return count ? *count : (unsigned long long)count_host;
     }
-    __device__ __forceinline__ K key(long long i) const {
-        if (rect) return (K)(rect_count(rect[i]) ? __float_as_uint(depth[i]) : 0xffffffffu);
-        return keys[i];
+    // key of item i; false if it is dropped
+    __device__ __forceinline__ bool key(long long i, K &k) const {
+        if (rect) {
+            const uint2 rc = rect[i];
+            k = (K)__float_as_uint(depth[i]);
+            return rect_count(rc) != 0u;
+        }
+        k = keys[i];
+        return true;
     }
-    __device__ __forceinline__ uint32_t val(long long i) const { return rect ? (uint32_t)i : vals[i]; }
+    // key and value of item i; a dropped item gets the value kDropped
+    __device__ __forceinline__ void load(long long i, K &k, uint32_t &v) const {
+        if (rect) {
+            v = key(i, k) ? (uint32_t)i : kDropped;
+        } else {
+            k = keys[i];
+            v = vals[i];
+        }
+    }
+    __device__ __forceinline__ bool live(uint32_t v) const { return !rect || v != kDropped; }
 };
 
 template <typename K>
@@ -438,8 +477,10 @@ k_radix_hist(const PassInput<K> in, int shift, int nb, uint32_t *__restrict__ hi
     for (int i = threadIdx.x; i < (kSortThreads / 32) * kRadix; i += kSortThreads) (&h[0][0])[i] = 0;
     __syncthreads();
     const Chunk c = sort_chunk(in.n(), nb, blockIdx.x);
-    for (long long i = c.lo + threadIdx.x; i < c.hi; i += kSortThreads)
-        atomicAdd(&h[warp][(uint32_t)(in.key(i) >> shift) & (kRadix - 1)], 1u);
+    for (long long i = c.lo + threadIdx.x; i < c.hi; i += kSortThreads) {
+        K k;
+        if (in.key(i, k)) atomicAdd(&h[warp][(uint32_t)(k >> shift) & (kRadix - 1)], 1u);
+    }
     __syncthreads();
     for (int d = threadIdx.x; d < kRadix; d += kSortThreads) {
         uint32_t s = 0;
@@ -489,10 +530,12 @@ struct ScatterSmem {
 // ranges (optional, the last pass over tile keys): every tile's [start, end)
 // in the output, found from the staged, sorted items (min/max atomics over
 // the run boundaries; the ranges start at {UINT32_MAX, 0}).
+// count_out (optional): the items written (the sum of the digit totals).
 template <typename K>
 __global__ void __launch_bounds__(kSortThreads, 2)
 k_radix_scatter(const PassInput<K> in, K *__restrict__ kout, uint32_t *__restrict__ vout, int shift, int nb,
-                const uint32_t *__restrict__ hist, const uint32_t *__restrict__ totals, uint2 *__restrict__ ranges) {
+                const uint32_t *__restrict__ hist, const uint32_t *__restrict__ totals, uint2 *__restrict__ ranges,
+                unsigned long long *__restrict__ count_out) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     ScatterSmem<K> &S = *reinterpret_cast<ScatterSmem<K> *>(smem_raw);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -513,6 +556,8 @@ k_radix_scatter(const PassInput<K> in, K *__restrict__ kout, uint32_t *__restric
         uint32_t pre = 0;
         for (int w = 0; w < warp; w++) pre += S.wtot[w];
         S.run[threadIdx.x] += pre + hist[(size_t)threadIdx.x * nb + blockIdx.x];
+        if (count_out && blockIdx.x == 0 && threadIdx.x == kRadix - 1)
+            *count_out = (unsigned long long)S.run[threadIdx.x] + totals[threadIdx.x];
     }
     __syncthreads();
     const uint32_t lt_mask = (1u << lane) - 1u;
@@ -524,9 +569,9 @@ k_radix_scatter(const PassInput<K> in, K *__restrict__ kout, uint32_t *__restric
 #pragma unroll
     for (int r = 0; r < kSortItems; r++) {
         const long long idx = c.lo + (long long)warp * 32 * kSortItems + r * 32 + lane;
-        const bool valid = idx < c.hi;
-        kn[r] = valid ? in.key(idx) : K(0);
-        vn[r] = valid ? in.val(idx) : 0u;
+        kn[r] = K(0);
+        vn[r] = kDropped;
+        if (idx < c.hi) in.load(idx, kn[r], vn[r]);
     }
     for (long long t0 = c.lo; t0 < c.hi; t0 += kSortTile) {
         for (int i = lane; i < kRadix; i += 32) S.wcnt[warp][i] = 0;
@@ -541,11 +586,18 @@ k_radix_scatter(const PassInput<K> in, K *__restrict__ kout, uint32_t *__restric
 #pragma unroll
         for (int r = 0; r < kSortItems; r++) {
             const long long idx = t0 + (long long)warp * 32 * kSortItems + r * 32 + lane;
-            const bool valid = idx < c.hi;
+            const bool valid = idx < c.hi && in.live(v[r]);
             const uint32_t d = (uint32_t)(k[r] >> shift) & (kRadix - 1);
             dg[r] = valid ? d : kRadix;  // kRadix marks an empty slot
-            const uint32_t key = valid ? d : (uint32_t)(kRadix + lane);
-            const uint32_t peers = __match_any_sync(0xffffffffu, key);
+            // lanes with the same digit: one ballot per digit bit (cheaper
+            // than a match over up to 32 distinct digits)
+            uint32_t peers = __ballot_sync(0xffffffffu, valid);
+#pragma unroll
+            for (int bit = 0; bit < kRadixBits; bit++) {
+                const bool set = (d >> bit) & 1u;
+                const uint32_t m = __ballot_sync(0xffffffffu, set);
+                peers &= set ? m : ~m;
+            }
             const uint32_t before = (uint32_t)__popc(peers & lt_mask);
             uint32_t base = valid ? S.wcnt[warp][d] : 0u;
             __syncwarp();
@@ -557,9 +609,9 @@ k_radix_scatter(const PassInput<K> in, K *__restrict__ kout, uint32_t *__restric
 #pragma unroll
             for (int r = 0; r < kSortItems; r++) {
                 const long long idx = t0 + kSortTile + (long long)warp * 32 * kSortItems + r * 32 + lane;
-                const bool valid = idx < c.hi;
-                kn[r] = valid ? in.key(idx) : K(0);
-                vn[r] = valid ? in.val(idx) : 0u;
+                kn[r] = K(0);
+                vn[r] = kDropped;
+                if (idx < c.hi) in.load(idx, kn[r], vn[r]);
             }
         }
         __syncthreads();
@@ -602,7 +654,7 @@ k_radix_scatter(const PassInput<K> in, K *__restrict__ kout, uint32_t *__restric
             }
         }
         __syncthreads();
-        const int n = (int)min((long long)kSortTile, c.hi - t0);
+        const int n = (int)(S.tstart[kRadix - 1] + S.tcnt[kRadix - 1]);  // staged items
         for (int i = threadIdx.x; i < n; i += kSortThreads) {
             const K key = S.skey[i];
             const uint32_t d = (uint32_t)(key >> shift) & (kRadix - 1);
@@ -611,12 +663,13 @@ k_radix_scatter(const PassInput<K> in, K *__restrict__ kout, uint32_t *__restric
             vout[pos] = S.sval[i];
             if (ranges) {
                 // within a digit's run the staged keys are in output order, so a
-                // tile's items here are contiguous; its neighbours across run
-                // edges were staged by other tiles or blocks (min/max settle it)
+                // tile's items here are contiguous (the items next to a digit
+                // run's edges have another digit, hence another key); its
+                // neighbours across run edges were staged by other tiles or
+                // blocks (min/max settle it)
                 const uint32_t t = (uint32_t)key;
-                const int r0 = (int)S.tstart[d], r1 = r0 + (int)S.tcnt[d];
-                if (i == r0 || S.skey[i - 1] != key) atomicMin(&ranges[t].x, pos);
-                if (i + 1 == r1 || S.skey[i + 1] != key) atomicMax(&ranges[t].y, pos + 1u);
+                if (i == 0 || S.skey[i - 1] != key) atomicMin(&ranges[t].x, pos);
+                if (i + 1 == n || S.skey[i + 1] != key) atomicMax(&ranges[t].y, pos + 1u);
             }
         }
         __syncthreads();
@@ -704,12 +757,12 @@ namespace {
 // with `ranges`, the last pass over tile keys also finds the tile ranges.
 template <typename K>
 cudaError_t radix_pass(const PassInput<K> &in, K *kout, uint32_t *vout, int shift, int nb, uint32_t *hist,
-                       cudaStream_t s, uint2 *ranges = nullptr) {
+                       cudaStream_t s, uint2 *ranges = nullptr, unsigned long long *count_out = nullptr) {
     uint32_t *totals = hist + (size_t)kRadix * nb;
     k_radix_hist<K><<<nb, kSortThreads, 0, s>>>(in, shift, nb, hist);
     k_radix_colscan<<<kRadix, kColThreads, 0, s>>>(hist, nb, totals);
     k_radix_scatter<K><<<nb, kSortThreads, sizeof(ScatterSmem<K>), s>>>(in, kout, vout, shift, nb, hist, totals,
-                                                                        ranges);
+                                                                        ranges, count_out);
     return cudaGetLastError();
 }
 
@@ -763,26 +816,27 @@ cudaError_t launch_bin_sort(const gs_batch *b, const gs_opts *o, const Layout &L
     if (L.emit_blocks > 0) {
         // stage 1: stable depth order of the records (4 passes, ends in buffer 0;
         // the first reads the records' depths and rectangles)
+        unsigned long long *live = &stats->num_records;  // records that survive culling
         e = radix_pass(PassInput<uint32_t>{nullptr, nullptr, rect, depth, nullptr, R}, rkeys[1], rvals[1], 0,
-                       L.rec_sort_blocks, hist, s);
+                       L.rec_sort_blocks, hist, s, nullptr, live);
         for (int p = 1; p < 4 && e == cudaSuccess; p++)
-            e = radix_pass(rkeys[p & 1], rvals[p & 1], rkeys[(p + 1) & 1], rvals[(p + 1) & 1],
-                           (const unsigned long long *)nullptr, 8 * p, L.rec_sort_blocks, hist, s, R);
+            e = radix_pass(rkeys[p & 1], rvals[p & 1], rkeys[(p + 1) & 1], rvals[(p + 1) & 1], live, 8 * p,
+                           L.rec_sort_blocks, hist, s);
         if (e != cudaSuccess) return e;
         // stage 2: pairs emitted in that order (exact tiles or whole rectangles)
         if (exact) {
             uint2 *rec_pairs = reinterpret_cast<uint2 *>(ws + L.rec_pairs);
             k_pair_count_exact<<<L.emit_blocks, kEmitThreads, 0, s>>>(b->frames_dev, b->num_frames, b->tile, lmin,
-                                                                      rect, splat, R, rvals[0], sums, rec_pairs);
+                                                                      rect, splat, R, live, rvals[0], sums, rec_pairs);
             k_pair_scan<<<1, 1024, 0, s>>>(sums, L.emit_blocks, b->pair_capacity, stats);
             k_pair_emit_exact<<<L.emit_blocks, kEmitThreads, sizeof(EmitExactSmem), s>>>(
-                b->frames_dev, b->num_frames, b->tile, lmin, rect, splat, R, rvals[0], sums, rec_pairs, stats,
+                b->frames_dev, b->num_frames, b->tile, lmin, rect, splat, R, live, rvals[0], sums, rec_pairs, stats,
                 keys[L.first_buffer], vals[L.first_buffer]);
         } else {
-            k_pair_count<<<L.emit_blocks, kEmitThreads, 0, s>>>(rect, R, rvals[0], sums);
+            k_pair_count<<<L.emit_blocks, kEmitThreads, 0, s>>>(rect, R, live, rvals[0], sums);
             k_pair_scan<<<1, 1024, 0, s>>>(sums, L.emit_blocks, b->pair_capacity, stats);
             k_pair_emit<uint32_t><<<L.emit_blocks, kEmitThreads, 0, s>>>(b->frames_dev, b->num_frames, rect, depth,
-                                                                         R, rvals[0], sums, stats,
+                                                                         R, live, rvals[0], sums, stats,
                                                                          keys[L.first_buffer], vals[L.first_buffer]);
         }
     } else {
@@ -1060,11 +1114,11 @@ extern "C" gs_status gs_bin_sort_noalloc(const gs_batch *b, const gs_opts *o, co
     if (e == cudaSuccess && emit_blocks > 0) {
         k_noalloc_check_rects<<<(unsigned)((b->num_records + 255) / 256), 256, 0, s>>>(
             b->frames_dev, b->num_frames, r2, b->num_records, &sc->stats);
-        k_pair_count<<<emit_blocks, kEmitThreads, 0, s>>>(r2, b->num_records, nullptr, sc->emit_sums);
+        k_pair_count<<<emit_blocks, kEmitThreads, 0, s>>>(r2, b->num_records, nullptr, nullptr, sc->emit_sums);
         k_pair_scan<<<1, 1024, 0, s>>>(sc->emit_sums, emit_blocks, b->pair_capacity, &sc->stats);
         k_noalloc_gate<<<1, 1, 0, s>>>(&sc->stats);
         k_pair_emit<unsigned long long><<<emit_blocks, kEmitThreads, 0, s>>>(
-            b->frames_dev, b->num_frames, r2, depth, b->num_records, nullptr, sc->emit_sums, &sc->stats, kb[cur],
+            b->frames_dev, b->num_frames, r2, depth, b->num_records, nullptr, nullptr, sc->emit_sums, &sc->stats, kb[cur],
             vb[cur]);
         e = cudaGetLastError();
     }

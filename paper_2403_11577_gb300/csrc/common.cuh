@@ -32,7 +32,7 @@ struct Stats {
     unsigned long long eval_fwd;
     unsigned long long eval_bwd;
     unsigned long long raw_pairs;   // pairs requested before the capacity check
-    unsigned long long num_records; // records of the batch (count of the record sort)
+    unsigned long long num_records; // records that survive culling (count of the record sort)
     unsigned long long pad[2];
 };
 
