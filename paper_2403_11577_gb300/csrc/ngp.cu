@@ -179,11 +179,6 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, unsigne
     }
 }
 
-// A wait for the MMAs (the settable bound).
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-    return mbar_wait(bar, parity, *(volatile unsigned long long *)&g_ngp_wait_ns);
-}
-
 // After a timeout: the wait for the MMAs still in flight before the tensor
 // memory is released (always the fixed one-second bound).
 __device__ __forceinline__ bool mbar_drain(uint32_t bar, uint32_t parity) { return mbar_wait(bar, parity, kWaitNs); }
@@ -409,10 +404,11 @@ __device__ __forceinline__ void epi_mask(uint32_t tacc, const Lane &ln, uint32_t
 
 struct Sync {
     uint32_t bar, phase;
+    unsigned long long limit_ns;  // the settable bound on a wait for the MMAs, read once per kernel
     // Every thread waits until the issuing thread's MMAs are done; false (for
     // all threads) when any thread's wait ran out.
     __device__ bool wait_all() {
-        const bool ok = mbar_wait(bar, phase);
+        const bool ok = mbar_wait(bar, phase, limit_ns);
         if (ok) phase ^= 1u;
         const bool bad = __syncthreads_or(!ok);
         fence_after_sync();
@@ -479,7 +475,7 @@ k_ngp_fwd(NgpArgs a, const float *__restrict__ theta, const float *__restrict__ 
     // encoding columns 2L .. 31 stay zero
     const int pad = kK1 - a.D;
     for (int e = threadIdx.x; e < kTile * pad; e += kThreads) put(F, e / pad, a.D + e % pad, 0.f);
-    Sync s{smem_addr(bar), 0u};
+    Sync s{smem_addr(bar), 0u, *(volatile unsigned long long *)&g_ngp_wait_ns};
     init_bar(s.bar);
     tmem_alloc(tslot, kFwdCols);
     publish();
@@ -571,7 +567,7 @@ __device__ __forceinline__ void consumer_publish() {
 // The consumers wait for the issuing thread's MMAs; a timeout in any of them
 // sets *abort (read by all consumers after their barrier).
 __device__ __forceinline__ bool consumer_wait(Sync &s, volatile int *abort) {
-    const bool ok = mbar_wait(s.bar, s.phase);
+    const bool ok = mbar_wait(s.bar, s.phase, s.limit_ns);
     if (ok) s.phase ^= 1u;
     else *abort = 1;
     consumer_sync();
@@ -711,7 +707,7 @@ k_ngp_bwd(NgpArgs a, const float *__restrict__ theta, const float *__restrict__ 
         const int b = e / (kTile * 48), r = (e / 48) % kTile, c = e % 48;
         if (c >= D) put(E[b], r, c, c == 32 ? 1.f : 0.f);
     }
-    Sync s{smem_addr(bar), 0u};
+    Sync s{smem_addr(bar), 0u, *(volatile unsigned long long *)&g_ngp_wait_ns};
     init_bar(s.bar);
     tmem_alloc(tslot, 512u);
     const int warp = (int)(threadIdx.x >> 5);
