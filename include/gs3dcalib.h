@@ -273,7 +273,10 @@ gs_status gs_bin_sort(const gs_batch *batch, const gs_opts *opts, void *ws_dev, 
  *   out_T[P]          final transmittance (float)
  *   out_last[P]       one past the position, within the tile's sorted
  *                     range, of the last composited Gaussian; 0 if none
- *                     (int32) -- the backward's starting point */
+ *                     (int32) -- the backward's starting point
+ * It also leaves in the workspace, per band of pixels and per 32 entries of
+ * the tile's list, a mask of the entries some pixel of the band composited,
+ * which gs_render_bwd walks. */
 gs_status gs_render_fwd(const gs_batch *batch, const float *colors, const gs_opts *opts,
                         void *ws_dev, float *out_rgb, float *out_T, int32_t *out_last,
                         void *stream);
@@ -310,7 +313,9 @@ gs_status gs_loss_photo(const gs_batch *batch, const float *rgb, const float *ta
  * projection and Eq. 2-3 to the Gaussian parameters and to a per-frame
  * camera twist (kept in the workspace for gs_pose_grad).
  *   dL_drgb[P][3]  gradient of the loss w.r.t. out_rgb
- *   out_T, out_last: as written by gs_render_fwd for the same inputs
+ *   out_T, out_last: as written by gs_render_fwd for the same inputs (the
+ *                  masks that call left in the workspace are read too: the
+ *                  pair list must still be the one it rendered)
  *   d_quat[N][4], d_log_scale[N][3], d_logit_opacity[N], d_colors[N][3]:
  *                  gradients of all N Gaussians; added to the arrays if
  *                  accumulate != 0, written over them if accumulate == 0.

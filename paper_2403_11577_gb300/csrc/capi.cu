@@ -22,10 +22,11 @@ cudaError_t launch_project_bwd(const gs_batch *, const float *, const float *, c
                                float *, float *, double *, bool, cudaStream_t);
 cudaError_t launch_bin_sort(const gs_batch *, const gs_opts *, const Layout &, unsigned char *, cudaStream_t, int);
 cudaError_t launch_render_fwd(const gs_batch *, const gs_opts *, const uint32_t *, const uint2 *, const uint32_t *,
-                              const float4 *, const float *, Stats *, float *, float *, int32_t *, cudaStream_t);
+                              const float4 *, const float *, Stats *, float *, float *, int32_t *, uint32_t *,
+                              long long, cudaStream_t);
 cudaError_t launch_render_bwd(const gs_batch *, const gs_opts *, const uint32_t *, const uint2 *, const uint32_t *,
                               const float4 *, const float *, Stats *, const float *, const int32_t *, const float *,
-                              float4 *, cudaStream_t);
+                              float4 *, const uint32_t *, long long, cudaStream_t);
 cudaError_t launch_l1(const float *, const float *, long long, float, double *, float *, double *, cudaStream_t);
 cudaError_t launch_photo(const gs_batch *, const float *, const float *, float, float, double *, float *, float *,
                          double *, cudaStream_t);
@@ -76,6 +77,10 @@ bool make_layout(const gs_batch *b, Layout *L) {
     L->order = take(T * 4);
     L->emit_sums = take((size_t)std::max(1, L->emit_blocks) * 8);
     L->rec_pairs = take(R * 8);  // exact tiles: pairs and non-empty rows per sorted record
+    // render: per forward band slot, one bit per tile-list entry (each tile's
+    // bits start on a word: word (range start / 32) + tile)
+    L->band_words = (long long)(cap / 32 + T + 2);
+    L->band_masks = take((size_t)render_band_slots(b->tile) * (size_t)L->band_words * 4);
     L->sort_hist = take((size_t)kRadix * (std::max(L->sort_blocks, L->rec_sort_blocks) + 1) * 4);  // counts + totals
     L->twist_part = take(F * (size_t)L->twist_parts * 6 * 8);
     L->twist_mid = take(F * 32 * 6 * 8);  // 32 slices per frame of the twist reduction
@@ -278,7 +283,7 @@ gs_status gs_render_fwd(const gs_batch *b, const float *colors, const gs_opts *o
         e = launch_render_fwd(b, o, (const uint32_t *)(w + L.order), (const uint2 *)(w + L.ranges),
                               (const uint32_t *)(w + L.vals[0]),
                               (const float4 *)(w + L.splat), colors, (Stats *)(w + L.stats), out_rgb, out_T,
-                              out_last, S(stream));
+                              out_last, (uint32_t *)(w + L.band_masks), L.band_words, S(stream));
     if (e == cudaSuccess) e = prof_mark(GS_PROF_RENDER_FWD, false, S(stream));
     return cuda_status(e);
 }
@@ -374,7 +379,8 @@ gs_status gs_render_bwd(const gs_batch *b, const float *X, const float *quat, co
         e = launch_render_bwd(b, o, (const uint32_t *)(w + L.order), (const uint2 *)(w + L.ranges),
                               (const uint32_t *)(w + L.vals[0]),
                               (const float4 *)(w + L.splat), colors, st, out_T, out_last, dL_drgb,
-                              (float4 *)(w + L.grad2d), S(stream));
+                              (float4 *)(w + L.grad2d), (const uint32_t *)(w + L.band_masks), L.band_words,
+                              S(stream));
     if (e == cudaSuccess) e = prof_mark(GS_PROF_RENDER_BWD, false, S(stream));
     if (e != cudaSuccess) return GS_ERR_CUDA;
     if (b->num_gaussians == 0)

@@ -38,18 +38,20 @@ struct Stats {
 
 struct Layout {
     size_t stats, pose32, pose64, rect, depth, splat, grad2d, keys[2], vals[2], rec_keys[2], rec_vals[2], ranges,
-        order, emit_sums, rec_pairs, sort_hist, twist_part, twist_mid, twist_frame, loss_part, photo_maps, photo_part, total;
+        order, emit_sums, rec_pairs, band_masks, sort_hist, twist_part, twist_mid, twist_frame, loss_part, photo_maps, photo_part, total;
     int emit_blocks;     // blocks of the pair count / emit kernels
     int sort_blocks;     // blocks of the radix passes over pairs
     int rec_sort_blocks; // blocks of the radix passes over records
     int twist_parts;     // twist partials per frame (one per warp of the projection backward)
     int passes;          // radix passes over the tile bits of the pairs
     int first_buffer;    // buffer the emission writes (the last pass ends in 0)
+    long long band_words; // words per band slot of the render's composited-entry masks
 };
 
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 int radix_passes(int num_tiles);
+int render_band_slots(int tile);
 int full_key_passes(int num_tiles);
 bool make_layout(const gs_batch *b, Layout *L);
 

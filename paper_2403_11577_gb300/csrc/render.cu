@@ -34,6 +34,16 @@
 //   skip if e2 > 0;  e = e2 + F (F = log2 opacity); skip if e < log2 alpha_min
 //   alpha = min(alpha_max, 2^e)
 //
+// The forward also records, per band and per 32 entries of the tile's list,
+// a mask of the entries that some pixel of the band composited (one bit
+// per entry; each tile's bits start on a word of its own, word
+// range.start / 32 + tile, in one array per band slot).  The backward's
+// band is the union of one or two forward bands; at batch 64 it loads and
+// stages only the entries of the OR of their masks, which skips the band
+// test and every entry that no pixel of the band composites (on the
+// 1M-Gaussian drive, 12.7M kept (band, Gaussian) entries of the band test
+// against 10.5M composited).  At the other batches it keeps its band test.
+//
 // Backward: walks the pixel's range from its last composited Gaussian back
 // to the first, recovering T_i = T_{i+1} / (1 - alpha_i) from the final
 // transmittance instead of storing it, with S = light composited behind,
@@ -96,6 +106,24 @@ struct Cfg {
     static constexpr int ROWS = NW / BPR * BH;           // pixel rows of the item
     static_assert(NT % 32 == 0 && TILE % BW == 0 && 32 % BW == 0 && NW % BPR == 0 && ROWS <= TILE,
                   "the bands tile the work item");
+};
+
+// The forward bands that tile backward band wb of a work item of the same
+// kind (whole tile or heavy half), as forward band indices: the backward's
+// bands are unions of NX x NY forward bands (two 8x8 bands for a 16x8 band at
+// tile 16; the same band at tiles 8 and 32).
+template <int TILE, int PPTF, int NTF, int PPTB, int NTB>
+struct BandMap {
+    using Cf = Cfg<TILE, PPTF, NTF>;
+    using Cb = Cfg<TILE, PPTB, NTB>;
+    static constexpr int NX = Cb::BW / Cf::BW, NY = Cb::BH / Cf::BH, N = NX * NY;
+    static_assert(Cb::BW % Cf::BW == 0 && Cb::BH % Cf::BH == 0 && N >= 1 && N <= 2 && Cf::ROWS == Cb::ROWS,
+                  "backward bands are unions of at most two forward bands");
+    __device__ static int fwd_band(int wb, int k) {
+        const int bx = (wb % Cb::BPR) * Cb::BW + (k % NX) * Cf::BW;
+        const int by = (wb / Cb::BPR) * Cb::BH + (k / NX) * Cf::BH;
+        return (by / Cf::BH) * Cf::BPR + bx / Cf::BW;
+    }
 };
 
 template <int TILE>
@@ -249,7 +277,7 @@ __device__ __forceinline__ int compact(Staged *st, const Entry (&cu)[PER], int p
 
 // Forward of one work item: rows [rbase, rbase + ROWS) of tile t.
 template <int TILE, int PPT, int NT, int BATCH>
-__device__ __forceinline__ void fwd_item(int t, int rbase, int warp, Staged *st,
+__device__ __forceinline__ void fwd_item(int t, int rbase, int warp, uint32_t *__restrict__ bits, Staged *st,
                                          const gs_frame *__restrict__ frames, int F,
                                          const uint2 *__restrict__ ranges, const uint32_t *__restrict__ vals,
                                          const float4 *__restrict__ splat, const float *__restrict__ colors,
@@ -305,6 +333,9 @@ __device__ __forceinline__ void fwd_item(int t, int rbase, int warp, Staged *st,
             }
         }
         const int cnt = compact<PER>(st, cu, cb0, lane, rp.lmin, xlo, xhi, ylo, yhi);
+        uint32_t cmask[PER];  // chunk entries that some pixel of the band composites, 32 per word
+#pragma unroll
+        for (int q = 0; q < PER; q++) cmask[q] = 0u;
         for (int j = 0; j < cnt; j++) {
             const float4 a = st[j].a, b = st[j].b;
             // every lane evaluates the exponent; one warp vote decides
@@ -337,6 +368,15 @@ __device__ __forceinline__ void fwd_item(int t, int rbase, int warp, Staged *st,
             }
             if (!__any_sync(0xffffffffu, anyc)) continue;
             const uint4 z = st[j].z;
+            // bit (position mod 32), by a funnel shift that wraps its count
+            if constexpr (PER == 1) {
+                cmask[0] |= __funnelshift_l(0u, 1u, z.y);
+            } else {
+                const int q0 = ((int)z.y - cb0) >> 5;
+#pragma unroll
+                for (int q = 0; q < PER; q++)
+                    if (q0 == q) cmask[q] |= __funnelshift_l(0u, 1u, z.y);
+            }
             const float cb = __uint_as_float(z.x);
             const int pos1 = (int)z.y + 1;
             if constexpr (PPT % 2 == 0) {
@@ -386,6 +426,12 @@ __device__ __forceinline__ void fwd_item(int t, int rbase, int warp, Staged *st,
             }
             }
         }
+        if (lane < PER && cb0 + 32 * lane < n) {  // the words of list positions (the tile's own)
+            uint32_t word = cmask[0];
+#pragma unroll
+            for (int q = 1; q < PER; q++) word = lane == q ? cmask[q] : word;
+            bits[(long long)(range.x >> 5) + t + (cb0 >> 5) + lane] = word;
+        }
         __syncwarp();
     }
 #pragma unroll
@@ -413,6 +459,7 @@ __device__ __forceinline__ void fwd_item(int t, int rbase, int warp, Staged *st,
 template <int TILE, int BATCH>
 __global__ void __launch_bounds__(32)
 k_render_fwd(const gs_frame *__restrict__ frames, int F, const uint32_t *__restrict__ order, int heavy,
+             uint32_t *__restrict__ bits, long long band_words,
              const uint2 *__restrict__ ranges, const uint32_t *__restrict__ vals,
              const float4 *__restrict__ splat, const float *__restrict__ colors, RenderParams rp,
              Stats *__restrict__ stats, float *__restrict__ out_rgb, float *__restrict__ out_T,
@@ -422,11 +469,12 @@ k_render_fwd(const gs_frame *__restrict__ frames, int F, const uint32_t *__restr
     Staged *st = reinterpret_cast<Staged *>(smem_raw);
     const int i = (int)blockIdx.x / NW, warp = (int)blockIdx.x % NW;
     if (i < 2 * heavy)
-        fwd_item<TILE, PL / 2, NT, BATCH>((int)order[i >> 1], (i & 1) * (TILE / 2), warp, st, frames, F, ranges,
+        fwd_item<TILE, PL / 2, NT, BATCH>((int)order[i >> 1], (i & 1) * (TILE / 2), warp,
+                                          bits + band_words * (NW * (1 + (i & 1)) + warp), st, frames, F, ranges,
                                           vals, splat, colors, rp, stats, out_rgb, out_T, out_last);
     else
-        fwd_item<TILE, PL, NT, BATCH>((int)order[i - heavy], 0, warp, st, frames, F, ranges, vals, splat, colors,
-                                      rp, stats, out_rgb, out_T, out_last);
+        fwd_item<TILE, PL, NT, BATCH>((int)order[i - heavy], 0, warp, bits + band_words * warp, st, frames, F, ranges,
+                                      vals, splat, colors, rp, stats, out_rgb, out_T, out_last);
 }
 
 __device__ __forceinline__ float warp_sum_f(float v) {
@@ -464,7 +512,8 @@ __device__ __forceinline__ float warp_sum8_transposed(const float (&v)[8], int l
 
 // Backward of one work item: rows [rbase, rbase + ROWS) of tile t.
 template <int TILE, int PPT, int NT, int BATCH>
-__device__ __forceinline__ void bwd_item(int t, int rbase, int warp, Staged *st_all,
+__device__ __forceinline__ void bwd_item(int t, int rbase, int warp, const uint32_t *__restrict__ bits,
+                                         const uint32_t *__restrict__ bits2, Staged *st_all,
                                          const gs_frame *__restrict__ frames, int F,
                                          const uint2 *__restrict__ ranges, const uint32_t *__restrict__ vals,
                                          const float4 *__restrict__ splat, const float *__restrict__ colors,
@@ -521,29 +570,59 @@ __device__ __forceinline__ void bwd_item(int t, int rbase, int warp, Staged *st_
     const long long rec0 = fr.record_offset;
     const float *col = colors + 3 * (size_t)fr.gauss_offset;
     unsigned evals = 0;  // composited (pixel, Gaussian) pairs
+    // At batch 64 (32-entry chunks) the chunks are aligned to 32 list
+    // positions, and only the entries that some pixel of one of the forward
+    // bands tiling this band composited (the forward's masks) are loaded and
+    // staged, in order.  Every entry the band's pixels composite is among
+    // them (the forward composites a superset), so the result is the same as
+    // with the band test, which picks the entries at the other batches.
+    constexpr bool kBits = CH == 32;
+    const long long wbase = (long long)(range.x >> 5) + t;
+    const uint32_t lt_mask = (1u << lane) - 1u;
     Entry nx[PER];
+    uint32_t mnx = 0;
     {
-        const int c0 = max(0, warp_last - CH);
+        const int c0 = kBits ? ((warp_last - 1) & ~31) : max(0, warp_last - CH);
+        if (kBits && warp_last > 0) {
+            const int k = warp_last - c0;
+            mnx = (bits[wbase + (c0 >> 5)] | bits2[wbase + (c0 >> 5)]) & (k >= 32 ? 0xffffffffu : (1u << k) - 1u);
+        }
 #pragma unroll
         for (int p = 0; p < PER; p++) {
             const int i = c0 + p * 32 + lane;
-            load_entry(nx[p], i < warp_last, vals, range.x + i, rec0, splat, col);
+            const bool want = kBits ? ((mnx >> lane) & 1u) != 0u : i < warp_last;
+            load_entry(nx[p], want && warp_last > 0, vals, range.x + i, rec0, splat, col);
         }
     }
-    for (int c_end = warp_last; c_end > 0; c_end -= CH) {
-        const int c0 = max(0, c_end - CH);
+    for (int c_end = warp_last; c_end > 0;) {
+        const int c0 = kBits ? ((c_end - 1) & ~31) : max(0, c_end - CH);
         Entry cu[PER];
 #pragma unroll
         for (int p = 0; p < PER; p++) cu[p] = nx[p];
+        const uint32_t m = mnx;
         if (c0 > 0) {
-            const int n0 = max(0, c0 - CH);
+            const int n0 = kBits ? c0 - 32 : max(0, c0 - CH);
+            if (kBits) mnx = bits[wbase + (n0 >> 5)] | bits2[wbase + (n0 >> 5)];
 #pragma unroll
             for (int p = 0; p < PER; p++) {
                 const int i = n0 + p * 32 + lane;
-                load_entry(nx[p], i < c0, vals, range.x + i, rec0, splat, col);
+                const bool want = kBits ? ((mnx >> lane) & 1u) != 0u : i < c0;
+                load_entry(nx[p], want, vals, range.x + i, rec0, splat, col);
             }
         }
-        const int cnt = compact<PER>(st, cu, c0, lane, rp.lmin, xlo, xhi, ylo, yhi);
+        int cnt;
+        if constexpr (kBits) {
+            if ((m >> lane) & 1u) {
+                Staged &sg = st[__popc(m & lt_mask)];
+                sg.a = cu[0].a;
+                sg.b = make_float4(cu[0].b.x, cu[0].b.y, cu[0].cr, cu[0].cg);
+                sg.z = make_uint4(__float_as_uint(cu[0].cb), (uint32_t)(c0 + lane), cu[0].g, 0u);
+            }
+            __syncwarp();
+            cnt = __popc(m);
+        } else {
+            cnt = compact<PER>(st, cu, c0, lane, rp.lmin, xlo, xhi, ylo, yhi);
+        }
         for (int j = cnt - 1; j >= 0; j--) {
             const float4 a = st[j].a, b = st[j].b;
             const uint4 z = st[j].z;  // b, pos, g
@@ -687,6 +766,7 @@ __device__ __forceinline__ void bwd_item(int t, int rbase, int warp, Staged *st_
             if (lane == 0) atomicAdd(rec + 8, dbt);
         }
         __syncwarp();
+        c_end = c0;
     }
     unsigned long long ev = evals;
     for (int s = 16; s > 0; s >>= 1) ev += __shfl_xor_sync(0xffffffffu, ev, s);
@@ -696,20 +776,28 @@ __device__ __forceinline__ void bwd_item(int t, int rbase, int warp, Staged *st_
 template <int TILE, int BATCH>
 __global__ void __launch_bounds__(32)
 k_render_bwd(const gs_frame *__restrict__ frames, int F, const uint32_t *__restrict__ order, int heavy,
+             const uint32_t *__restrict__ bits, long long band_words,
              const uint2 *__restrict__ ranges, const uint32_t *__restrict__ vals,
              const float4 *__restrict__ splat, const float *__restrict__ colors, RenderParams rp,
              Stats *__restrict__ stats, const float *__restrict__ in_T, const int32_t *__restrict__ in_last,
              const float *__restrict__ dL_drgb, float4 *__restrict__ grad2d) {
     constexpr int NT = BwdThreads<TILE>::NT, PL = bwd_pix_per_thread(TILE), NW = NT / 32;
+    constexpr int NTF = Threads<TILE>::NT, PLF = pix_per_thread(TILE), NWF = NTF / 32;
+    using MW = BandMap<TILE, PLF, NTF, PL, NT>;
+    using MH = BandMap<TILE, PLF / 2, NTF, PL / 2, NT>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Staged *st = reinterpret_cast<Staged *>(smem_raw);
     const int i = (int)blockIdx.x / NW, warp = (int)blockIdx.x % NW;
     if (i < 2 * heavy)
-        bwd_item<TILE, PL / 2, NT, BATCH>((int)order[i >> 1], (i & 1) * (TILE / 2), warp, st, frames, F, ranges,
-                                          vals, splat, colors, rp, stats, in_T, in_last, dL_drgb, grad2d);
+        bwd_item<TILE, PL / 2, NT, BATCH>((int)order[i >> 1], (i & 1) * (TILE / 2), warp,
+                                          bits + band_words * (NWF * (1 + (i & 1)) + MH::fwd_band(warp, 0)),
+                                          bits + band_words * (NWF * (1 + (i & 1)) + MH::fwd_band(warp, MH::N - 1)),
+                                          st, frames, F, ranges, vals, splat, colors, rp, stats, in_T, in_last,
+                                          dL_drgb, grad2d);
     else
-        bwd_item<TILE, PL, NT, BATCH>((int)order[i - heavy], 0, warp, st, frames, F, ranges, vals, splat, colors,
-                                      rp, stats, in_T, in_last, dL_drgb, grad2d);
+        bwd_item<TILE, PL, NT, BATCH>((int)order[i - heavy], 0, warp, bits + band_words * MW::fwd_band(warp, 0),
+                                      bits + band_words * MW::fwd_band(warp, MW::N - 1), st, frames, F,
+                                      ranges, vals, splat, colors, rp, stats, in_T, in_last, dL_drgb, grad2d);
 }
 
 // ---------------------------------------------------------------- launch
@@ -743,27 +831,29 @@ constexpr size_t stage_bytes() {
 template <int TILE, int BATCH>
 cudaError_t run_fwd(const gs_batch *b, const uint32_t *order, const uint2 *ranges, const uint32_t *vals,
                     const float4 *splat, const float *colors, RenderParams rp, Stats *stats, float *out_rgb,
-                    float *out_T, int32_t *out_last, cudaStream_t s) {
+                    float *out_T, int32_t *out_last, uint32_t *masks, long long band_words, cudaStream_t s) {
     constexpr size_t smem = stage_bytes<BATCH>();
     const int heavy = heavy_tiles(b->num_tiles);
     cudaError_t e = smem_opt_in(k_render_fwd<TILE, BATCH>, smem);
     if (e != cudaSuccess) return e;
     k_render_fwd<TILE, BATCH><<<(unsigned)((b->num_tiles + heavy) * (Threads<TILE>::NT / 32)), 32, smem, s>>>(
-        b->frames_dev, b->num_frames, order, heavy, ranges, vals, splat, colors, rp, stats, out_rgb, out_T, out_last);
+        b->frames_dev, b->num_frames, order, heavy, masks, band_words, ranges, vals, splat, colors, rp, stats,
+        out_rgb, out_T, out_last);
     return cudaGetLastError();
 }
 
 template <int TILE, int BATCH>
 cudaError_t run_bwd(const gs_batch *b, const uint32_t *order, const uint2 *ranges, const uint32_t *vals,
                     const float4 *splat, const float *colors, RenderParams rp, Stats *stats, const float *in_T,
-                    const int32_t *in_last, const float *dL, float4 *grad2d, cudaStream_t s) {
+                    const int32_t *in_last, const float *dL, float4 *grad2d, const uint32_t *masks,
+                    long long band_words, cudaStream_t s) {
     constexpr size_t smem = stage_bytes<BATCH>();
     const int heavy = heavy_tiles(b->num_tiles);
     cudaError_t e = smem_opt_in(k_render_bwd<TILE, BATCH>, smem);
     if (e != cudaSuccess) return e;
     k_render_bwd<TILE, BATCH><<<(unsigned)((b->num_tiles + heavy) * (BwdThreads<TILE>::NT / 32)), 32, smem, s>>>(
-        b->frames_dev, b->num_frames, order, heavy, ranges, vals, splat, colors, rp, stats, in_T, in_last, dL,
-        grad2d);
+        b->frames_dev, b->num_frames, order, heavy, masks, band_words, ranges, vals, splat, colors, rp, stats, in_T,
+        in_last, dL, grad2d);
     return cudaGetLastError();
 }
 
@@ -797,10 +887,12 @@ RenderParams make_params(const gs_opts *o) {
 cudaError_t launch_render_fwd(const gs_batch *b, const gs_opts *o, const uint32_t *order, const uint2 *ranges,
                               const uint32_t *vals,
                               const float4 *splat, const float *colors, Stats *stats, float *out_rgb,
-                              float *out_T, int32_t *out_last, cudaStream_t s) {
+                              float *out_T, int32_t *out_last, uint32_t *masks, long long band_words,
+                              cudaStream_t s) {
     if (b->num_tiles == 0) return cudaSuccess;
     const RenderParams rp = make_params(o);
-#define GS_FWD(T_, B_) run_fwd<T_, B_>(b, order, ranges, vals, splat, colors, rp, stats, out_rgb, out_T, out_last, s)
+#define GS_FWD(T_, B_) \
+    run_fwd<T_, B_>(b, order, ranges, vals, splat, colors, rp, stats, out_rgb, out_T, out_last, masks, band_words, s)
     GS_DISPATCH(o->tile, o->batch, GS_FWD)
 #undef GS_FWD
 }
@@ -808,12 +900,25 @@ cudaError_t launch_render_fwd(const gs_batch *b, const gs_opts *o, const uint32_
 cudaError_t launch_render_bwd(const gs_batch *b, const gs_opts *o, const uint32_t *order, const uint2 *ranges,
                               const uint32_t *vals,
                               const float4 *splat, const float *colors, Stats *stats, const float *in_T,
-                              const int32_t *in_last, const float *dL, float4 *grad2d, cudaStream_t s) {
+                              const int32_t *in_last, const float *dL, float4 *grad2d, const uint32_t *masks,
+                              long long band_words, cudaStream_t s) {
     if (b->num_tiles == 0) return cudaSuccess;
     const RenderParams rp = make_params(o);
-#define GS_BWD(T_, B_) run_bwd<T_, B_>(b, order, ranges, vals, splat, colors, rp, stats, in_T, in_last, dL, grad2d, s)
+#define GS_BWD(T_, B_) \
+    run_bwd<T_, B_>(b, order, ranges, vals, splat, colors, rp, stats, in_T, in_last, dL, grad2d, masks, band_words, s)
     GS_DISPATCH(o->tile, o->batch, GS_BWD)
 #undef GS_BWD
+}
+
+// Band slots of the masks: the forward's bands of a whole tile, then those of
+// the two halves of a heavy tile.
+int render_band_slots(int tile) {
+    switch (tile) {
+    case 8: return 3 * (Threads<8>::NT / 32);
+    case 16: return 3 * (Threads<16>::NT / 32);
+    case 32: return 3 * (Threads<32>::NT / 32);
+    default: return 3 * (Threads<32>::NT / 32);
+    }
 }
 
 }  // namespace gs

@@ -309,6 +309,36 @@ def _lidar_grads(tile, batch, W):
     return plan, g
 
 
+def test_render_bwd_walks_the_forwards_band_masks():
+    """The forward records, per band and 32 list entries, which entries some
+    pixel of the band composited; at batch 64 the backward walks only those
+    (OR-ing the two forward bands that tile each of its 16x8 bands), at the
+    other batches it runs its band test.  Masks written by a forward at
+    batch 128 serve a backward at batch 64, and all of these give the same
+    composited pairs and gradients (to the order of the float atomics)."""
+    p = scenes.lidar_frame_problem()
+    cam = p.frames[0].camera
+    W = torch.from_numpy(np.random.default_rng(5).normal(size=(cam.height * cam.width, 3)).astype(np.float32)).cuda()
+    o64, o128 = render.RenderOptions(tile=16, batch=64), render.RenderOptions(tile=16, batch=128)
+    scene, plan, ext, dl = setup(p, o64)
+
+    def run(fwd, bwd):
+        plan.copts = fwd.c()
+        plan.forward(scene, ext, dl)
+        plan.copts = bwd.c()
+        g = render.empty_grads(scene, 1)
+        plan.backward(scene, W.view_as(plan.rgb), g, ext)
+        return plan.rgb.clone(), g, plan.stats()
+
+    rgb, g_ref, st = run(o64, o64)
+    assert st.status == 0 and st.eval_fwd == st.eval_bwd > 10_000_000
+    for fwd, bwd in ((o128, o64), (o64, o128), (o128, o128)):
+        rgb2, g, s2 = run(fwd, bwd)
+        assert torch.equal(rgb2, rgb) and s2.eval_fwd == st.eval_fwd and s2.eval_bwd == st.eval_bwd
+        for k in ("quat", "log_scale", "logit_opacity", "rgb", "ext", "delta"):
+            assert rel_l2(g[k].cpu().numpy(), g_ref[k].cpu().numpy()) <= 5e-5, (fwd.batch, bwd.batch, k)
+
+
 def test_render_band_shapes_agree_on_lidar_frame():
     """Full-size LiDAR frame of anisotropic Gaussians: every tile size culls
     with its own band shapes (8x8 bands at tiles 8 and 16, 16x8 at 32; 8x4,
