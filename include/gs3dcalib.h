@@ -171,7 +171,8 @@ size_t gs_workspace_size(const gs_batch *batch);
  * row-major 9 (high parts), camera centre hi 3, camera centre lo 3, pad,
  * R_cw row-major 9 (low parts: R_cw - high part, rounded), pad 7), [2] pose64
  * (double[F][32]), [3] rect (uint32[R][2]: x0 | y0 << 16, x1 | y1 << 16,
- * inclusive tile coordinates, empty as x0 > x1), [4] depth (float[R]),
+ * inclusive tile coordinates, empty as x0 > x1), [4] depth (float[R];
+ * +inf for a record with an empty rectangle),
  * [5] splat (float4[R][2]: (mean_x, mean_y, A, B), (C, F, rx, ry), the
  * base-2 exponent log2 alpha = A dx^2 + B dx dy + C dy^2 + F and the
  * half-widths of the box outside which alpha < alpha_min), [6] grad2d
@@ -238,7 +239,7 @@ gs_status gs_pose_compose(const gs_batch *batch, const double *traj_t, const dou
  * in float-float arithmetic, and the depth and the 2D mean are rounded once:
  * the depth is the float nearest to the exact depth, the depth order's key.
  * Gaussians with that depth <= near_z or opacity < alpha_min are culled
- * (empty rectangle).
+ * (empty rectangle, and depth +inf, so that gs_bin_sort drops the record).
  *   X[N][3]        centres, world frame (float; fixed LiDAR points, Sec. III-B)
  *   quat[N][4]     rotation r, any non-zero norm (normalised inside)
  *   log_scale[N][3] s = exp(log_scale), clamped to scale_max
@@ -259,7 +260,10 @@ gs_status gs_project(const gs_batch *batch, const float *X, const float *quat,
  * of the depth, equal keys in record order (a stable sort), and each tile's
  * [start, end) range is found, plus a heavy-first order of the tiles for
  * the render.  The workspace keys region holds each sorted pair's global
- * tile (the high half of that key).  If the pairs exceed pair_capacity,
+ * tile (the high half of that key).  It reads the rect, depth and splat
+ * regions that gs_project wrote; a record of depth +inf is dropped before
+ * the sort (gs_project writes +inf for every culled record), and a record
+ * with an empty rectangle emits no pair.  If the pairs exceed pair_capacity,
  * GS_DEV_PAIR_OVERFLOW is set and the batch is treated as having no pairs. */
 gs_status gs_bin_sort(const gs_batch *batch, const gs_opts *opts, void *ws_dev, void *stream);
 

@@ -7,9 +7,11 @@
 // 32-bit keys throughout:
 // 1. 4 LSD passes over the per-(frame, Gaussian) records keyed by the float
 //    bits of their depth: a stable depth order of the records (ties keep
-//    record order).  The first pass reads the depths and rectangles
-//    directly and drops the culled records (empty rectangle); it counts the
-//    rest, and the later passes and stage 2 visit only those.
+//    record order).  The first pass reads the depths directly and drops the
+//    culled records (depth +inf, as gs_project writes for an empty
+//    rectangle); it counts the rest, and the later passes and stage 2 visit
+//    only those.  (A record with an empty rectangle and a finite depth is
+//    sorted like the others and emits no pair.)
 // 2. k_pair_count / k_pair_scan / k_pair_emit over the records in that
 //    order: every record emits one pair per tile of its rectangle (emission
 //    is cooperative: threads stride over the block's output range and find
@@ -430,18 +432,19 @@ __device__ __forceinline__ Chunk sort_chunk(unsigned long long P, int nb, int b)
 }
 
 // The input of a pass: key/value buffers, or (the first pass over the
-// records) the records themselves, keyed by the float bits of their depth
-// (positive, so ordered like the depths) and valued by their index; culled
-// records (empty rectangle) are dropped there, so the later passes and the
-// pair emission see only the records that can make pairs.
-constexpr uint32_t kDropped = 0xffffffffu;  // value of a dropped record (indices are < 2^31)
+// records) the records' depths, each keyed by its float bits (positive, so
+// ordered like the depths) and valued by its index; a record of depth +inf
+// (what gs_project writes for a culled record) is dropped there, so the
+// later passes and the pair emission see only the records that can make
+// pairs.
+constexpr uint32_t kDropped = 0xffffffffu;       // value of a dropped record (indices are < 2^31)
+constexpr uint32_t kCulledDepth = 0x7f800000u;   // +inf
 
 template <typename K>
 struct PassInput {
     const K *keys;
     const uint32_t *vals;
-    const uint2 *rect;    // non-null: read the records instead
-    const float *depth;
+    const float *depth;   // non-null: read the records' depths instead
     const unsigned long long *count;  // items (device), or null: count_host
     long long count_host;
     __device__ __forceinline__ unsigned long long n() const {
@@ -449,24 +452,24 @@ struct PassInput {
     }
     // key of item i; false if it is dropped
     __device__ __forceinline__ bool key(long long i, K &k) const {
-        if (rect) {
-            const uint2 rc = rect[i];
-            k = (K)__float_as_uint(depth[i]);
-            return rect_count(rc) != 0u;
+        if (depth) {
+            const uint32_t bits = __float_as_uint(depth[i]);
+            k = (K)bits;
+            return bits != kCulledDepth;
         }
         k = keys[i];
         return true;
     }
     // key and value of item i; a dropped item gets the value kDropped
     __device__ __forceinline__ void load(long long i, K &k, uint32_t &v) const {
-        if (rect) {
+        if (depth) {
             v = key(i, k) ? (uint32_t)i : kDropped;
         } else {
             k = keys[i];
             v = vals[i];
         }
     }
-    __device__ __forceinline__ bool live(uint32_t v) const { return !rect || v != kDropped; }
+    __device__ __forceinline__ bool live(uint32_t v) const { return !depth || v != kDropped; }
 };
 
 template <typename K>
@@ -772,8 +775,7 @@ template <typename K>
 cudaError_t radix_pass(const K *kin, const uint32_t *vin, K *kout, uint32_t *vout, const unsigned long long *count,
                        int shift, int nb, uint32_t *hist, cudaStream_t s, long long count_host = 0,
                        uint2 *ranges = nullptr) {
-    return radix_pass(PassInput<K>{kin, vin, nullptr, nullptr, count, count_host}, kout, vout, shift, nb, hist, s,
-                      ranges);
+    return radix_pass(PassInput<K>{kin, vin, nullptr, count, count_host}, kout, vout, shift, nb, hist, s, ranges);
 }
 
 __global__ void k_ranges_init(uint2 *__restrict__ ranges, int T) {
@@ -815,9 +817,9 @@ cudaError_t launch_bin_sort(const gs_batch *b, const gs_opts *o, const Layout &L
     if (e != cudaSuccess) return e;
     if (L.emit_blocks > 0) {
         // stage 1: stable depth order of the records (4 passes, ends in buffer 0;
-        // the first reads the records' depths and rectangles)
+        // the first reads the records' depths)
         unsigned long long *live = &stats->num_records;  // records that survive culling
-        e = radix_pass(PassInput<uint32_t>{nullptr, nullptr, rect, depth, nullptr, R}, rkeys[1], rvals[1], 0,
+        e = radix_pass(PassInput<uint32_t>{nullptr, nullptr, depth, nullptr, R}, rkeys[1], rvals[1], 0,
                        L.rec_sort_blocks, hist, s, nullptr, live);
         for (int p = 1; p < 4 && e == cudaSuccess; p++)
             e = radix_pass(rkeys[p & 1], rvals[p & 1], rkeys[(p + 1) & 1], rvals[(p + 1) & 1], live, 8 * p,

@@ -269,7 +269,7 @@ k_project(const gs_frame *__restrict__ frames, int F, int N, const float *__rest
             }
         }
         rect[r] = rc;
-        depth[r] = vis ? Q.p[2] : 0.f;
+        depth[r] = rect_count(rc) ? Q.p[2] : INFINITY;  // +inf: culled (the sort drops it)
     }
     if (nonfinite) atomicOr(&stats->status, (unsigned)GS_DEV_NONFINITE);
 }
