@@ -69,7 +69,8 @@ namespace gs {
 
 namespace {
 
-// Pixels per thread, halved in the halves of heavy tiles.
+// Pixels per thread: 2 at tiles 8 and 16, 4 at 32; half of that in the
+// halves of heavy tiles.
 // The forward's pixels per thread: two at tiles 8 and 16 (8x8 bands), four at
 // tile 32.  GS_FWD_PPT16 overrides tile 16's value (2 or 4) at build time.
 #ifndef GS_FWD_PPT16
@@ -80,8 +81,7 @@ __host__ __device__ constexpr int pix_per_thread(int tile) { return tile == 32 ?
 // The backward's pixels per thread: four at tiles 16 and 32 (16x8 bands, 8x8
 // in the halves of heavy tiles), which spreads each kept Gaussian's 9-value
 // warp reduction over twice the pixels of the forward's 8x8 bands; two at
-// tile 8.  GS_BWD_PPT16 overrides tile 16's value (2 or 4, not below
-// GS_FWD_PPT16: a backward band is a union of forward bands) at build time.
+// tile 8.  GS_BWD_PPT16 overrides tile 16's value (2 or 4) at build time.
 #ifndef GS_BWD_PPT16
 #define GS_BWD_PPT16 4
 #endif
